@@ -1,0 +1,379 @@
+"""Benchmark: SBV log-likelihood evaluations per second on one GB300.
+
+Workload (default): sine10d -- n = 1,000,000 points uniform on [0,1]^10, y from
+the sine-sum family, 20,000 K-means blocks (~50 points), m = 120 neighbours,
+Matern-5/2, one theta per evaluation (the shape of the paper's Sec. 8
+performance study: d = 10 on [0,1]^10).  Blocking and kNN run once, untimed
+(reported separately); a step is one full log-likelihood evaluation: gather,
+covariance, factorisation, block terms and the deterministic sum.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SBV loglik evals/s & TFLOP/s on 1 GB300, mixed vs FP64 at |dl|/n <= 1e-6"
+UNIT = "evals/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="sine10d")
+    p.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64"])
+    p.add_argument("--kmeans-iters", type=int, default=10)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-blocks", type=int, default=0)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- workload
+def make_workload(name: str):
+    from synth.inputs import workload
+    w = workload(name)
+    if w["y"] is None:
+        raise SystemExit(f"workload {name} needs a GP draw; use a sine-sum workload for the bench")
+    return w
+
+
+def algorithmic_flops(ptr: np.ndarray, cnt: np.ndarray) -> float:
+    """sum_i N_i^3/3 + N_i^2 (Cholesky of the joint matrix plus the bordered solve)."""
+    N = np.diff(ptr).astype(np.float64) + cnt.astype(np.float64)
+    return float(np.sum(N ** 3 / 3.0 + N ** 2))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 ALU peak: 1.25 TFLOP/s nominal for GB300 (the FP64 rate is far below the tensor rates);
+# derivation and the measured DFMA rate are recorded beside the roofline in the design notes.
+FP64_PEAK_TFLOPS = 1.25
+
+
+# ----------------------------------------------------------------------------- CPU baseline
+CPU_SNIPPET = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, {root!r})
+from synth.inputs import workload
+from oracle import sbv
+w = workload({name!r})
+n, bc, m = w["n"], w["bc"], w["m"]
+bs = n // bc
+# same block size and neighbour count on a smaller point set: the per-block arithmetic of the
+# oracle is identical, so its time per block extrapolates to the full workload
+nsub = min(n, {nblocks} * bs)
+X = w["X"][:nsub]; y = w["y"][:nsub]
+b = sbv.blocking(X, w["beta_scale"], nsub // bs, 3, 5)
+nbr, cnt = sbv.knn(b["Z"], b["blk"], b["rank"], b["centres"], m)
+rows = np.nonzero(cnt == min(m, int(cnt.max())))[0][:{nblocks}]
+th = w["theta"][0]
+t0 = time.perf_counter()
+sbv.loglik_terms(X, y, b["ptr"], b["pts"], nbr, cnt, th, w["nu2"], blocks=rows)
+dt = time.perf_counter() - t0
+print(json.dumps(dict(seconds=dt, blocks=int(rows.size), bc=bc, bs=bs, m=m)))
+"""
+
+
+def cpu_baseline(name: str, nblocks: int):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = CPU_SNIPPET.format(root=ROOT, name=name, nblocks=nblocks)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=900)
+    if r.returncode != 0:
+        return {"error": r.stderr[-400:]}
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    per_block = res["seconds"] / res["blocks"]
+    evals_per_s = 1.0 / (per_block * res["bc"])
+    return {"value": evals_per_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{res['blocks']} full-size blocks (bs~{res['bs']}, m={res['m']}) of the "
+                      f"{name} workload shape, {res['seconds']:.1f} s of single-thread FP64 oracle "
+                      f"time, extrapolated linearly to bc={res['bc']}"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from synth.inputs import WORKLOADS
+    w = WORKLOADS[args.workload]
+    per_step = []
+    nblocks = args.cpu_sample_blocks or 60
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(args.workload, nblocks)
+        if "error" in cb:
+            print(json.dumps({"impl": "reference", "unavailable": cb["error"][-200:]}))
+            return
+        if i >= args.warmup:
+            per_step.append(cb)
+    v = statistics.median([c["value"] for c in per_step])
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": w["n"], "d": w["d"], "bc": w["bc"],
+                   "m": w["m"], "nu": w["nu2"] / 2, "theta_per_eval": 1},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": per_step[-1]["sample"]},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2504_12004_gb300 import build, Context
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    ctx = Context(local)
+    dev = torch.device("cuda", local)
+
+    # ---------------- inputs (synthetic, seeded) and one-time structure
+    w = make_workload(args.workload)
+    X_h, y_h, beta, th = w["X"], w["y"], w["beta_scale"], w["theta"]
+    X = torch.from_numpy(X_h).to(dev)
+    y = torch.from_numpy(y_h).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = ctx.sbv_blocking(X, beta, w["bc"], args.kmeans_iters, 1234)
+    torch.cuda.synchronize()
+    t_block = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    nbr, cnt = ctx.sbv_knn(X, beta, b["ptr"], b["pts"], b["rank"], b["centres"], w["m"])
+    torch.cuda.synchronize()
+    t_knn = time.perf_counter() - t0
+    ptr, pts = b["ptr"], b["pts"]
+    bc = b["bc_eff"]
+    nbr = nbr.contiguous()
+    flops = algorithmic_flops(ptr.cpu().numpy(), cnt.cpu().numpy())
+
+    def evaluate(precision, stream=None):
+        return ctx.sbv_loglik(X, y, ptr, pts, nbr, cnt, th, nu2=w["nu2"], precision=precision,
+                              stream=stream)
+
+    precision = args.precision
+    if precision == "auto":
+        try:
+            evaluate("mixed")
+            torch.cuda.synchronize()
+            precision = "mixed"
+        except Exception:
+            precision = "fp64"
+
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(prec, steps, warmup):
+        for _ in range(warmup):
+            evaluate(prec)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        out = None
+        for i in range(steps):
+            flush.fill_(float(i))        # evict L2 between steps (inputs would otherwise stay resident)
+            ev[i][0].record(stream)
+            out = evaluate(prec)
+            ev[i][1].record(stream)
+        end.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        total_ms = start.elapsed_time(end)
+        per_call = [a.elapsed_time(c) for a, c in ev]
+        return total_ms, per_call, out
+
+    with ClockSampler(local) as clk:
+        total_ms, per_call, ll = timed(precision, args.steps, args.warmup)
+    clocks = clk.summary()
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ll_v = float(ll[0].item())
+    value = world * args.steps / (total_ms / 1000.0)
+    call_ms = statistics.mean(per_call)
+
+    # FP64 path beside the headline (same structure, same theta)
+    fp64_info = None
+    if precision == "mixed":
+        f_total, f_calls, f_ll = timed("fp64", max(3, args.steps // 4), 1)
+        fll = float(f_ll[0].item())
+        fp64_info = {"evals_per_s": max(3, args.steps // 4) / (f_total / 1000.0),
+                     "ms_per_call": statistics.mean(f_calls), "ll": fll,
+                     "delta_l_per_n_mixed_vs_fp64": abs(ll_v - fll) / w["n"]}
+
+    # ---------------- end to end: host buffers in, host scalar out, copies timed
+    pin = lambda t: t.cpu().pin_memory()
+    host = {k: pin(v) for k, v in dict(X=X, y=y, ptr=ptr, pts=pts, nbr=nbr, cnt=cnt).items()}
+    dev_bufs = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    ll_host = torch.empty(1, dtype=torch.float64).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    for i in range(args.warmup + args.steps):
+        if i == args.warmup:
+            torch.cuda.synchronize()
+            e0 = time.perf_counter()
+        for k, v in host.items():
+            dev_bufs[k].copy_(v, non_blocking=True)
+        o = ctx.sbv_loglik(dev_bufs["X"], dev_bufs["y"], dev_bufs["ptr"], dev_bufs["pts"],
+                           dev_bufs["nbr"], dev_bufs["cnt"], th, nu2=w["nu2"], precision=precision)
+        ll_host.copy_(o, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - e0
+    e2e = {"value": args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": 8}
+
+    # ---------------- roofline of the dominant kernel (the block log-likelihood)
+    peaks, src = measured_peaks()
+    achieved_tflops = flops / (call_ms / 1000.0) / 1e12
+    if precision == "fp64":
+        roof = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "nominal FP64 rate of GB300"}
+    else:
+        peak = peaks.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25)
+        roof = {"bound": "tensor", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved_tflops / peak, "traffic": None,
+                "peak_source": f"{src} bf16 sustained x nominal tf32/bf16 ratio"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload, args.cpu_sample_blocks or 120)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": w["n"], "d": w["d"], "bc": bc, "m": w["m"],
+                       "nu": w["nu2"] / 2, "theta_per_eval": 1, "precision": precision,
+                       "l2": "flushed between steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "tflops": achieved_tflops,
+            "ll": ll_v,
+            "fp64_path": fp64_info,
+            "preprocess_s": {"blocking": t_block, "knn": t_knn},
+            "algorithmic_flops_per_eval": flops,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * sbv.h -- C ABI of the GB300 Scaled Block Vecchia library (libsbv.so).
+ *
+ * Scaled Block Vecchia (SBV, arxiv 2504.12004) approximates a Gaussian-process
+ * log-likelihood by a product of block conditionals (Sec. 4.2, Eq.
+ * mmsearchingBV): points are scaled per dimension (Alg. 2), clustered into
+ * blocks (Alg. 3), the blocks are put in random order (Alg. 1 Step 2), every
+ * block conditions on the m points of earlier blocks nearest to its centre
+ * (Alg. 4), and each block contributes log p(y_B | y_J) (Alg. 5).
+ *
+ * Conventions for every entry point
+ *   - Return value: SBV_OK (0) or one of the SBV_E* codes below; the message
+ *     of the last failure on a context is returned by sbv_last_error().
+ *   - Pointers marked "device" are CUDA device pointers on the context's
+ *     device; "host" pointers are ordinary host memory.  The caller owns every
+ *     buffer it passes; the library never frees caller memory.  The library
+ *     owns only the context and its internal workspace.
+ *   - `stream` is a cudaStream_t (passed as void*; NULL = legacy default
+ *     stream).  Calls are ordered on that stream.  sbv_blocking, sbv_knn and
+ *     sbv_predict return after their work has finished; sbv_loglik only
+ *     enqueues work (see its comment).
+ *   - Point matrices are row-major n x d (point i occupies d consecutive
+ *     values), dtype SBV_F64 (double) or SBV_F32 (float; widened exactly to
+ *     double wherever a decision is taken).
+ *   - Parameter rows theta are (sigma^2, tau^2, beta_1 .. beta_d): process
+ *     variance, nugget and per-dimension ranges of the scaled Matern kernel
+ *     K(a,b) = sigma^2 M_nu(r) + tau^2 [a is b], r^2 = sum_t ((x_at-x_bt)/beta_t)^2
+ *     (Eq. scale, Eq. maternkernel), M_nu the closed-form Matern correlation
+ *     for nu = nu2/2, nu2 in {1,3,5,7}, evaluated at r itself (no sqrt(2 nu)
+ *     factor, as the equation is printed).  The nugget is added only where a
+ *     and b are the same data point.
+ *   - Indices in outputs are original point indices (0-based).
+ *   - There is no CPU fallback: every computation runs in CUDA kernels.
+ */
+#ifndef SBV_H
+#define SBV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SBV_OK            0
+#define SBV_EINVAL        1  /* invalid argument (sizes, null pointers, parameters) */
+#define SBV_ENOTSPD       2  /* a covariance matrix was not positive definite */
+#define SBV_ENOMEM        3  /* device or host allocation failed */
+#define SBV_ECUDA         4  /* a CUDA runtime call failed (message has the CUDA error) */
+#define SBV_ETIMEOUT      5  /* a bounded device wait gave up */
+#define SBV_EUNSUPPORTED  6  /* size above a compiled limit, unsupported nu */
+
+/* element types of point matrices */
+#define SBV_F64 0
+#define SBV_F32 1
+
+/* arithmetic of the per-block factorisation */
+#define SBV_PREC_FP64  0   /* everything in FP64 */
+#define SBV_PREC_MIXED 1   /* FP32 factorisation, FP64 diagonal tiles, log-det and refinement */
+
+/* compiled limits */
+#define SBV_MAX_DIM      64     /* d */
+#define SBV_MAX_BLOCK_N  1024   /* m_i + bs_i of one block */
+
+typedef struct sbv_ctx sbv_ctx;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int sbv_version(void);
+
+/* Create a context on CUDA device `device`.  *ctx receives the handle. */
+int sbv_create(sbv_ctx** ctx, int device);
+
+/* Destroy a context and release its workspace (NULL is ignored). */
+void sbv_destroy(sbv_ctx* ctx);
+
+/* Message describing the last non-zero status returned on `ctx`
+ * (empty string if none; "null context" for NULL).  Owned by the context. */
+const char* sbv_last_error(const sbv_ctx* ctx);
+
+/*
+ * sbv_blocking -- scaling, Random Anchor Clustering with Lloyd iterations, and
+ * the random block order (Alg. 2 dimension scaling; Alg. 3; Alg. 1 Step 2).
+ *
+ *   X            device, n x d, dtype           input points
+ *   beta_scale   host, d doubles > 0            scaling ranges: z = x / beta_scale
+ *   bc           requested block count, 1 <= bc <= n
+ *   kmeans_iters Lloyd iterations T >= 0 after the RAC assignment (T = 0 is RAC)
+ *   seed         seed of the SplitMix64 stream that draws anchors and order
+ *   blk          device, n int32     out: block of each point (compacted ids)
+ *   ptr          device, bc+1 int64  out: CSR offsets, block j = pts[ptr[j] .. ptr[j+1])
+ *   pts          device, n int32     out: points grouped by block, increasing index inside
+ *   rank         device, bc int32    out: position of each block in the random order
+ *   centres      device, bc x d f64  out: mean of each block's scaled members
+ *   bc_eff       host, int64         out: number of non-empty blocks (entries
+ *                                    beyond bc_eff of ptr/rank/centres are unused)
+ *
+ * Anchors are the first bc entries of a Fisher-Yates shuffle of [0, n) drawn
+ * from SplitMix64(seed) with Lemire's bounded draw; every point joins the
+ * anchor/centre with the smallest squared scaled distance (sum over
+ * dimensions left to right, no fused multiply-add, ties to the smaller block);
+ * Lloyd iterations recompute centres as member means (members summed in
+ * increasing point index) and stop early when no assignment changes; empty
+ * blocks are dropped; the order is a full Fisher-Yates shuffle from the same
+ * stream, block perm[r] receiving rank r.  Results are bit-identical for a
+ * given input on any GB300.
+ * Errors: SBV_EINVAL (n < 1, d < 1 or > SBV_MAX_DIM, bc outside [1, n],
+ * kmeans_iters < 0, beta_scale <= 0 or null pointers), SBV_ENOMEM, SBV_ECUDA.
+ */
+int sbv_blocking(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_t d,
+                 const double* beta_scale, int64_t bc, int32_t kmeans_iters,
+                 uint64_t seed, int32_t* blk, int64_t* ptr, int32_t* pts,
+                 int32_t* rank, double* centres, int64_t* bc_eff, void* stream);
+
+/*
+ * sbv_knn -- earlier-ordered m nearest neighbours of every block (Alg. 4,
+ * Eq. mmsearchingBV).
+ *
+ *   X, dtype, n, d, beta_scale   as for sbv_blocking (same scaling)
+ *   ptr, pts, rank, centres      device, output of sbv_blocking for bc blocks
+ *   m            neighbours per block, 0 <= m <= SBV_MAX_BLOCK_N - 1
+ *   nbr          device, bc x m int32  out: row j = neighbours of block j,
+ *                                      ascending by (squared scaled distance to
+ *                                      the centre, point index); -1 padded
+ *   cnt          device, bc int32      out: m_j = min(m, #points of blocks
+ *                                      with smaller rank)
+ *
+ * Candidates of block j are exactly the points of blocks with rank strictly
+ * below rank[j] (a block never conditions on itself).  Distances are the
+ * same bit-exact sums as in sbv_blocking.
+ * Errors: SBV_EINVAL, SBV_EUNSUPPORTED (m too large), SBV_ENOMEM, SBV_ECUDA.
+ */
+int sbv_knn(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_t d,
+            const double* beta_scale, const int64_t* ptr, const int32_t* pts,
+            const int32_t* rank, const double* centres, int64_t bc, int32_t m,
+            int32_t* nbr, int32_t* cnt, void* stream);
+
+/*
+ * sbv_loglik -- Block Vecchia log-likelihood for B parameter rows (Alg. 5
+ * per block; Alg. 1 Step 5 for the sum).
+ *
+ *   X, dtype, n, d     device points (unscaled; the kernel ranges come from theta)
+ *   y                  device, n doubles, observations
+ *   ptr, pts           device, block CSR from sbv_blocking (bc blocks)
+ *   nbr, cnt           device, neighbours from sbv_knn (row stride m)
+ *   theta              host, B x (2+d) doubles, rows (sigma^2, tau^2, beta_1..beta_d)
+ *   nu2                2*nu in {1, 3, 5, 7}
+ *   precision          SBV_PREC_FP64 or SBV_PREC_MIXED
+ *   ll                 device, B doubles  out: l(theta_b) = sum_i l_{b,i}
+ *   block_terms        device, B x bc doubles out (or NULL): l_{b,i}
+ *   status             device, B x bc int32 out (or NULL): 0, or SBV_ENOTSPD
+ *                      for a block whose matrix was not positive definite
+ *                      (its term and the total are then NaN)
+ *
+ * Block i conditions its points B_i (in increasing index) on its neighbours
+ * J_i (in the order of nbr): with Sigma the joint covariance of [J_i; B_i]
+ * and L its Cholesky factor, w = L^{-1} [y_J; y_B] and
+ *   l_{b,i} = -1/2 [ bs_i log(2 pi) + 2 sum_{t in B} log L_tt + sum_{t in B} w_t^2 ],
+ * which equals the POTRF/TRSM/GEMM/Schur/POTRF/TRSV chain of Alg. 5 (with
+ * Sigma^lk in the Schur step).  The sum over blocks is a fixed-order tree, so
+ * repeated calls give bit-identical results.  The call only enqueues work on
+ * `stream` and returns; failures inside kernels are reported through
+ * `status`, NaN totals, and sbv_sync_status().
+ * Errors (argument checks, before any work): SBV_EINVAL (null pointers,
+ * B < 1, sigma^2 <= 0, tau^2 < 0, beta <= 0, bad nu2 or precision),
+ * SBV_EUNSUPPORTED (a block with m_i + bs_i > SBV_MAX_BLOCK_N), SBV_ENOMEM,
+ * SBV_ECUDA.
+ */
+int sbv_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y,
+               int64_t n, int32_t d, const int64_t* ptr, const int32_t* pts,
+               const int32_t* nbr, const int32_t* cnt, int64_t bc, int32_t m,
+               const double* theta, int32_t B, int32_t nu2, int32_t precision,
+               double* ll, double* block_terms, int32_t* status, void* stream);
+
+/*
+ * sbv_sync_status -- wait for `stream`, then report whether any sbv_loglik or
+ * sbv_predict kernel since the previous call met a non-positive-definite
+ * matrix (SBV_ENOTSPD, message names the first block/test point) or a CUDA
+ * error (SBV_ECUDA).  Clears the record.
+ */
+int sbv_sync_status(sbv_ctx* ctx, void* stream);
+
+/*
+ * sbv_predict -- Block Vecchia prediction with one test point per block
+ * (Sec. 4.2 prediction product; Sec. 5.5).
+ *
+ *   X, dtype, y, n, d  device training points and observations
+ *   Xtest              device, ntest x d, same dtype
+ *   beta_scale         host, d doubles: scaling used to rank neighbours
+ *   m_pred             neighbours per test point, 1 <= m_pred <= min(n, SBV_MAX_BLOCK_N - 1)
+ *   theta              host, 2+d doubles (one parameter row)
+ *   mean, var, var_latent  device, ntest doubles out: conditional mean, variance
+ *                      on the observation scale (includes tau^2) and of the
+ *                      latent process (var - tau^2)
+ *   nbr                device, ntest x m_pred int32 out (or NULL): neighbours
+ *                      of each test point, ascending by (scaled distance, index)
+ *
+ * Each test point conditions on its m_pred nearest training points (all n are
+ * candidates): mean = Sigma_{*J} Sigma_JJ^{-1} y_J and
+ * var = sigma^2 + tau^2 - Sigma_{*J} Sigma_JJ^{-1} Sigma_{J*}.
+ * Errors: SBV_EINVAL, SBV_EUNSUPPORTED, SBV_ENOTSPD, SBV_ENOMEM, SBV_ECUDA.
+ */
+int sbv_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y,
+                int64_t n, int32_t d, const void* Xtest, int64_t ntest,
+                const double* beta_scale, int32_t m_pred, const double* theta,
+                int32_t nu2, int32_t precision, double* mean, double* var,
+                double* var_latent, int32_t* nbr, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBV_H */

@@ -1,0 +1,213 @@
+"""ctypes binding of libsbv.so: argument marshalling only.
+
+Every function here converts torch tensors / numpy arrays into the plain
+pointers and sizes of the C ABI in include/sbv.h and calls it.  No step of the
+method runs in Python.  If the shared library has not been built, importing
+the binding raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+import torch
+
+LIB_PATH = Path(__file__).resolve().parent / "libsbv.so"
+
+SBV_OK, SBV_EINVAL, SBV_ENOTSPD, SBV_ENOMEM, SBV_ECUDA, SBV_ETIMEOUT, SBV_EUNSUPPORTED = range(7)
+SBV_F64, SBV_F32 = 0, 1
+SBV_PREC_FP64, SBV_PREC_MIXED = 0, 1
+PRECISIONS = {"fp64": SBV_PREC_FP64, "mixed": SBV_PREC_MIXED}
+ERRNAMES = {1: "SBV_EINVAL", 2: "SBV_ENOTSPD", 3: "SBV_ENOMEM", 4: "SBV_ECUDA",
+            5: "SBV_ETIMEOUT", 6: "SBV_EUNSUPPORTED"}
+
+_lib = None
+
+# (name, restype, argtypes) of every exported symbol
+_P, _I32, _I64, _U64, _D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+SIGNATURES = {
+    "sbv_version": (C.c_int, []),
+    "sbv_create": (C.c_int, [C.POINTER(_P), C.c_int]),
+    "sbv_destroy": (None, [_P]),
+    "sbv_last_error": (C.c_char_p, [_P]),
+    "sbv_blocking": (C.c_int, [_P, _P, C.c_int, _I64, _I32, _P, _I64, _I32, _U64,
+                               _P, _P, _P, _P, _P, C.POINTER(_I64), _P]),
+    "sbv_knn": (C.c_int, [_P, _P, C.c_int, _I64, _I32, _P, _P, _P, _P, _P, _I64, _I32,
+                          _P, _P, _P]),
+    "sbv_loglik": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64, _I32,
+                             _P, _I32, _I32, _I32, _P, _P, _P, _P]),
+    "sbv_sync_status": (C.c_int, [_P, _P]),
+    "sbv_predict": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _I64, _P, _I32, _P,
+                              _I32, _I32, _P, _P, _P, _P, _P]),
+}
+
+
+class SBVError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load() -> C.CDLL:
+    """Load libsbv.so (built by paper_2504_12004_gb300.build); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not LIB_PATH.exists():
+        raise RuntimeError(f"{LIB_PATH} is missing: run `python -m paper_2504_12004_gb300.build` "
+                           "(the CUDA library is required; there is no CPU fallback)")
+    lib = C.CDLL(str(LIB_PATH))
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return C.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(C.c_void_p)
+    raise TypeError(type(t))
+
+
+def _stream(stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _xdtype(X: torch.Tensor) -> int:
+    if X.dtype == torch.float64:
+        return SBV_F64
+    if X.dtype == torch.float32:
+        return SBV_F32
+    raise TypeError(f"points must be float64 or float32, got {X.dtype}")
+
+
+def _dev(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _host_f64(a, name: str) -> np.ndarray:
+    if isinstance(a, torch.Tensor):
+        a = a.detach().cpu().numpy()
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class Context:
+    """An sbv_ctx on one CUDA device (owns the library's workspace)."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        self.device = device
+        h = C.c_void_p()
+        rc = self.lib.sbv_create(C.byref(h), device)
+        if rc != SBV_OK:
+            raise SBVError(rc, f"sbv_create(device={device}) failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sbv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != SBV_OK:
+            raise SBVError(rc, self.lib.sbv_last_error(self.h).decode())
+
+    # ---- entry points -------------------------------------------------------
+    def sbv_blocking(self, X, beta_scale, bc: int, kmeans_iters: int, seed: int, stream=None):
+        X = _dev(X, None, "X")
+        n, d = X.shape
+        beta = _host_f64(beta_scale, "beta_scale")
+        dev = X.device
+        blk = torch.empty(n, dtype=torch.int32, device=dev)
+        ptr = torch.empty(bc + 1, dtype=torch.int64, device=dev)
+        pts = torch.empty(n, dtype=torch.int32, device=dev)
+        rank = torch.empty(bc, dtype=torch.int32, device=dev)
+        centres = torch.empty(bc, d, dtype=torch.float64, device=dev)
+        bc_eff = C.c_int64(0)
+        rc = self.lib.sbv_blocking(self.h, _ptr(X), _xdtype(X), n, d, _ptr(beta), bc, kmeans_iters,
+                                   seed, _ptr(blk), _ptr(ptr), _ptr(pts), _ptr(rank), _ptr(centres),
+                                   C.byref(bc_eff), _stream(stream))
+        self._check(rc)
+        k = bc_eff.value
+        return dict(blk=blk, ptr=ptr[:k + 1].contiguous(), pts=pts, rank=rank[:k].contiguous(),
+                    centres=centres[:k].contiguous(), bc_eff=k)
+
+    def sbv_knn(self, X, beta_scale, ptr, pts, rank, centres, m: int, stream=None):
+        X = _dev(X, None, "X")
+        n, d = X.shape
+        bc = rank.numel()
+        beta = _host_f64(beta_scale, "beta_scale")
+        nbr = torch.empty(bc, max(m, 1), dtype=torch.int32, device=X.device)
+        cnt = torch.empty(bc, dtype=torch.int32, device=X.device)
+        rc = self.lib.sbv_knn(self.h, _ptr(X), _xdtype(X), n, d, _ptr(beta),
+                              _ptr(_dev(ptr, torch.int64, "ptr")), _ptr(_dev(pts, torch.int32, "pts")),
+                              _ptr(_dev(rank, torch.int32, "rank")),
+                              _ptr(_dev(centres, torch.float64, "centres")), bc, m, _ptr(nbr),
+                              _ptr(cnt), _stream(stream))
+        self._check(rc)
+        return nbr[:, :m], cnt
+
+    def sbv_loglik(self, X, y, ptr, pts, nbr, cnt, theta, nu2: int = 5, precision="fp64",
+                   ll=None, block_terms=None, status=None, stream=None):
+        """Enqueue the log-likelihood of every theta row; returns the device tensor ll (B)."""
+        X = _dev(X, None, "X")
+        n, d = X.shape
+        bc = cnt.numel()
+        m = nbr.shape[1] if nbr.dim() == 2 else 0
+        th = _host_f64(theta, "theta").reshape(-1, 2 + d)
+        B = th.shape[0]
+        if ll is None:
+            ll = torch.empty(B, dtype=torch.float64, device=X.device)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        nbr_c = _dev(nbr.contiguous() if nbr.stride(0) != m else nbr, torch.int32, "nbr")
+        rc = self.lib.sbv_loglik(self.h, _ptr(X), _xdtype(X), _ptr(_dev(y, torch.float64, "y")), n, d,
+                                 _ptr(_dev(ptr, torch.int64, "ptr")), _ptr(_dev(pts, torch.int32, "pts")),
+                                 _ptr(nbr_c), _ptr(_dev(cnt, torch.int32, "cnt")), bc, m,
+                                 _ptr(th), B, nu2, prec, _ptr(ll), _ptr(block_terms), _ptr(status),
+                                 _stream(stream))
+        self._check(rc)
+        return ll
+
+    def sbv_sync_status(self, stream=None):
+        self._check(self.lib.sbv_sync_status(self.h, _stream(stream)))
+
+    def sbv_predict(self, X, y, Xtest, beta_scale, m_pred: int, theta, nu2: int = 5,
+                    precision="fp64", want_nbr=False, stream=None):
+        X = _dev(X, None, "X")
+        Xtest = _dev(Xtest, X.dtype, "Xtest")
+        n, d = X.shape
+        nt = Xtest.shape[0]
+        beta = _host_f64(beta_scale, "beta_scale")
+        th = _host_f64(theta, "theta").reshape(-1)
+        dev = X.device
+        mean = torch.empty(nt, dtype=torch.float64, device=dev)
+        var = torch.empty(nt, dtype=torch.float64, device=dev)
+        var_lat = torch.empty(nt, dtype=torch.float64, device=dev)
+        nbr = torch.empty(nt, m_pred, dtype=torch.int32, device=dev) if want_nbr else None
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        rc = self.lib.sbv_predict(self.h, _ptr(X), _xdtype(X), _ptr(_dev(y, torch.float64, "y")), n, d,
+                                  _ptr(Xtest), nt, _ptr(beta), m_pred, _ptr(th), nu2, prec,
+                                  _ptr(mean), _ptr(var), _ptr(var_lat), _ptr(nbr), _stream(stream))
+        self._check(rc)
+        return mean, var, var_lat, nbr

@@ -1,0 +1,44 @@
+// Device building blocks shared by the block log-likelihood and prediction
+// kernels: per-theta parameters, the gather of a block's points, the scaled
+// Matern covariance (Eq. scale, Eq. maternkernel) and the work counter.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sbv.h"
+#include "sbv_internal.cuh"
+
+namespace sbv {
+
+// Derived parameters of one theta row.
+struct ThetaDev {
+  double sigma2;
+  double tau2;
+  double inv_beta[SBV_MAX_DIM];
+};
+
+// Closed-form Matern correlation 2^(1-nu)/Gamma(nu) r^nu K_nu(r), nu = nu2/2,
+// at the scaled distance r (no sqrt(2 nu) factor).
+__device__ __forceinline__ double matern64(double r, int nu2) {
+  double e = exp(-r);
+  switch (nu2) {
+    case 1: return e;
+    case 3: return (1.0 + r) * e;
+    case 5: return fma(r, fma(r, 1.0 / 3.0, 1.0), 1.0) * e;
+    default: return fma(r, fma(r, fma(r, 1.0 / 15.0, 0.4), 1.0), 1.0) * e;
+  }
+}
+
+// Record the first failing item on the context's device status.
+__device__ __forceinline__ void record_failure(DevStatus* st, int code, int item, int theta) {
+  if (atomicCAS(&st->code, 0, code) == 0) {
+    st->item = item;
+    st->theta = theta;
+  }
+  atomicAdd(&st->count, 1);
+}
+
+// Packed lower-triangular index of (i, j), j <= i.
+__device__ __forceinline__ int tri(int i, int j) { return (i * (i + 1) >> 1) + j; }
+
+}  // namespace sbv

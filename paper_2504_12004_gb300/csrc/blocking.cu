@@ -1,0 +1,416 @@
+// Scaling (Alg. 2), Random Anchor Clustering and Lloyd iterations (Alg. 3,
+// K-means of Sec. 5.2), compaction and the random block order (Alg. 1 Step 2).
+#include <cub/cub.cuh>
+#include <algorithm>
+#include <unordered_map>
+#include <vector>
+
+#include "dist.cuh"
+#include "sbv_internal.cuh"
+
+namespace sbv {
+
+// ---------------------------------------------------------------------------
+// Host-side random choices: SplitMix64 stream, Lemire's bounded draw and
+// Fisher-Yates shuffles (the generator reading adopted for Alg. 1 and 3).
+// ---------------------------------------------------------------------------
+struct SplitMix64 {
+  uint64_t state;
+  explicit SplitMix64(uint64_t seed) : state(seed) {}
+  uint64_t next() {
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  // uniform in [0, s): high word of x*s; reject while the low word < (2^64 - s) mod s
+  uint64_t below(uint64_t s) {
+    unsigned __int128 p = (unsigned __int128)next() * s;
+    uint64_t low = (uint64_t)p;
+    if (low < s) {
+      uint64_t t = (0ull - s) % s;
+      while (low < t) {
+        p = (unsigned __int128)next() * s;
+        low = (uint64_t)p;
+      }
+    }
+    return (uint64_t)(p >> 64);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+struct BetaArg {
+  double b[SBV_MAX_DIM];
+};
+
+template <typename T>
+__global__ void scale_kernel(const T* __restrict__ X, int64_t n, int d, BetaArg beta,
+                             double* __restrict__ Z) {
+  int64_t total = n * d;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int t = (int)(i % d);
+    Z[i] = __ddiv_rn((double)X[i], beta.b[t]);
+  }
+}
+
+__global__ void absmax_kernel(const double* __restrict__ Z, int64_t total,
+                              unsigned long long* __restrict__ out) {
+  double m = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(Z[i]));
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void gather_rows_kernel(const double* __restrict__ Z, const int32_t* __restrict__ idx,
+                                   int64_t k, int d, double* __restrict__ C) {
+  int64_t total = k * d;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = i / d;
+    int t = (int)(i % d);
+    C[i] = Z[(int64_t)idx[r] * d + t];
+  }
+}
+
+// One thread per point: argmin over all centres of the exact FP64 distance,
+// screened by float32 distances (two passes over centre tiles in shared memory).
+constexpr int ASSIGN_THREADS = 256;
+constexpr int ASSIGN_TILE = 128;
+
+template <int DM>
+__global__ void __launch_bounds__(ASSIGN_THREADS)
+assign_kernel(const double* __restrict__ Z, int64_t n, int d, const double* __restrict__ C,
+              int64_t k, ScreenBound sb, const int32_t* __restrict__ old_blk,
+              int32_t* __restrict__ blk, unsigned long long* __restrict__ changed) {
+  __shared__ float cf[ASSIGN_TILE * DM];
+  int64_t i = blockIdx.x * (int64_t)ASSIGN_THREADS + threadIdx.x;
+  bool live = i < n;
+  float zf[DM];
+#pragma unroll
+  for (int t = 0; t < DM; ++t) zf[t] = (live && t < d) ? (float)Z[i * d + t] : 0.0f;
+
+  // pass 1: smallest upper bound D32 + margin
+  float best_ub = INFINITY;
+  for (int64_t j0 = 0; j0 < k; j0 += ASSIGN_TILE) {
+    int nt = (int)min((int64_t)ASSIGN_TILE, k - j0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nt * d; e += ASSIGN_THREADS) {
+      int jj = e / d, t = e % d;
+      cf[jj * DM + t] = (float)C[(j0 + jj) * d + t];
+    }
+    __syncthreads();
+    if (live) {
+      for (int jj = 0; jj < nt; ++jj) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int t = 0; t < DM; ++t) {
+          if (t < d) {
+            float df = zf[t] - cf[jj * DM + t];
+            acc = fmaf(df, df, acc);
+          }
+        }
+        float ub = acc + screen_margin(acc, sb);
+        best_ub = fminf(best_ub, ub);
+      }
+    }
+  }
+  // pass 2: exact FP64 distance for every centre whose lower bound can reach best_ub
+  double best = INFINITY;
+  int64_t arg = 0;
+  double zi[DM];
+#pragma unroll
+  for (int t = 0; t < DM; ++t) zi[t] = (live && t < d) ? Z[i * d + t] : 0.0;
+  for (int64_t j0 = 0; j0 < k; j0 += ASSIGN_TILE) {
+    int nt = (int)min((int64_t)ASSIGN_TILE, k - j0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nt * d; e += ASSIGN_THREADS) {
+      int jj = e / d, t = e % d;
+      cf[jj * DM + t] = (float)C[(j0 + jj) * d + t];
+    }
+    __syncthreads();
+    if (live) {
+      for (int jj = 0; jj < nt; ++jj) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int t = 0; t < DM; ++t) {
+          if (t < d) {
+            float df = zf[t] - cf[jj * DM + t];
+            acc = fmaf(df, df, acc);
+          }
+        }
+        float lb = acc - screen_margin(acc, sb);
+        if (lb <= best_ub) {
+          double D = dist2_exact<DM>(zi, C + (j0 + jj) * d, d);
+          if (D < best) {  // strict: ties keep the smaller index
+            best = D;
+            arg = j0 + jj;
+          }
+        }
+      }
+    }
+  }
+  if (live) {
+    int32_t a = (int32_t)arg;
+    if (old_blk && old_blk[i] != a) atomicAdd(changed, 1ull);
+    blk[i] = a;
+  }
+}
+
+__global__ void iota_kernel(int32_t* __restrict__ v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = (int32_t)i;
+}
+
+__global__ void count_kernel(const int32_t* __restrict__ keys, int64_t n,
+                             int64_t* __restrict__ counts) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd((unsigned long long*)&counts[keys[i]], 1ull);
+}
+
+// Mean of each block's members, summed one by one in increasing point index.
+// One thread per (block, dimension).  Empty blocks keep `prev` (if given).
+__global__ void centroid_kernel(const double* __restrict__ Z, int d,
+                                const int64_t* __restrict__ ptr,
+                                const int32_t* __restrict__ pts, int64_t k,
+                                const double* __restrict__ prev, double* __restrict__ C) {
+  int64_t total = k * d;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j = e / d;
+    int t = (int)(e % d);
+    int64_t a = ptr[j], b = ptr[j + 1];
+    if (b == a) {
+      C[e] = prev ? prev[e] : __longlong_as_double(0x7ff8000000000000ll);
+      continue;
+    }
+    double s = 0.0;
+    for (int64_t q = a; q < b; ++q) s = __dadd_rn(s, Z[(int64_t)pts[q] * d + t]);
+    C[e] = __ddiv_rn(s, (double)(b - a));
+  }
+}
+
+__global__ void used_kernel(const int64_t* __restrict__ counts, int64_t k,
+                            int32_t* __restrict__ used) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < k;
+       j += (int64_t)gridDim.x * blockDim.x)
+    used[j] = counts[j] > 0 ? 1 : 0;
+}
+
+// remap: new id of used block j = exclusive prefix of used flags
+__global__ void compact_kernel(const int64_t* __restrict__ ptr_old, const int32_t* __restrict__ used,
+                               const int32_t* __restrict__ newid, int64_t k, int64_t n,
+                               int64_t* __restrict__ ptr_new, int64_t bc_eff) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < k;
+       j += (int64_t)gridDim.x * blockDim.x)
+    if (used[j]) ptr_new[newid[j]] = ptr_old[j];
+  if (blockIdx.x == 0 && threadIdx.x == 0) ptr_new[bc_eff] = n;
+}
+
+__global__ void relabel_kernel(int32_t* __restrict__ blk, int64_t n,
+                               const int32_t* __restrict__ newid) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    blk[i] = newid[blk[i]];
+}
+
+static int grid_for(int64_t work, int threads, int sms) {
+  int64_t g = (work + threads - 1) / threads;
+  int64_t cap = (int64_t)sms * 32;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+int scale_points(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int d, const double*,
+                 const double* h_beta, double* Z, cudaStream_t s) {
+  BetaArg ba;
+  for (int t = 0; t < d; ++t) ba.b[t] = h_beta[t];
+  int g = grid_for(n * d, 256, ctx->num_sms);
+  if (dtype == SBV_F64)
+    scale_kernel<double><<<g, 256, 0, s>>>((const double*)X, n, d, ba, Z);
+  else
+    scale_kernel<float><<<g, 256, 0, s>>>((const float*)X, n, d, ba, Z);
+  SBV_LAUNCH_CHECK(ctx, "scale_kernel");
+  return SBV_OK;
+}
+
+// Upper bound of |coordinate| over Z (n x d), for the float32 screening margin.
+int absmax(sbv_ctx* ctx, const double* Z, int64_t total, double* out, cudaStream_t s) {
+  int st = 0;
+  unsigned long long* d = (unsigned long long*)ws_get(ctx, WS_SMALL, 64, &st);
+  if (!d) return st;
+  SBV_CUDA_TRY(ctx, cudaMemsetAsync(d, 0, 8, s));
+  absmax_kernel<<<grid_for(total, 256, ctx->num_sms), 256, 0, s>>>(Z, total, d);
+  SBV_LAUNCH_CHECK(ctx, "absmax_kernel");
+  unsigned long long h = 0;
+  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(&h, d, 8, cudaMemcpyDeviceToHost, s));
+  SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  double v;
+  memcpy(&v, &h, 8);
+  *out = v;
+  return SBV_OK;
+}
+
+static int launch_assign(sbv_ctx* ctx, const double* Z, int64_t n, int d, const double* C,
+                         int64_t k, ScreenBound sb, const int32_t* old_blk, int32_t* blk,
+                         unsigned long long* changed, cudaStream_t s) {
+  int g = (int)((n + ASSIGN_THREADS - 1) / ASSIGN_THREADS);
+#define SBV_ASSIGN(DM) \
+  assign_kernel<DM><<<g, ASSIGN_THREADS, 0, s>>>(Z, n, d, C, k, sb, old_blk, blk, changed)
+  if (d <= 4) SBV_ASSIGN(4);
+  else if (d <= 8) SBV_ASSIGN(8);
+  else if (d <= 12) SBV_ASSIGN(12);
+  else if (d <= 16) SBV_ASSIGN(16);
+  else if (d <= 24) SBV_ASSIGN(24);
+  else if (d <= 32) SBV_ASSIGN(32);
+  else SBV_ASSIGN(64);
+#undef SBV_ASSIGN
+  SBV_LAUNCH_CHECK(ctx, "assign_kernel");
+  return SBV_OK;
+}
+
+// Sort point ids by block (stable: increasing index inside a block) and build
+// counts and CSR offsets for k blocks.
+static int group_by_block(sbv_ctx* ctx, const int32_t* blk, int64_t n, int64_t k,
+                          int32_t* ids_tmp, int32_t* keys_out, int32_t* pts,
+                          int64_t* counts, int64_t* ptr, cudaStream_t s) {
+  int st = 0;
+  iota_kernel<<<grid_for(n, 256, ctx->num_sms), 256, 0, s>>>(ids_tmp, n);
+  int end_bit = 1;
+  while ((1ll << end_bit) < k) ++end_bit;
+  size_t tb = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, tb, blk, keys_out, ids_tmp, pts, (int)n, 0, end_bit, s);
+  size_t tb2 = 0;
+  cub::DeviceScan::ExclusiveSum(nullptr, tb2, counts, ptr, (int)(k + 1), s);
+  void* tmp = ws_get(ctx, WS_CUB, std::max(tb, tb2), &st);
+  if (!tmp) return st;
+  SBV_CUDA_TRY(ctx, cub::DeviceRadixSort::SortPairs(tmp, tb, blk, keys_out, ids_tmp, pts, (int)n,
+                                                    0, end_bit, s));
+  SBV_CUDA_TRY(ctx, cudaMemsetAsync(counts, 0, (k + 1) * sizeof(int64_t), s));
+  count_kernel<<<grid_for(n, 256, ctx->num_sms), 256, 0, s>>>(blk, n, counts);
+  SBV_LAUNCH_CHECK(ctx, "count_kernel");
+  SBV_CUDA_TRY(ctx, cub::DeviceScan::ExclusiveSum(tmp, tb2, counts, ptr, (int)(k + 1), s));
+  return SBV_OK;
+}
+
+int run_blocking(sbv_ctx* ctx, const double* Z, int64_t n, int d, int64_t bc, int kmeans_iters,
+                 uint64_t seed, int32_t* blk, int64_t* ptr, int32_t* pts, int32_t* rank,
+                 double* centres, int64_t* bc_eff, cudaStream_t s) {
+  int st = 0;
+  // workspace: two centre buffers, old assignment, sort scratch, counts, ptr
+  size_t cbytes = (size_t)bc * d * sizeof(double);
+  char* wsA = (char*)ws_get(ctx, WS_CENTRES, 2 * cbytes + 256, &st);
+  if (!wsA) return st;
+  double* Ca = (double*)wsA;
+  double* Cb = (double*)(wsA + ((cbytes + 255) / 256) * 256);
+  char* wsB = (char*)ws_get(ctx, WS_SORT_A, (size_t)n * 3 * sizeof(int32_t) + 1024, &st);
+  if (!wsB) return st;
+  int32_t* old_blk = (int32_t*)wsB;
+  int32_t* ids_tmp = old_blk + n;
+  int32_t* keys_out = ids_tmp + n;
+  char* wsC = (char*)ws_get(ctx, WS_SORT_B, (size_t)(bc + 1) * (2 * sizeof(int64_t) + 2 * sizeof(int32_t)) + 1024, &st);
+  if (!wsC) return st;
+  int64_t* counts = (int64_t*)wsC;
+  int64_t* ptr_tmp = counts + (bc + 1);
+  int32_t* used = (int32_t*)(ptr_tmp + (bc + 1));
+  int32_t* newid = used + (bc + 1);
+  unsigned long long* changed = (unsigned long long*)ws_get(ctx, WS_SMALL, 64, &st);
+  if (!changed) return st;
+
+  double M = 0.0;
+  if ((st = absmax(ctx, Z, n * d, &M, s))) return st;
+  ScreenBound sb = make_screen(M, d);
+
+  // RAC anchors: first bc entries of a Fisher-Yates shuffle of [0, n)
+  SplitMix64 rng(seed);
+  std::vector<int32_t> anchors(bc);
+  {
+    std::unordered_map<int64_t, int64_t> sw;
+    sw.reserve((size_t)bc * 2);
+    auto get = [&](int64_t i) {
+      auto it = sw.find(i);
+      return it == sw.end() ? i : it->second;
+    };
+    for (int64_t j = 0; j < bc; ++j) {
+      int64_t r = j + (int64_t)rng.below((uint64_t)(n - j));
+      int64_t aj = get(j), ar = get(r);
+      sw[j] = ar;
+      sw[r] = aj;
+      anchors[j] = (int32_t)ar;
+    }
+  }
+  int32_t* d_anchor = newid;  // reuse (bc entries) before compaction needs it
+  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(d_anchor, anchors.data(), bc * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, s));
+  gather_rows_kernel<<<grid_for(bc * d, 256, ctx->num_sms), 256, 0, s>>>(Z, d_anchor, bc, d, Ca);
+  SBV_LAUNCH_CHECK(ctx, "gather_rows_kernel");
+  SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));  // anchors buffer reused below
+
+  if ((st = launch_assign(ctx, Z, n, d, Ca, bc, sb, nullptr, blk, changed, s))) return st;
+  double* C = Ca;
+  double* Cn = Cb;
+  for (int it = 0; it < kmeans_iters; ++it) {
+    if ((st = group_by_block(ctx, blk, n, bc, ids_tmp, keys_out, pts, counts, ptr_tmp, s)))
+      return st;
+    centroid_kernel<<<grid_for(bc * d, 128, ctx->num_sms), 128, 0, s>>>(Z, d, ptr_tmp, pts, bc,
+                                                                         C, Cn);
+    SBV_LAUNCH_CHECK(ctx, "centroid_kernel");
+    std::swap(C, Cn);
+    SBV_CUDA_TRY(ctx, cudaMemcpyAsync(old_blk, blk, n * sizeof(int32_t),
+                                      cudaMemcpyDeviceToDevice, s));
+    SBV_CUDA_TRY(ctx, cudaMemsetAsync(changed, 0, 8, s));
+    if ((st = launch_assign(ctx, Z, n, d, C, bc, sb, old_blk, blk, changed, s))) return st;
+    unsigned long long h_changed = 0;
+    SBV_CUDA_TRY(ctx, cudaMemcpyAsync(&h_changed, changed, 8, cudaMemcpyDeviceToHost, s));
+    SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (h_changed == 0) break;
+  }
+  // final grouping, compaction of empty blocks
+  if ((st = group_by_block(ctx, blk, n, bc, ids_tmp, keys_out, pts, counts, ptr_tmp, s)))
+    return st;
+  used_kernel<<<grid_for(bc, 256, ctx->num_sms), 256, 0, s>>>(counts, bc, used);
+  SBV_LAUNCH_CHECK(ctx, "used_kernel");
+  {
+    size_t tb = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, tb, used, newid, (int)bc, s);
+    void* tmp = ws_get(ctx, WS_CUB, tb, &st);
+    if (!tmp) return st;
+    SBV_CUDA_TRY(ctx, cub::DeviceScan::ExclusiveSum(tmp, tb, used, newid, (int)bc, s));
+  }
+  int32_t last_new = 0, last_used = 0;
+  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(&last_new, newid + bc - 1, 4, cudaMemcpyDeviceToHost, s));
+  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(&last_used, used + bc - 1, 4, cudaMemcpyDeviceToHost, s));
+  SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  int64_t k_eff = (int64_t)last_new + last_used;
+  compact_kernel<<<grid_for(bc, 256, ctx->num_sms), 256, 0, s>>>(ptr_tmp, used, newid, bc, n, ptr,
+                                                                 k_eff);
+  SBV_LAUNCH_CHECK(ctx, "compact_kernel");
+  relabel_kernel<<<grid_for(n, 256, ctx->num_sms), 256, 0, s>>>(blk, n, newid);
+  SBV_LAUNCH_CHECK(ctx, "relabel_kernel");
+  centroid_kernel<<<grid_for(k_eff * d, 128, ctx->num_sms), 128, 0, s>>>(Z, d, ptr, pts, k_eff,
+                                                                         nullptr, centres);
+  SBV_LAUNCH_CHECK(ctx, "centroid_kernel");
+  // random block order: full Fisher-Yates shuffle from the same stream
+  std::vector<int32_t> perm(k_eff), rk(k_eff);
+  for (int64_t j = 0; j < k_eff; ++j) perm[j] = (int32_t)j;
+  for (int64_t j = 0; j + 1 < k_eff; ++j) {
+    int64_t r = j + (int64_t)rng.below((uint64_t)(k_eff - j));
+    std::swap(perm[j], perm[r]);
+  }
+  for (int64_t r = 0; r < k_eff; ++r) rk[perm[r]] = (int32_t)r;
+  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(rank, rk.data(), k_eff * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, s));
+  SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  *bc_eff = k_eff;
+  return SBV_OK;
+}
+
+}  // namespace sbv

@@ -1,0 +1,508 @@
+// Batched Block Vecchia log-likelihood (Alg. 5 per block, Alg. 1 Step 5 for
+// the sum) and block-Vecchia prediction (Sec. 4.2, 5.5): FP64 path.
+//
+// One CTA factors one (theta, block) work item at a time; a persistent grid
+// takes items from an atomic counter.  The item's N = m_i + bs_i points are
+// gathered, the packed lower triangle of the joint covariance of [J; B] is
+// built in shared memory (global scratch when it does not fit) with the
+// observations bordered as row N, and a right-looking Cholesky of the first N
+// columns leaves L on the diagonal/below and w = L^{-1} y in row N.  Then
+//   l_i = -1/2 [ bs log 2pi + 2 sum_{t>=m_i} log L_tt + sum_{t>=m_i} w_t^2 ],
+// which is the Schur-complement chain of Alg. 5 (POTRF of Sigma^con, TRSM,
+// GEMM, Schur with Sigma^lk, POTRF, TRSV, dot, log-det) done in one pass.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "block_common.cuh"
+#include "sbv_internal.cuh"
+
+namespace sbv {
+
+constexpr int LL_THREADS = 256;
+
+struct LoglikArgs {
+  const void* X;
+  int dtype;
+  const double* y;
+  int64_t n;
+  int d;
+  const int64_t* ptr;
+  const int32_t* pts;
+  const int32_t* nbr;
+  const int32_t* cnt;
+  int64_t bc;
+  int m;
+  const ThetaDev* theta;
+  int B;
+  int nu2;
+  int ncap;                // largest N the launch can hold
+  double* terms;           // B x bc
+  int32_t* status;         // B x bc or NULL
+  DevStatus* dstat;
+  unsigned int* counter;   // work counter
+  double* gmat;            // global scratch (one matrix per CTA) or NULL
+  size_t gmat_stride;      // doubles per CTA slice
+};
+
+template <typename T>
+__device__ __forceinline__ double ld_x(const void* X, int64_t i) {
+  return (double)((const T*)X)[i];
+}
+
+// Gather the N points of an item into u[t][p] = x_p,t / beta_t and yv[p].
+// Point p < mb is neighbour p of the block, p >= mb is member p - mb.
+__device__ void gather_item(const LoglikArgs& a, int64_t blk, int mb, int N,
+                            const ThetaDev& th, double* u, int ustride, double* yv) {
+  const int d = a.d;
+  const int64_t base = a.ptr[blk];
+  for (int e = threadIdx.x; e < N * d; e += blockDim.x) {
+    int p = e / d, t = e - p * d;
+    int64_t id = p < mb ? (int64_t)a.nbr[blk * a.m + p] : (int64_t)a.pts[base + (p - mb)];
+    double x = a.dtype == SBV_F64 ? ld_x<double>(a.X, id * d + t) : ld_x<float>(a.X, id * d + t);
+    u[t * ustride + p] = x * th.inv_beta[t];
+  }
+  for (int p = threadIdx.x; p < N; p += blockDim.x) {
+    int64_t id = p < mb ? (int64_t)a.nbr[blk * a.m + p] : (int64_t)a.pts[base + (p - mb)];
+    yv[p] = a.y[id];
+  }
+}
+
+// Packed lower triangle of the joint covariance, rows 0..N-1, plus row N = yv.
+__device__ void build_cov(const double* u, int ustride, int d, int N, const ThetaDev& th,
+                          int nu2, const double* yv, double* A) {
+  const int total = N * (N + 1) / 2;
+  int i = 0, j = threadIdx.x;
+  while (j > i) { j -= i + 1; ++i; }
+  for (int l = threadIdx.x; l < total; l += blockDim.x) {
+    double s = 0.0;
+    for (int t = 0; t < d; ++t) {
+      double df = u[t * ustride + i] - u[t * ustride + j];
+      s = fma(df, df, s);
+    }
+    double K = th.sigma2 * matern64(sqrt(s), nu2);
+    if (i == j) K += th.tau2;
+    A[l] = K;
+    j += blockDim.x;
+    while (j > i) { j -= i + 1; ++i; }
+  }
+  const int rowN = N * (N + 1) / 2;
+  for (int p = threadIdx.x; p < N; p += blockDim.x) A[rowN + p] = yv[p];
+}
+
+// Right-looking Cholesky of columns 0..kend-1 of the (N+1)-row packed matrix
+// (row N is the bordered right-hand side).  Returns false if a pivot is not
+// positive; all threads return the same value.
+__device__ bool chol_columns(double* A, int N, int kend, double* s_scalar, int* s_flag) {
+  for (int k = 0; k < kend; ++k) {
+    if (threadIdx.x == 0) {
+      double piv = A[tri(k, k)];
+      if (!(piv > 0.0) || !isfinite(piv)) {
+        *s_flag = 1;
+      } else {
+        double L = sqrt(piv);
+        A[tri(k, k)] = L;
+        *s_scalar = 1.0 / L;
+      }
+    }
+    __syncthreads();
+    if (*s_flag) return false;
+    const double inv = *s_scalar;
+    for (int i = k + 1 + threadIdx.x; i <= N; i += blockDim.x) A[tri(i, k)] *= inv;
+    __syncthreads();
+    // trailing update of rows k+1..N, columns k+1..min(i, N-1)
+    const int T = N - 1 - k;
+    const int tri_n = T * (T + 1) / 2;
+    const int total = tri_n + T;
+    int ii = 0, jj = threadIdx.x;
+    while (jj > ii) { jj -= ii + 1; ++ii; }
+    for (int l = threadIdx.x; l < total; l += blockDim.x) {
+      int i, j;
+      if (l < tri_n) {
+        i = k + 1 + ii;
+        j = k + 1 + jj;
+      } else {
+        i = N;
+        j = k + 1 + (l - tri_n);
+      }
+      A[tri(i, j)] -= A[tri(i, k)] * A[tri(j, k)];
+      jj += blockDim.x;
+      while (jj > ii) { jj -= ii + 1; ++ii; }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// Deterministic CTA sum of v over threads (fixed tree).
+__device__ double cta_sum(double v, double* red) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < nw; ++q) s += red[q];
+  return s;  // valid on thread 0
+}
+
+__global__ void __launch_bounds__(LL_THREADS)
+loglik_fp64_kernel(LoglikArgs a) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ double s_scalar;
+  __shared__ int s_flag;
+  __shared__ unsigned int s_item;
+  __shared__ double red[LL_THREADS / 32];
+  const int d = a.d;
+  const int ustride = a.ncap + 1;
+  double* u = sm;                               // d x (ncap+1)
+  double* yv = u + (size_t)d * ustride;         // ncap+1
+  double* A = a.gmat ? a.gmat + (size_t)blockIdx.x * a.gmat_stride : yv + ustride;
+  const unsigned int total = (unsigned int)(a.bc * a.B);
+  const double log2pi = 1.8378770664093454836;
+
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const unsigned int item = s_item;
+    if (item >= total) break;
+    const int th_i = (int)(item / a.bc);
+    const int64_t blk = (int64_t)(item % a.bc);
+    const ThetaDev& th = a.theta[th_i];
+    const int bs = (int)(a.ptr[blk + 1] - a.ptr[blk]);
+    const int mb = a.cnt[blk];
+    const int N = mb + bs;
+    if (N > a.ncap) {
+      if (threadIdx.x == 0) {
+        a.terms[item] = __longlong_as_double(0x7ff8000000000000ll);
+        if (a.status) a.status[item] = SBV_EUNSUPPORTED;
+        record_failure(a.dstat, SBV_EUNSUPPORTED, (int)blk, th_i);
+      }
+      __syncthreads();
+      continue;
+    }
+    gather_item(a, blk, mb, N, th, u, ustride, yv);
+    __syncthreads();
+    build_cov(u, ustride, d, N, th, a.nu2, yv, A);
+    if (threadIdx.x == 0) s_flag = 0;
+    __syncthreads();
+    bool ok = chol_columns(A, N, N, &s_scalar, &s_flag);
+    double v = 0.0;
+    if (ok) {
+      for (int t = mb + threadIdx.x; t < N; t += blockDim.x) {
+        double w = A[tri(N, t)];
+        v += 2.0 * log(A[tri(t, t)]) + w * w;
+      }
+    }
+    double s = cta_sum(v, red);
+    if (threadIdx.x == 0) {
+      if (ok) {
+        a.terms[item] = -0.5 * ((double)bs * log2pi + s);
+        if (a.status) a.status[item] = 0;
+      } else {
+        a.terms[item] = __longlong_as_double(0x7ff8000000000000ll);
+        if (a.status) a.status[item] = SBV_ENOTSPD;
+        record_failure(a.dstat, SBV_ENOTSPD, (int)blk, th_i);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ll[b] = sum_i terms[b, i]: each thread adds a fixed strided subset in order,
+// then a fixed tree; identical results on every call.
+__global__ void reduce_terms_kernel(const double* __restrict__ terms, int64_t bc,
+                                    double* __restrict__ ll) {
+  __shared__ double red[32];
+  const double* t = terms + (int64_t)blockIdx.x * bc;
+  double v = 0.0;
+  for (int64_t i = threadIdx.x; i < bc; i += blockDim.x) v += t[i];
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) ll[blockIdx.x] = w;
+  }
+}
+
+// Largest m_i + bs_i over blocks.
+__global__ void max_n_kernel(const int64_t* __restrict__ ptr, const int32_t* __restrict__ cnt,
+                             int64_t bc, int* __restrict__ out) {
+  int v = 0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < bc;
+       j += (int64_t)gridDim.x * blockDim.x)
+    v = max(v, (int)(ptr[j + 1] - ptr[j]) + cnt[j]);
+  for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, v);
+}
+
+static std::vector<ThetaDev> derive_theta(const double* h, int B, int d) {
+  std::vector<ThetaDev> out(B);
+  for (int b = 0; b < B; ++b) {
+    const double* r = h + (size_t)b * (2 + d);
+    memset(&out[b], 0, sizeof(ThetaDev));
+    out[b].sigma2 = r[0];
+    out[b].tau2 = r[1];
+    for (int t = 0; t < d; ++t) out[b].inv_beta[t] = 1.0 / r[2 + t];
+  }
+  return out;
+}
+
+// Copy derived theta rows to the device.  A pageable-to-device cudaMemcpyAsync
+// stages the bytes before returning, so the host vector may die right away
+// and no host synchronisation is needed.
+static int upload_theta(sbv_ctx* ctx, const double* h, int B, int d, ThetaDev** out,
+                        cudaStream_t s) {
+  int st = 0;
+  std::vector<ThetaDev> v = derive_theta(h, B, d);
+  size_t bytes = v.size() * sizeof(ThetaDev);
+  ThetaDev* dth = (ThetaDev*)ws_get(ctx, WS_PARAMS, bytes, &st);
+  if (!dth) return st;
+  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(dth, v.data(), bytes, cudaMemcpyHostToDevice, s));
+  *out = dth;
+  return SBV_OK;
+}
+
+// Largest N over blocks (one small reduction and a host read per call; the
+// kernels still check every item against the capacity they were launched with).
+static int structure_max_n(sbv_ctx* ctx, const int64_t* ptr, const int32_t* cnt, int64_t bc,
+                           int* out, cudaStream_t s) {
+  int st = 0;
+  int* d = (int*)ws_get(ctx, WS_SMALL, 64, &st);
+  if (!d) return st;
+  SBV_CUDA_TRY(ctx, cudaMemsetAsync(d, 0, 4, s));
+  int g = (int)std::min<int64_t>((bc + 255) / 256, (int64_t)ctx->num_sms * 8);
+  max_n_kernel<<<std::max(g, 1), 256, 0, s>>>(ptr, cnt, bc, d);
+  SBV_LAUNCH_CHECK(ctx, "max_n_kernel");
+  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(out, d, 4, cudaMemcpyDeviceToHost, s));
+  SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  return SBV_OK;
+}
+
+int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a, int nmax, cudaStream_t s);
+
+int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n, int d,
+               const int64_t* ptr, const int32_t* pts, const int32_t* nbr, const int32_t* cnt,
+               int64_t bc, int m, const double* h_theta, int B, int nu2, int precision,
+               double* ll, double* terms, int32_t* status, cudaStream_t s) {
+  int st = 0;
+  if ((uint64_t)bc * (uint64_t)B >= 0xffffffffull)
+    return fail(ctx, SBV_EUNSUPPORTED, "bc*B too large");
+  int nmax = 0;
+  if ((st = structure_max_n(ctx, ptr, cnt, bc, &nmax, s))) return st;
+  if (nmax > SBV_MAX_BLOCK_N)
+    return fail(ctx, SBV_EUNSUPPORTED, "a block has m_i + bs_i = %d > %d", nmax, SBV_MAX_BLOCK_N);
+  ThetaDev* dth = nullptr;
+  if ((st = upload_theta(ctx, h_theta, B, d, &dth, s))) return st;
+  if (!terms) {
+    terms = (double*)ws_get(ctx, WS_TERMS, (size_t)B * bc * sizeof(double), &st);
+    if (!terms) return st;
+  }
+  unsigned int* counter = (unsigned int*)ws_get(ctx, WS_SMALL, 64, &st);
+  if (!counter) return st;
+  counter += 4;  // first words hold the max-N scratch
+  SBV_CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
+
+  LoglikArgs a;
+  a.X = X;
+  a.dtype = dtype;
+  a.y = y;
+  a.n = n;
+  a.d = d;
+  a.ptr = ptr;
+  a.pts = pts;
+  a.nbr = nbr;
+  a.cnt = cnt;
+  a.bc = bc;
+  a.m = m;
+  a.theta = dth;
+  a.B = B;
+  a.nu2 = nu2;
+  a.ncap = nmax;
+  a.terms = terms;
+  a.status = status;
+  a.dstat = ctx->d_status;
+  a.counter = counter;
+  a.gmat = nullptr;
+  a.gmat_stride = 0;
+
+  if (precision == SBV_PREC_MIXED) {
+    if ((st = launch_loglik_mixed(ctx, a, nmax, s))) return st;
+  } else {
+    const size_t ub = (size_t)(d + 1) * (nmax + 1) * sizeof(double);
+    const size_t mat = (size_t)(nmax + 1) * (nmax + 2) / 2 * sizeof(double);
+    size_t smem = ub + mat;
+    int grid = 0;
+    if (smem + 1024 <= ctx->smem_optin) {
+      int per_sm = (int)std::max<size_t>(1, (228 * 1024) / (smem + 2048));
+      grid = ctx->num_sms * std::min(per_sm, 4);
+    } else {
+      smem = ub;
+      if (smem + 1024 > ctx->smem_optin)
+        return fail(ctx, SBV_EUNSUPPORTED, "d=%d with N=%d exceeds shared memory", d, nmax);
+      grid = ctx->num_sms * 2;
+      size_t stride = (mat / sizeof(double) + 31) & ~(size_t)31;
+      double* g = (double*)ws_get(ctx, WS_MATRIX, stride * grid * sizeof(double), &st);
+      if (!g) return st;
+      a.gmat = g;
+      a.gmat_stride = stride;
+    }
+    int64_t items = bc * (int64_t)B;
+    if (grid > items) grid = (int)items;
+    SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_fp64_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    loglik_fp64_kernel<<<grid, LL_THREADS, smem, s>>>(a);
+    SBV_LAUNCH_CHECK(ctx, "loglik_fp64_kernel");
+  }
+  reduce_terms_kernel<<<B, 1024, 0, s>>>(terms, bc, ll);
+  SBV_LAUNCH_CHECK(ctx, "reduce_terms_kernel");
+  return SBV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Prediction: one test point per item, conditioned on its m nearest training
+// points; the joint matrix is [J; *] with the bordered row (y_J, 0).
+// ---------------------------------------------------------------------------
+struct PredictArgs {
+  const void* X;
+  const void* Xt;
+  int dtype;
+  const double* y;
+  int d;
+  const int32_t* nbr;   // nt x m
+  int64_t nt;
+  int m;
+  const ThetaDev* theta;
+  int nu2;
+  double* mean;
+  double* var;
+  double* var_latent;
+  DevStatus* dstat;
+  unsigned int* counter;
+  double* gmat;
+  size_t gmat_stride;
+};
+
+__global__ void __launch_bounds__(LL_THREADS)
+predict_fp64_kernel(PredictArgs a) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ double s_scalar;
+  __shared__ int s_flag;
+  __shared__ unsigned int s_item;
+  __shared__ double red[LL_THREADS / 32];
+  const int d = a.d, m = a.m, N = m + 1;
+  const int ustride = N + 1;
+  double* u = sm;
+  double* yv = u + (size_t)d * ustride;
+  double* A = a.gmat ? a.gmat + (size_t)blockIdx.x * a.gmat_stride : yv + ustride;
+  const ThetaDev& th = a.theta[0];
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const unsigned int item = s_item;
+    if (item >= a.nt) break;
+    for (int e = threadIdx.x; e < N * d; e += blockDim.x) {
+      int p = e / d, t = e - p * d;
+      double x;
+      if (p < m) {
+        int64_t id = a.nbr[(int64_t)item * m + p];
+        x = a.dtype == SBV_F64 ? ld_x<double>(a.X, id * d + t) : ld_x<float>(a.X, id * d + t);
+      } else {
+        x = a.dtype == SBV_F64 ? ld_x<double>(a.Xt, (int64_t)item * d + t)
+                               : ld_x<float>(a.Xt, (int64_t)item * d + t);
+      }
+      u[t * ustride + p] = x * th.inv_beta[t];
+    }
+    for (int p = threadIdx.x; p < N; p += blockDim.x)
+      yv[p] = p < m ? a.y[a.nbr[(int64_t)item * m + p]] : 0.0;
+    __syncthreads();
+    build_cov(u, ustride, d, N, th, a.nu2, yv, A);
+    if (threadIdx.x == 0) s_flag = 0;
+    __syncthreads();
+    bool ok = chol_columns(A, N, m, &s_scalar, &s_flag);
+    double v = 0.0;
+    if (ok)
+      for (int t = threadIdx.x; t < m; t += blockDim.x) v += A[tri(m, t)] * A[tri(N, t)];
+    double s = cta_sum(v, red);
+    if (threadIdx.x == 0) {
+      if (ok) {
+        double var = A[tri(m, m)];
+        a.mean[item] = s;
+        a.var[item] = var;
+        a.var_latent[item] = var - th.tau2;
+      } else {
+        double nan = __longlong_as_double(0x7ff8000000000000ll);
+        a.mean[item] = nan;
+        a.var[item] = nan;
+        a.var_latent[item] = nan;
+        record_failure(a.dstat, SBV_ENOTSPD, (int)item, 0);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+int run_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n, int d,
+                const void* Xt, int64_t nt, const int32_t* nbr, int m, const double* h_theta,
+                int nu2, int precision, double* mean, double* var, double* var_latent,
+                cudaStream_t s) {
+  (void)n;
+  (void)precision;
+  int st = 0;
+  ThetaDev* dth = nullptr;
+  if ((st = upload_theta(ctx, h_theta, 1, d, &dth, s))) return st;
+  unsigned int* counter = (unsigned int*)ws_get(ctx, WS_SMALL, 64, &st);
+  if (!counter) return st;
+  counter += 4;
+  SBV_CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
+  PredictArgs a;
+  a.X = X;
+  a.Xt = Xt;
+  a.dtype = dtype;
+  a.y = y;
+  a.d = d;
+  a.nbr = nbr;
+  a.nt = nt;
+  a.m = m;
+  a.theta = dth;
+  a.nu2 = nu2;
+  a.mean = mean;
+  a.var = var;
+  a.var_latent = var_latent;
+  a.dstat = ctx->d_status;
+  a.counter = counter;
+  a.gmat = nullptr;
+  a.gmat_stride = 0;
+  const int N = m + 1;
+  const size_t ub = (size_t)(d + 1) * (N + 1) * sizeof(double);
+  const size_t mat = (size_t)(N + 1) * (N + 2) / 2 * sizeof(double);
+  size_t smem = ub + mat;
+  int grid;
+  if (smem + 1024 <= ctx->smem_optin) {
+    int per_sm = (int)std::max<size_t>(1, (228 * 1024) / (smem + 2048));
+    grid = ctx->num_sms * std::min(per_sm, 4);
+  } else {
+    smem = ub;
+    if (smem + 1024 > ctx->smem_optin)
+      return fail(ctx, SBV_EUNSUPPORTED, "d=%d with m_pred=%d exceeds shared memory", d, m);
+    grid = ctx->num_sms * 2;
+    size_t stride = (mat / sizeof(double) + 31) & ~(size_t)31;
+    double* g = (double*)ws_get(ctx, WS_MATRIX, stride * grid * sizeof(double), &st);
+    if (!g) return st;
+    a.gmat = g;
+    a.gmat_stride = stride;
+  }
+  if (grid > nt) grid = (int)nt;
+  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(predict_fp64_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  predict_fp64_kernel<<<grid, LL_THREADS, smem, s>>>(a);
+  SBV_LAUNCH_CHECK(ctx, "predict_fp64_kernel");
+  return SBV_OK;
+}
+
+}  // namespace sbv

@@ -1,0 +1,245 @@
+// C ABI of libsbv.so: contexts, argument checks, workspace, and the entry
+// points declared in include/sbv.h.  Every computation is delegated to the
+// CUDA kernels of the other translation units.
+#include <stdarg.h>
+#include <math.h>
+#include <string.h>
+
+#include "sbv_internal.cuh"
+
+namespace sbv {
+
+int fail(sbv_ctx* ctx, int code, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return code;
+}
+
+int cuda_fail(sbv_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, SBV_ECUDA, "%s: %s (%s)", where, cudaGetErrorName(e),
+              cudaGetErrorString(e));
+}
+
+void* ws_get(sbv_ctx* ctx, int slot, size_t bytes, int* status) {
+  DevBuf& b = ctx->ws[slot];
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return b.p;
+  if (b.p) {
+    cudaDeviceSynchronize();
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  size_t want = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *status = fail(ctx, SBV_ENOMEM, "workspace allocation of %zu bytes failed: %s", want,
+                   cudaGetErrorString(e));
+    return nullptr;
+  }
+  b.bytes = want;
+  return b.p;
+}
+
+}  // namespace sbv
+
+using namespace sbv;
+
+extern "C" int sbv_version(void) { return 100; }
+
+extern "C" int sbv_create(sbv_ctx** out, int device) {
+  if (!out) return SBV_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return SBV_ECUDA;
+  if (device < 0 || device >= ndev) return SBV_EINVAL;
+  sbv_ctx* ctx = new sbv_ctx();
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete ctx;
+    return SBV_ECUDA;
+  }
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  ctx->smem_optin = (size_t)optin;
+  if (cudaMalloc(&ctx->d_status, sizeof(DevStatus)) != cudaSuccess ||
+      cudaMemset(ctx->d_status, 0, sizeof(DevStatus)) != cudaSuccess) {
+    delete ctx;
+    return SBV_ENOMEM;
+  }
+  *out = ctx;
+  return SBV_OK;
+}
+
+extern "C" void sbv_destroy(sbv_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto& b : ctx->ws)
+    if (b.p) cudaFree(b.p);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  delete ctx;
+}
+
+extern "C" const char* sbv_last_error(const sbv_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+static int check_common(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_t d) {
+  if (!ctx) return SBV_EINVAL;
+  if (!X) return fail(ctx, SBV_EINVAL, "X is null");
+  if (dtype != SBV_F64 && dtype != SBV_F32) return fail(ctx, SBV_EINVAL, "bad dtype %d", dtype);
+  if (n < 1 || n > (int64_t)INT32_MAX - 1) return fail(ctx, SBV_EINVAL, "n=%lld out of range", (long long)n);
+  if (d < 1 || d > SBV_MAX_DIM) return fail(ctx, SBV_EINVAL, "d=%d outside [1,%d]", d, SBV_MAX_DIM);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, SBV_ECUDA, "cudaSetDevice failed");
+  return SBV_OK;
+}
+
+static int check_beta(sbv_ctx* ctx, const double* beta, int d, const char* name) {
+  if (!beta) return fail(ctx, SBV_EINVAL, "%s is null", name);
+  for (int t = 0; t < d; ++t)
+    if (!(beta[t] > 0.0) || !isfinite(beta[t]))
+      return fail(ctx, SBV_EINVAL, "%s[%d]=%g must be positive and finite", name, t, beta[t]);
+  return SBV_OK;
+}
+
+static int check_theta(sbv_ctx* ctx, const double* theta, int B, int d) {
+  if (!theta) return fail(ctx, SBV_EINVAL, "theta is null");
+  if (B < 1) return fail(ctx, SBV_EINVAL, "B=%d must be >= 1", B);
+  for (int b = 0; b < B; ++b) {
+    const double* r = theta + (size_t)b * (2 + d);
+    if (!(r[0] > 0.0) || !isfinite(r[0]))
+      return fail(ctx, SBV_EINVAL, "theta[%d]: sigma^2=%g must be positive", b, r[0]);
+    if (!(r[1] >= 0.0) || !isfinite(r[1]))
+      return fail(ctx, SBV_EINVAL, "theta[%d]: tau^2=%g must be >= 0", b, r[1]);
+    for (int t = 0; t < d; ++t)
+      if (!(r[2 + t] > 0.0) || !isfinite(r[2 + t]))
+        return fail(ctx, SBV_EINVAL, "theta[%d]: beta_%d=%g must be positive", b, t + 1, r[2 + t]);
+  }
+  return SBV_OK;
+}
+
+static bool nu_ok(int nu2) { return nu2 == 1 || nu2 == 3 || nu2 == 5 || nu2 == 7; }
+
+extern "C" int sbv_blocking(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_t d,
+                            const double* beta_scale, int64_t bc, int32_t kmeans_iters,
+                            uint64_t seed, int32_t* blk, int64_t* ptr, int32_t* pts,
+                            int32_t* rank, double* centres, int64_t* bc_eff, void* stream) {
+  int st = check_common(ctx, X, dtype, n, d);
+  if (st) return st;
+  if ((st = check_beta(ctx, beta_scale, d, "beta_scale"))) return st;
+  if (bc < 1 || bc > n) return fail(ctx, SBV_EINVAL, "bc=%lld outside [1, n]", (long long)bc);
+  if (kmeans_iters < 0) return fail(ctx, SBV_EINVAL, "kmeans_iters must be >= 0");
+  if (!blk || !ptr || !pts || !rank || !centres || !bc_eff)
+    return fail(ctx, SBV_EINVAL, "null output pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  double* Z = (double*)ws_get(ctx, WS_Z, (size_t)n * d * sizeof(double), &st);
+  if (!Z) return st;
+  if ((st = scale_points(ctx, X, dtype, n, d, nullptr, beta_scale, Z, s))) return st;
+  return run_blocking(ctx, Z, n, d, bc, kmeans_iters, seed, blk, ptr, pts, rank, centres,
+                      bc_eff, s);
+}
+
+extern "C" int sbv_knn(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_t d,
+                       const double* beta_scale, const int64_t* ptr, const int32_t* pts,
+                       const int32_t* rank, const double* centres, int64_t bc, int32_t m,
+                       int32_t* nbr, int32_t* cnt, void* stream) {
+  int st = check_common(ctx, X, dtype, n, d);
+  if (st) return st;
+  if ((st = check_beta(ctx, beta_scale, d, "beta_scale"))) return st;
+  if (bc < 1 || bc > n) return fail(ctx, SBV_EINVAL, "bc=%lld outside [1, n]", (long long)bc);
+  if (m < 0) return fail(ctx, SBV_EINVAL, "m=%d must be >= 0", m);
+  if (m > SBV_MAX_BLOCK_N - 1) return fail(ctx, SBV_EUNSUPPORTED, "m=%d above %d", m, SBV_MAX_BLOCK_N - 1);
+  if (!ptr || !pts || !rank || !centres || !cnt || (m > 0 && !nbr))
+    return fail(ctx, SBV_EINVAL, "null pointer argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  double* Z = (double*)ws_get(ctx, WS_Z, (size_t)n * d * sizeof(double), &st);
+  if (!Z) return st;
+  if ((st = scale_points(ctx, X, dtype, n, d, nullptr, beta_scale, Z, s))) return st;
+  return run_knn(ctx, Z, n, d, ptr, pts, rank, centres, bc, m, nbr, cnt, s);
+}
+
+extern "C" int sbv_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y,
+                          int64_t n, int32_t d, const int64_t* ptr, const int32_t* pts,
+                          const int32_t* nbr, const int32_t* cnt, int64_t bc, int32_t m,
+                          const double* theta, int32_t B, int32_t nu2, int32_t precision,
+                          double* ll, double* block_terms, int32_t* status, void* stream) {
+  int st = check_common(ctx, X, dtype, n, d);
+  if (st) return st;
+  if (!y || !ptr || !pts || !cnt || !ll || (m > 0 && !nbr))
+    return fail(ctx, SBV_EINVAL, "null pointer argument");
+  if (bc < 1 || bc > n) return fail(ctx, SBV_EINVAL, "bc=%lld outside [1, n]", (long long)bc);
+  if (m < 0) return fail(ctx, SBV_EINVAL, "m=%d must be >= 0", m);
+  if ((st = check_theta(ctx, theta, B, d))) return st;
+  if (!nu_ok(nu2)) return fail(ctx, SBV_EINVAL, "nu2=%d not in {1,3,5,7}", nu2);
+  if (precision != SBV_PREC_FP64 && precision != SBV_PREC_MIXED)
+    return fail(ctx, SBV_EINVAL, "precision=%d unknown", precision);
+  return run_loglik(ctx, X, dtype, y, n, d, ptr, pts, nbr, cnt, bc, m, theta, B, nu2,
+                    precision, ll, block_terms, status, (cudaStream_t)stream);
+}
+
+extern "C" int sbv_sync_status(sbv_ctx* ctx, void* stream) {
+  if (!ctx) return SBV_EINVAL;
+  cudaSetDevice(ctx->device);
+  DevStatus h;
+  cudaStream_t s = (cudaStream_t)stream;
+  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(&h, ctx->d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
+  SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  SBV_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(DevStatus), s));
+  SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  if (h.code == SBV_ENOTSPD)
+    return fail(ctx, SBV_ENOTSPD,
+                "%d matrices not positive definite; first: item %d of parameter row %d",
+                h.count, h.item, h.theta);
+  if (h.code != 0)
+    return fail(ctx, h.code, "device reported code %d at item %d", h.code, h.item);
+  return SBV_OK;
+}
+
+extern "C" int sbv_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y,
+                           int64_t n, int32_t d, const void* Xtest, int64_t ntest,
+                           const double* beta_scale, int32_t m_pred, const double* theta,
+                           int32_t nu2, int32_t precision, double* mean, double* var,
+                           double* var_latent, int32_t* nbr, void* stream) {
+  int st = check_common(ctx, X, dtype, n, d);
+  if (st) return st;
+  if (!y || !Xtest || !mean || !var || !var_latent)
+    return fail(ctx, SBV_EINVAL, "null pointer argument");
+  if (ntest < 1 || ntest > (int64_t)INT32_MAX - 1) return fail(ctx, SBV_EINVAL, "ntest out of range");
+  if ((st = check_beta(ctx, beta_scale, d, "beta_scale"))) return st;
+  if (m_pred < 1 || m_pred > n) return fail(ctx, SBV_EINVAL, "m_pred=%d outside [1, n]", m_pred);
+  if (m_pred > SBV_MAX_BLOCK_N - 1)
+    return fail(ctx, SBV_EUNSUPPORTED, "m_pred=%d above %d", m_pred, SBV_MAX_BLOCK_N - 1);
+  if ((st = check_theta(ctx, theta, 1, d))) return st;
+  if (!nu_ok(nu2)) return fail(ctx, SBV_EINVAL, "nu2=%d not in {1,3,5,7}", nu2);
+  if (precision != SBV_PREC_FP64 && precision != SBV_PREC_MIXED)
+    return fail(ctx, SBV_EINVAL, "precision=%d unknown", precision);
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t zbytes = (size_t)(n + ntest) * d * sizeof(double);
+  double* Z = (double*)ws_get(ctx, WS_Z, zbytes, &st);
+  if (!Z) return st;
+  double* Zt = Z + (size_t)n * d;
+  if ((st = scale_points(ctx, X, dtype, n, d, nullptr, beta_scale, Z, s))) return st;
+  if ((st = scale_points(ctx, Xtest, dtype, ntest, d, nullptr, beta_scale, Zt, s))) return st;
+  int32_t* knbr = nbr;
+  if (!knbr) {
+    knbr = (int32_t*)ws_get(ctx, WS_EXTRA, (size_t)ntest * m_pred * sizeof(int32_t), &st);
+    if (!knbr) return st;
+  }
+  if ((st = run_knn_all(ctx, Z, n, d, Zt, ntest, m_pred, knbr, s))) return st;
+  if ((st = run_predict(ctx, X, dtype, y, n, d, Xtest, ntest, knbr, m_pred, theta, nu2,
+                        precision, mean, var, var_latent, s)))
+    return st;
+  SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  return sbv_sync_status(ctx, stream);
+}

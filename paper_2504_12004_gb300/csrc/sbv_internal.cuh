@@ -1,0 +1,100 @@
+// Internal declarations shared by the translation units of libsbv.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string>
+#include <vector>
+
+#include "sbv.h"
+
+namespace sbv {
+
+// Device-side error record written by kernels (first failure wins).
+struct DevStatus {
+  int32_t code;      // 0 or SBV_ENOTSPD / SBV_ETIMEOUT
+  int32_t item;      // block or test-point index of the first failure
+  int32_t theta;     // parameter row of the first failure
+  int32_t count;     // number of failures
+};
+
+// Grow-only device buffer owned by the context.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace sbv
+
+struct sbv_ctx {
+  int device = 0;
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  std::string err;
+  sbv::DevStatus* d_status = nullptr;  // device record
+  sbv::DevBuf ws[16];                  // named workspace slots
+};
+
+namespace sbv {
+
+enum WsSlot {
+  WS_Z = 0,       // scaled coordinates
+  WS_SORT_A,      // sort keys / values
+  WS_SORT_B,
+  WS_SORT_C,
+  WS_SORT_D,
+  WS_CUB,         // cub temporary storage
+  WS_SMALL,       // counters, flags
+  WS_PARAMS,      // per-theta derived parameters
+  WS_TERMS,       // block terms when the caller passes NULL
+  WS_ORDER,       // rank-ordered point list
+  WS_MATRIX,      // global-memory matrices for blocks too large for shared memory
+  WS_CENTRES,
+  WS_EXTRA,
+  WS_COUNT
+};
+
+int fail(sbv_ctx* ctx, int code, const char* fmt, ...);
+int cuda_fail(sbv_ctx* ctx, cudaError_t e, const char* where);
+void* ws_get(sbv_ctx* ctx, int slot, size_t bytes, int* status);
+
+#define SBV_CUDA_TRY(ctx, call)                                     \
+  do {                                                              \
+    cudaError_t e_ = (call);                                        \
+    if (e_ != cudaSuccess) return ::sbv::cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+#define SBV_LAUNCH_CHECK(ctx, what)                                 \
+  do {                                                              \
+    cudaError_t e_ = cudaGetLastError();                            \
+    if (e_ != cudaSuccess) return ::sbv::cuda_fail(ctx, e_, what);  \
+  } while (0)
+
+// ---- launchers implemented in the .cu files ----
+// scaling / blocking
+int scale_points(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int d,
+                 const double* d_inv_unused, const double* h_beta, double* Z,
+                 cudaStream_t s);
+int run_blocking(sbv_ctx* ctx, const double* Z, int64_t n, int d, int64_t bc,
+                 int kmeans_iters, uint64_t seed, int32_t* blk, int64_t* ptr,
+                 int32_t* pts, int32_t* rank, double* centres, int64_t* bc_eff,
+                 cudaStream_t s);
+// kNN
+int run_knn(sbv_ctx* ctx, const double* Z, int64_t n, int d, const int64_t* ptr,
+            const int32_t* pts, const int32_t* rank, const double* centres,
+            int64_t bc, int m, int32_t* nbr, int32_t* cnt, cudaStream_t s);
+int run_knn_all(sbv_ctx* ctx, const double* Z, int64_t n, int d,
+                const double* Q, int64_t nq, int m, int32_t* nbr, cudaStream_t s);
+// likelihood and prediction
+int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n,
+               int d, const int64_t* ptr, const int32_t* pts, const int32_t* nbr,
+               const int32_t* cnt, int64_t bc, int m, const double* h_theta, int B,
+               int nu2, int precision, double* ll, double* terms, int32_t* status,
+               cudaStream_t s);
+int run_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n,
+                int d, const void* Xt, int64_t nt, const int32_t* nbr, int m,
+                const double* h_theta, int nu2, int precision, double* mean,
+                double* var, double* var_latent, cudaStream_t s);
+
+}  // namespace sbv

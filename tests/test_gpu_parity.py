@@ -1,0 +1,287 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Integer outputs (blocks, order, neighbours) must be bit-identical; FP64
+likelihood terms must agree to |dl|/n <= 1e-9; mixed precision to 1e-6.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import prng, sbv
+from synth.inputs import uniform_points, standard_normal, workload
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-9    # |dl| / n, FP64 path
+TOL_MIXED = 1e-6   # |dl| / n, mixed path
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2504_12004_gb300 import build, Context
+    build.build()
+    return Context(0)
+
+
+def cuda(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def np_(t):
+    return t.cpu().numpy()
+
+
+def gp_draw(X, theta, nu2, z):
+    idx = np.arange(X.shape[0])
+    S = sbv.cov_points(X, idx, idx, theta, nu2)
+    return np.linalg.cholesky(S) @ z
+
+
+@pytest.fixture(scope="module")
+def gp5d():
+    w = workload("gp5d")
+    w["y"] = gp_draw(w["X"], w["theta"][0], w["nu2"], w["z"])
+    return w
+
+
+def oracle_structure(w, T=10, seed=77):
+    b = sbv.blocking(w["X"], w["beta_scale"], w["bc"], T, seed)
+    nbr, cnt = sbv.knn(b["Z"], b["blk"], b["rank"], b["centres"], w["m"])
+    b["nbr"], b["cnt"] = nbr, cnt
+    return b
+
+
+@pytest.fixture(scope="module")
+def gp5d_oracle(gp5d):
+    return oracle_structure(gp5d)
+
+
+# ------------------------------------------------------------------ blocking
+def check_blocking_equal(got, want):
+    assert got["bc_eff"] == want["bc_eff"]
+    assert np.array_equal(np_(got["blk"]), want["blk"])
+    assert np.array_equal(np_(got["ptr"]), want["ptr"])
+    assert np.array_equal(np_(got["pts"]), want["pts"])
+    assert np.array_equal(np_(got["rank"]), want["rank"])
+    assert np.array_equal(np_(got["centres"]), want["centres"])  # bit-identical
+
+
+def test_blocking_bit_exact(ctx, gp5d, gp5d_oracle):
+    got = ctx.sbv_blocking(cuda(gp5d["X"]), gp5d["beta_scale"], gp5d["bc"], 10, 77)
+    check_blocking_equal(got, gp5d_oracle)
+
+
+@pytest.mark.parametrize("n,d,bc,T,seed", [(1000, 3, 1, 3, 1), (777, 7, 777, 2, 2),
+                                           (3001, 13, 257, 5, 3), (500, 2, 64, 0, 4)])
+def test_blocking_edge_sizes(ctx, n, d, bc, T, seed):
+    X = uniform_points(n, d, 40 + seed)
+    beta = np.linspace(0.2, 1.5, d)
+    got = ctx.sbv_blocking(cuda(X), beta, bc, T, seed)
+    check_blocking_equal(got, sbv.blocking(X, beta, bc, T, seed))
+
+
+def test_blocking_float32_points(ctx):
+    X = uniform_points(2000, 4, 9, np.float32)
+    beta = np.array([0.1, 0.3, 0.7, 1.0])
+    got = ctx.sbv_blocking(cuda(X), beta, 150, 6, 5)
+    check_blocking_equal(got, sbv.blocking(X, beta, 150, 6, 5))
+
+
+def test_blocking_with_duplicate_points(ctx):
+    # many exactly equal points and ties in distance: smaller block index wins everywhere
+    rng = np.random.default_rng(3)
+    X = rng.integers(0, 5, size=(600, 2)).astype(np.float64)
+    got = ctx.sbv_blocking(cuda(X), np.ones(2), 40, 4, 8)
+    check_blocking_equal(got, sbv.blocking(X, np.ones(2), 40, 4, 8))
+
+
+# ------------------------------------------------------------------ kNN
+def run_knn(ctx, w, b, m):
+    return ctx.sbv_knn(cuda(w["X"]), w["beta_scale"], cuda(b["ptr"], torch.int64),
+                       cuda(b["pts"], torch.int32), cuda(b["rank"], torch.int32),
+                       cuda(b["centres"]), m)
+
+
+def test_knn_bit_exact(ctx, gp5d, gp5d_oracle):
+    nbr, cnt = run_knn(ctx, gp5d, gp5d_oracle, gp5d["m"])
+    assert np.array_equal(np_(cnt), gp5d_oracle["cnt"])
+    want = gp5d_oracle["nbr"]
+    assert np.array_equal(np_(nbr), want)
+
+
+@pytest.mark.parametrize("m", [0, 1, 7, 300, 600])
+def test_knn_m_edges(ctx, m):
+    X = uniform_points(900, 3, 21)
+    beta = np.array([0.3, 0.6, 0.9])
+    b = sbv.blocking(X, beta, 45, 3, 6)
+    w = dict(X=X, beta_scale=beta)
+    nbr, cnt = run_knn(ctx, w, b, m)
+    on, oc = sbv.knn(b["Z"], b["blk"], b["rank"], b["centres"], m)
+    assert np.array_equal(np_(cnt), oc)
+    if m:
+        assert np.array_equal(np_(nbr), on)
+
+
+def test_knn_ties(ctx):
+    rng = np.random.default_rng(11)
+    X = rng.integers(0, 3, size=(400, 3)).astype(np.float64)
+    beta = np.ones(3)
+    b = sbv.blocking(X, beta, 30, 2, 3)
+    nbr, cnt = run_knn(ctx, dict(X=X, beta_scale=beta), b, 25)
+    on, oc = sbv.knn(b["Z"], b["blk"], b["rank"], b["centres"], 25)
+    assert np.array_equal(np_(cnt), oc)
+    assert np.array_equal(np_(nbr), on)
+
+
+# ------------------------------------------------------------------ likelihood
+def gpu_loglik(ctx, X, y, b, theta, nu2, precision, terms=True):
+    bc = len(b["cnt"])
+    th = np.atleast_2d(theta)
+    B = th.shape[0]
+    bt = torch.empty(B, bc, dtype=torch.float64, device="cuda") if terms else None
+    st = torch.empty(B, bc, dtype=torch.int32, device="cuda")
+    nbr = b["nbr"]
+    if nbr.shape[1] == 0:
+        nbr = np.full((bc, 1), -1)
+    ll = ctx.sbv_loglik(cuda(X), cuda(y), cuda(b["ptr"], torch.int64), cuda(b["pts"], torch.int32),
+                        cuda(nbr, torch.int32), cuda(b["cnt"], torch.int32), th, nu2=nu2,
+                        precision=precision, block_terms=bt, status=st)
+    torch.cuda.synchronize()
+    return np_(ll), (np_(bt) if terms else None), np_(st)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("mixed", TOL_MIXED)])
+def test_loglik_matches_oracle(ctx, gp5d, gp5d_oracle, precision, tol):
+    b, th = gp5d_oracle, gp5d["theta"][0]
+    ll, bt, st = gpu_loglik(ctx, gp5d["X"], gp5d["y"], b, th, 5, precision)
+    want_terms = sbv.loglik_terms(gp5d["X"], gp5d["y"], b["ptr"], b["pts"], b["nbr"], b["cnt"], th, 5)
+    want = sbv.loglik(gp5d["X"], gp5d["y"], b["ptr"], b["pts"], b["nbr"], b["cnt"], b["rank"], th, 5)
+    n = gp5d["n"]
+    assert np.all(st == 0)
+    bs = np.diff(b["ptr"])
+    assert np.all(np.abs(bt[0] - want_terms) <= tol * bs * 10)
+    assert abs(ll[0] - want) / n <= tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_loglik_batched_theta(ctx, gp5d, gp5d_oracle, precision):
+    b = gp5d_oracle
+    rng = np.random.default_rng(2)
+    ths = []
+    for _ in range(5):
+        th = gp5d["theta"][0].copy()
+        th[0] *= math.exp(rng.uniform(-0.5, 0.5))
+        th[1] *= math.exp(rng.uniform(0, 2))
+        th[2:] *= np.exp(rng.uniform(-0.4, 0.4, size=th.size - 2))
+        ths.append(th)
+    ths = np.array(ths)
+    ll, _, st = gpu_loglik(ctx, gp5d["X"], gp5d["y"], b, ths, 5, precision, terms=False)
+    tol = TOL_FP64 if precision == "fp64" else TOL_MIXED
+    for i, th in enumerate(ths):
+        want = sbv.loglik(gp5d["X"], gp5d["y"], b["ptr"], b["pts"], b["nbr"], b["cnt"], b["rank"], th, 5)
+        assert abs(ll[i] - want) / gp5d["n"] <= tol
+
+
+@pytest.mark.parametrize("nu2", [1, 3, 7])
+def test_loglik_other_smoothness(ctx, nu2):
+    X = uniform_points(700, 3, 31)
+    y = standard_normal(700, 32)
+    beta = np.array([0.2, 0.4, 0.8])
+    b = sbv.blocking(X, beta, 70, 3, 9)
+    b["nbr"], b["cnt"] = sbv.knn(b["Z"], b["blk"], b["rank"], b["centres"], 25)
+    th = np.array([1.5, 0.05, 0.2, 0.4, 0.8])
+    ll, _, _ = gpu_loglik(ctx, X, y, b, th, nu2, "fp64", terms=False)
+    want = sbv.loglik(X, y, b["ptr"], b["pts"], b["nbr"], b["cnt"], b["rank"], th, nu2)
+    assert abs(ll[0] - want) / 700 <= TOL_FP64
+
+
+def test_loglik_degenerate_structures(ctx):
+    X = uniform_points(300, 2, 41)
+    y = standard_normal(300, 42)
+    th = np.array([1.0, 0.01, 0.3, 0.6])
+    # one block holding every point, no neighbours: exact dense GP (Eq. 1)
+    one = dict(ptr=np.array([0, 300]), pts=np.arange(300), nbr=np.full((1, 1), -1),
+               cnt=np.array([0]), rank=np.array([0]))
+    ll, _, _ = gpu_loglik(ctx, X, y, one, th, 5, "fp64", terms=False)
+    want = sbv.loglik(X, y, one["ptr"], one["pts"], one["nbr"], one["cnt"], one["rank"], th, 5)
+    assert abs(ll[0] - want) / 300 <= TOL_FP64
+    # every point its own block, no neighbours
+    sing = dict(ptr=np.arange(301), pts=np.arange(300), nbr=np.full((300, 1), -1),
+                cnt=np.zeros(300, dtype=np.int64), rank=np.arange(300))
+    ll, _, _ = gpu_loglik(ctx, X, y, sing, th, 5, "fp64", terms=False)
+    want = sbv.loglik(X, y, sing["ptr"], sing["pts"], sing["nbr"], sing["cnt"], sing["rank"], th, 5)
+    assert abs(ll[0] - want) / 300 <= TOL_FP64
+
+
+def test_loglik_large_blocks_use_global_scratch(ctx):
+    # N = m + bs above the shared-memory capacity of the FP64 kernel
+    X = uniform_points(3000, 4, 51)
+    y = standard_normal(3000, 52)
+    beta = np.array([0.3, 0.5, 0.7, 0.9])
+    b = sbv.blocking(X, beta, 12, 2, 1)
+    b["nbr"], b["cnt"] = sbv.knn(b["Z"], b["blk"], b["rank"], b["centres"], 400)
+    th = np.array([1.0, 0.01, 0.3, 0.5, 0.7, 0.9])
+    ll, bt, st = gpu_loglik(ctx, X, y, b, th, 5, "fp64")
+    want = sbv.loglik(X, y, b["ptr"], b["pts"], b["nbr"], b["cnt"], b["rank"], th, 5)
+    assert np.all(st == 0)
+    assert abs(ll[0] - want) / 3000 <= TOL_FP64
+
+
+def test_loglik_deterministic(ctx, gp5d, gp5d_oracle):
+    a, ta, _ = gpu_loglik(ctx, gp5d["X"], gp5d["y"], gp5d_oracle, gp5d["theta"][0], 5, "fp64")
+    b, tb, _ = gpu_loglik(ctx, gp5d["X"], gp5d["y"], gp5d_oracle, gp5d["theta"][0], 5, "fp64")
+    assert a[0] == b[0] and np.array_equal(ta, tb)
+
+
+def test_loglik_not_positive_definite_is_reported(ctx):
+    from paper_2504_12004_gb300 import SBVError
+    # duplicated coordinates with no nugget make the joint matrix singular
+    X = uniform_points(100, 2, 61)
+    X[50:] = X[:50]
+    y = standard_normal(100, 62)
+    struct = dict(ptr=np.array([0, 100]), pts=np.arange(100), nbr=np.full((1, 1), -1),
+                  cnt=np.array([0]), rank=np.array([0]))
+    th = np.array([1.0, 0.0, 0.5, 0.5])
+    ll, bt, st = gpu_loglik(ctx, X, y, struct, th, 5, "fp64")
+    assert st[0, 0] == 2 and math.isnan(ll[0])
+    with pytest.raises(SBVError) as e:
+        ctx.sbv_sync_status()
+    assert e.value.code == 2
+    ctx.sbv_sync_status()  # cleared
+
+
+def test_invalid_arguments_are_rejected(ctx, gp5d, gp5d_oracle):
+    from paper_2504_12004_gb300 import SBVError
+    b = gp5d_oracle
+    bad = gp5d["theta"][0].copy()
+    bad[0] = -1.0
+    with pytest.raises(SBVError) as e:
+        gpu_loglik(ctx, gp5d["X"], gp5d["y"], b, bad, 5, "fp64")
+    assert e.value.code == 1
+    with pytest.raises(SBVError):
+        gpu_loglik(ctx, gp5d["X"], gp5d["y"], b, gp5d["theta"][0], 4, "fp64")
+    with pytest.raises(SBVError):
+        ctx.sbv_blocking(cuda(gp5d["X"]), gp5d["beta_scale"], 0, 1, 1)
+    with pytest.raises(SBVError):
+        ctx.sbv_blocking(cuda(gp5d["X"]), -gp5d["beta_scale"], 10, 1, 1)
+
+
+# ------------------------------------------------------------------ prediction
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-6)])
+def test_predict_matches_oracle(ctx, gp5d, precision, tol):
+    th = gp5d["theta"][0]
+    mean, var, var_lat, nbr = ctx.sbv_predict(cuda(gp5d["X"]), cuda(gp5d["y"]), cuda(gp5d["Xtest"]),
+                                              gp5d["beta_scale"], gp5d["m_pred"], th, 5,
+                                              precision=precision, want_nbr=True)
+    rows = np.arange(0, 500, 5)
+    om, ov, ol, onbr = sbv.predict(gp5d["X"], gp5d["y"], gp5d["Xtest"], gp5d["beta_scale"],
+                                   gp5d["m_pred"], th, 5, rows=rows)
+    assert np.array_equal(np_(nbr)[rows], onbr)
+    assert np.max(np.abs(np_(mean)[rows] - om)) <= tol
+    assert np.max(np.abs(np_(var)[rows] - ov)) <= tol
+    assert np.max(np.abs(np_(var_lat)[rows] - ol)) <= tol
