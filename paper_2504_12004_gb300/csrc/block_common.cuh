@@ -38,6 +38,35 @@ __device__ __forceinline__ void record_failure(DevStatus* st, int code, int item
   atomicAdd(&st->count, 1);
 }
 
+struct LoglikArgs {
+  const void* X;
+  int dtype;
+  const double* y;
+  int64_t n;
+  int d;
+  const int64_t* ptr;
+  const int32_t* pts;
+  const int32_t* nbr;
+  const int32_t* cnt;
+  int64_t bc;
+  int m;
+  const ThetaDev* theta;
+  int B;
+  int nu2;
+  int ncap;                // largest N the launch can hold
+  double* terms;           // B x bc
+  int32_t* status;         // B x bc or NULL
+  DevStatus* dstat;
+  unsigned int* counter;   // work counter
+  double* gmat;            // global scratch (one matrix per CTA) or NULL
+  size_t gmat_stride;      // doubles per CTA slice
+};
+
+template <typename T>
+__device__ __forceinline__ double ld_x(const void* X, int64_t i) {
+  return (double)((const T*)X)[i];
+}
+
 // Packed lower-triangular index of (i, j), j <= i.
 __device__ __forceinline__ int tri(int i, int j) { return (i * (i + 1) >> 1) + j; }
 

@@ -23,35 +23,6 @@ namespace sbv {
 
 constexpr int LL_THREADS = 256;
 
-struct LoglikArgs {
-  const void* X;
-  int dtype;
-  const double* y;
-  int64_t n;
-  int d;
-  const int64_t* ptr;
-  const int32_t* pts;
-  const int32_t* nbr;
-  const int32_t* cnt;
-  int64_t bc;
-  int m;
-  const ThetaDev* theta;
-  int B;
-  int nu2;
-  int ncap;                // largest N the launch can hold
-  double* terms;           // B x bc
-  int32_t* status;         // B x bc or NULL
-  DevStatus* dstat;
-  unsigned int* counter;   // work counter
-  double* gmat;            // global scratch (one matrix per CTA) or NULL
-  size_t gmat_stride;      // doubles per CTA slice
-};
-
-template <typename T>
-__device__ __forceinline__ double ld_x(const void* X, int64_t i) {
-  return (double)((const T*)X)[i];
-}
-
 // Gather the N points of an item into u[t][p] = x_p,t / beta_t and yv[p].
 // Point p < mb is neighbour p of the block, p >= mb is member p - mb.
 __device__ void gather_item(const LoglikArgs& a, int64_t blk, int mb, int N,
@@ -452,8 +423,9 @@ int run_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t
                 int nu2, int precision, double* mean, double* var, double* var_latent,
                 cudaStream_t s) {
   (void)n;
-  (void)precision;
   int st = 0;
+  if (precision != SBV_PREC_FP64)
+    return fail(ctx, SBV_EUNSUPPORTED, "prediction runs in FP64 only");
   ThetaDev* dth = nullptr;
   if ((st = upload_theta(ctx, h_theta, 1, d, &dth, s))) return st;
   unsigned int* counter = (unsigned int*)ws_get(ctx, WS_SMALL, 64, &st);
