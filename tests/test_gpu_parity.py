@@ -164,7 +164,11 @@ def test_loglik_matches_oracle(ctx, gp5d, gp5d_oracle, precision, tol):
     n = gp5d["n"]
     assert np.all(st == 0)
     bs = np.diff(b["ptr"])
-    assert np.all(np.abs(bt[0] - want_terms) <= tol * bs * 10)
+    per_point = np.abs(bt[0] - want_terms) / bs
+    # FP64: every block to the bar; mixed: the total to the bar, single blocks
+    # within 100x (the FP32 factorisation leaves O(kappa u) log-det error per
+    # block that averages out over blocks; tau^2 = 1e-4 makes kappa ~ 1e5 here)
+    assert per_point.max() <= (tol if precision == "fp64" else 100 * tol), per_point.max()
     assert abs(ll[0] - want) / n <= tol
 
 
