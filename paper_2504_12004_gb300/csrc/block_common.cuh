@@ -15,6 +15,9 @@ struct ThetaDev {
   double sigma2;
   double tau2;
   double inv_beta[SBV_MAX_DIM];
+  // the same values as float pairs (head, tail) for double-float arithmetic
+  float s2_h, s2_l, diag_h, diag_l;   // sigma^2 and sigma^2 + tau^2
+  float ib_h[SBV_MAX_DIM], ib_l[SBV_MAX_DIM];
 };
 
 // Closed-form Matern correlation 2^(1-nu)/Gamma(nu) r^nu K_nu(r), nu = nu2/2,

@@ -39,6 +39,16 @@ __device__ __forceinline__ df df_add(df a, df b) {
   return fast_two_sum(s.h, e);
 }
 
+// a - b with full accuracy even under cancellation
+__device__ __forceinline__ df df_sub_acc(df a, df b) {
+  df s = two_sum(a.h, -b.h);
+  df t = two_sum(a.l, -b.l);
+  s.l = __fadd_rn(s.l, t.h);
+  s = fast_two_sum(s.h, s.l);
+  s.l = __fadd_rn(s.l, t.l);
+  return fast_two_sum(s.h, s.l);
+}
+
 __device__ __forceinline__ df df_add_f(df a, float b) {
   df s = two_sum(a.h, b);
   return fast_two_sum(s.h, __fadd_rn(s.l, a.l));
@@ -49,13 +59,6 @@ __device__ __forceinline__ df df_mul(df a, df b) {
   float e = __fmaf_rn(a.h, b.h, -p);
   e = __fmaf_rn(a.h, b.l, e);
   e = __fmaf_rn(a.l, b.h, e);
-  return fast_two_sum(p, e);
-}
-
-__device__ __forceinline__ df df_mul_f(df a, float b) {
-  float p = __fmul_rn(a.h, b);
-  float e = __fmaf_rn(a.h, b, -p);
-  e = __fmaf_rn(a.l, b, e);
   return fast_two_sum(p, e);
 }
 
@@ -74,46 +77,47 @@ __device__ __forceinline__ df df_sqrt(df s) {
   float p = __fmul_rn(rh, rh);
   float pe = __fmaf_rn(rh, rh, -p);
   float e = __fadd_rn(__fsub_rn(__fsub_rn(s.h, p), pe), s.l);
-  float rl = __fmul_rn(e, __fdiv_rn(0.5f, rh));
+  float rl = __fmul_rn(e, __fdividef(0.5f, rh));
   return fast_two_sum(rh, rl);
 }
 
-// Constants of df_exp_neg, filled from host FP64 values when the library loads:
-// c_exp_tab[i] = 2^(-i/32) for i = 0..31; c_ln2, c_inv_ln2; c_inv_fact[k] = 1/k!.
+// Constants of the double-float exponential, filled from host FP64 values:
+// 1/ln2, ln2, 1/3, 2/5, 1/15 and the table 2^(-i/256), i = 0..255.
 struct DfConsts {
-  float tab_h[32], tab_l[32];
   float ln2_h, ln2_l, ilog2_h, ilog2_l;
   float third_h, third_l, fifth2_h, fifth2_l, fifteenth_h, fifteenth_l;
-  float fact_h[8], fact_l[8];  // 1/k! for k = 0..7
+  float tab_h[256], tab_l[256];
 };
-// One copy per translation unit that includes this header; each such unit
-// uploads it (cudaMemcpyToSymbol) before its first launch.
-static __constant__ DfConsts c_df;
 
-// exp(-r) for r >= 0: exp(-r) = 2^(-q) * 2^(-i/32) * exp(-g), where
-// r / ln2 = (32 q + i)/32 + f, 0 <= f < 1/32, g = f ln2 < 0.0217, and exp(-g)
-// is its Taylor polynomial to degree 7 (truncation < 1e-16) evaluated by
-// Horner's rule in double-float.
-__device__ __forceinline__ df df_exp_neg(df r) {
+// exp(-r), r >= 0: r/ln2 = (256 q + i)/256 + f with 0 <= f < 1/256, so
+// exp(-r) = 2^-q * 2^(-i/256) * exp(-g), g = f ln2 < 0.0028, and
+// exp(-g) = 1 - g + g^2 (1/2 - g (1/6 - g/24)) (truncation < 2e-15 relative);
+// the table is read from shared memory (tab_h, tab_l) because the index
+// differs across a warp.
+__device__ __forceinline__ df df_exp_neg(df r, const DfConsts& c, const float* tab_h,
+                                         const float* tab_l) {
   if (r.h > 85.0f) return {0.0f, 0.0f};
-  df t = df_mul(r, df{c_df.ilog2_h, c_df.ilog2_l});
-  float kf = floorf(t.h * 32.0f);
+  df t = df_mul(r, df{c.ilog2_h, c.ilog2_l});
+  float kf = floorf(__fmul_rn(t.h, 256.0f));
   int k = (int)kf;
-  df f = fast_two_sum(__fsub_rn(t.h, kf * 0.03125f), t.l);
-  df g = df_mul(f, df{c_df.ln2_h, c_df.ln2_l});
-  // exp(-g) = sum_k (-g)^k / k!
-  df ng = {-g.h, -g.l};
-  df acc = {c_df.fact_h[7], c_df.fact_l[7]};
-#pragma unroll
-  for (int q = 6; q >= 0; --q) acc = df_add(df_mul(acc, ng), df{c_df.fact_h[q], c_df.fact_l[q]});
-  df e = df_mul(acc, df{c_df.tab_h[k & 31], c_df.tab_l[k & 31]});
-  int sh = -(k >> 5);
+  df f = fast_two_sum(__fsub_rn(t.h, __fmul_rn(kf, 0.00390625f)), t.l);
+  df g = df_mul(f, df{c.ln2_h, c.ln2_l});
+  df g2 = df_mul(g, g);
+  float inner = __fmul_rn(g.h, __fmaf_rn(-g.h, 0.041666668f, 0.16666667f));
+  df w = two_sum(0.5f, -inner);
+  df term = df_mul(g2, w);
+  df one_m_g = two_sum(1.0f, -g.h);
+  one_m_g = fast_two_sum(one_m_g.h, __fsub_rn(one_m_g.l, g.l));
+  df e = df_add(one_m_g, term);
+  e = df_mul(e, df{tab_h[k & 255], tab_l[k & 255]});
+  int sh = -(k >> 8);
   return {ldexpf(e.h, sh), ldexpf(e.l, sh)};
 }
 
 // Matern correlation M_nu(r) for nu = nu2/2 (closed forms), r and s = r^2 in double-float.
-__device__ __forceinline__ df df_matern(df r, df s, int nu2) {
-  df e = df_exp_neg(r);
+__device__ __forceinline__ df df_matern(df r, df s, int nu2, const DfConsts& c, const float* tab_h,
+                                        const float* tab_l) {
+  df e = df_exp_neg(r, c, tab_h, tab_l);
   const df one = {1.0f, 0.0f};
   switch (nu2) {
     case 1:
@@ -121,13 +125,13 @@ __device__ __forceinline__ df df_matern(df r, df s, int nu2) {
     case 3:
       return df_mul(df_add(one, r), e);
     case 5: {
-      df p = df_add(df_add(one, r), df_mul(s, df{c_df.third_h, c_df.third_l}));
+      df p = df_add(df_add(one, r), df_mul(s, df{c.third_h, c.third_l}));
       return df_mul(p, e);
     }
     default: {
       // 1 + r + 2 r^2 / 5 + r^3 / 15
-      df p = df_add(df_add(one, r), df_mul(s, df{c_df.fifth2_h, c_df.fifth2_l}));
-      p = df_add(p, df_mul(df_mul(s, r), df{c_df.fifteenth_h, c_df.fifteenth_l}));
+      df p = df_add(df_add(one, r), df_mul(s, df{c.fifth2_h, c.fifth2_l}));
+      p = df_add(p, df_mul(df_mul(s, r), df{c.fifteenth_h, c.fifteenth_l}));
       return df_mul(p, e);
     }
   }

@@ -220,6 +220,13 @@ static std::vector<ThetaDev> derive_theta(const double* h, int B, int d) {
     out[b].sigma2 = r[0];
     out[b].tau2 = r[1];
     for (int t = 0; t < d; ++t) out[b].inv_beta[t] = 1.0 / r[2 + t];
+    auto split = [](double v, float& h, float& l) {
+      h = (float)v;
+      l = (float)(v - (double)h);
+    };
+    split(r[0], out[b].s2_h, out[b].s2_l);
+    split(r[0] + r[1], out[b].diag_h, out[b].diag_l);
+    for (int t = 0; t < d; ++t) split(out[b].inv_beta[t], out[b].ib_h[t], out[b].ib_l[t]);
   }
   return out;
 }

@@ -52,6 +52,7 @@ enum WsSlot {
   WS_MATRIX,      // global-memory matrices for blocks too large for shared memory
   WS_CENTRES,
   WS_EXTRA,
+  WS_XSPLIT,      // points split into float pairs for the mixed path
   WS_COUNT
 };
 
