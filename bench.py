@@ -281,6 +281,7 @@ def main():
         out = None
         for i in range(steps):
             flush.fill_(float(i))        # evict L2 between steps (inputs would otherwise stay resident)
+            torch.cuda.synchronize()     # an unsynchronised fill here slows the next call (measured)
             ev[i][0].record(stream)
             out = evaluate(prec)
             ev[i][1].record(stream)

@@ -55,8 +55,11 @@ extern "C" {
 #define SBV_F32 1
 
 /* arithmetic of the per-block factorisation */
-#define SBV_PREC_FP64  0   /* everything in FP64 */
-#define SBV_PREC_MIXED 1   /* FP32 factorisation, FP64 diagonal tiles, log-det and refinement */
+#define SBV_PREC_FP64       0  /* everything in FP64 */
+#define SBV_PREC_MIXED      1  /* FP32 factorisation (CUDA cores); FP64-accurate covariance,
+                                  diagonal-tile subtraction, log-det and one refinement step */
+#define SBV_PREC_MIXED_BF16 2  /* as SBV_PREC_MIXED with the trailing updates on the tensor
+                                  cores (tcgen05, split BF16 operands, FP32 accumulators) */
 
 /* compiled limits */
 #define SBV_MAX_DIM      64     /* d */
@@ -144,7 +147,7 @@ int sbv_knn(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_t d,
  *   nbr, cnt           device, neighbours from sbv_knn (row stride m)
  *   theta              host, B x (2+d) doubles, rows (sigma^2, tau^2, beta_1..beta_d)
  *   nu2                2*nu in {1, 3, 5, 7}
- *   precision          SBV_PREC_FP64 or SBV_PREC_MIXED
+ *   precision          SBV_PREC_FP64, SBV_PREC_MIXED or SBV_PREC_MIXED_BF16
  *   ll                 device, B doubles  out: l(theta_b) = sum_i l_{b,i}
  *   block_terms        device, B x bc doubles out (or NULL): l_{b,i}
  *   status             device, B x bc int32 out (or NULL): 0, or SBV_ENOTSPD

@@ -17,8 +17,8 @@ LIB_PATH = Path(__file__).resolve().parent / "libsbv.so"
 
 SBV_OK, SBV_EINVAL, SBV_ENOTSPD, SBV_ENOMEM, SBV_ECUDA, SBV_ETIMEOUT, SBV_EUNSUPPORTED = range(7)
 SBV_F64, SBV_F32 = 0, 1
-SBV_PREC_FP64, SBV_PREC_MIXED = 0, 1
-PRECISIONS = {"fp64": SBV_PREC_FP64, "mixed": SBV_PREC_MIXED}
+SBV_PREC_FP64, SBV_PREC_MIXED, SBV_PREC_MIXED_BF16 = 0, 1, 2
+PRECISIONS = {"fp64": SBV_PREC_FP64, "mixed": SBV_PREC_MIXED, "mixed_bf16": SBV_PREC_MIXED_BF16}
 ERRNAMES = {1: "SBV_EINVAL", 2: "SBV_ENOTSPD", 3: "SBV_ENOMEM", 4: "SBV_ECUDA",
             5: "SBV_ETIMEOUT", 6: "SBV_EUNSUPPORTED"}
 

@@ -262,7 +262,8 @@ static int structure_max_n(sbv_ctx* ctx, const int64_t* ptr, const int32_t* cnt,
   return SBV_OK;
 }
 
-int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a, int nmax, cudaStream_t s);
+int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a, int nmax, int precision,
+                        cudaStream_t s);
 
 int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n, int d,
                const int64_t* ptr, const int32_t* pts, const int32_t* nbr, const int32_t* cnt,
@@ -309,8 +310,8 @@ int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t 
   a.gmat = nullptr;
   a.gmat_stride = 0;
 
-  if (precision == SBV_PREC_MIXED) {
-    if ((st = launch_loglik_mixed(ctx, a, nmax, s))) return st;
+  if (precision == SBV_PREC_MIXED || precision == SBV_PREC_MIXED_BF16) {
+    if ((st = launch_loglik_mixed(ctx, a, nmax, precision, s))) return st;
   } else {
     const size_t ub = (size_t)(d + 1) * (nmax + 1) * sizeof(double);
     const size_t mat = (size_t)(nmax + 1) * (nmax + 2) / 2 * sizeof(double);

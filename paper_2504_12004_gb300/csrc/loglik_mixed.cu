@@ -6,21 +6,24 @@
 //     the first point and re-split on a common power-of-two grid so that every
 //     difference of the float heads is exact;
 //  2. evaluate the joint covariance in double-float (dfloat.cuh): the float
-//     head of each entry feeds the FP32 factorisation; for the 16 x 16
-//     diagonal tiles the head and tail are kept apart; the full double-float
-//     matrix goes to a per-CTA scratch slice (L2-resident) for the
-//     refinement residual;
-//  3. blocked right-looking Cholesky: each diagonal tile is formed as
-//     (double-float original) - (FP32-accumulated updates) with one exact
-//     subtraction, rounded, and factored in FP32 registers by one warp; the
-//     panel solve and the trailing update run in FP32; y is bordered as row
-//     N so the factorisation also yields w0 = L^{-1} y;
-//  4. x0 = L^-T w0 and x0_J = L_JJ^-T w0_J in FP32 (one two-column sweep);
+//     head of each off-diagonal-tile entry feeds the FP32 factorisation; the
+//     full double-float matrix goes to a per-CTA scratch slice (L2-resident)
+//     for the diagonal tiles and the refinement residual;
+//  3. blocked right-looking Cholesky (16-column panels): each diagonal tile is
+//     formed as (double-float original) - (FP32-accumulated updates) with one
+//     exact subtraction, rounded, and factored in FP32 registers by one warp;
+//     FP32 panel solve; trailing update either FP32 on the CUDA cores
+//     (SBV_PREC_MIXED) or split-BF16 on the tensor cores with TMEM
+//     accumulators (SBV_PREC_MIXED_BF16); y is bordered as row N so the
+//     factorisation also yields w0 = L^{-1} y;
+//  4. the diagonal tiles are replaced by their inverses, which turns the
+//     diagonal steps of the triangular solves into small parallel products;
+//     x0 = L^-T w0 and x0_J = L_JJ^-T w0_J in FP32 (one two-column sweep);
 //  5. one step of iterative refinement: r = y - Sigma x0 and r_J = y_J -
 //     Sigma_JJ x0_J accumulated in double-float from the scratch matrix, the
 //     corrections solved in FP32;
 //  6. l_i = -1/2 [bs log 2pi + 2 sum_{t>=m} log L_tt + y^T x - y_J^T x_J],
-//     log L_tt = e ln2 + log(mantissa) with the sums in FP64.
+//     log L_tt = e ln2 + log(mantissa), sums in FP64.
 // y^T Sigma^{-1} y - y_J^T Sigma_JJ^{-1} y_J is the quadratic form of the
 // Schur complement Sigma^lk - Sigma^cor of Alg. 5 (applied to y_B - mu^new),
 // and the trailing log-determinant is its log-determinant.
@@ -30,9 +33,12 @@
 #include <algorithm>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "block_common.cuh"
 #include "dfloat.cuh"
 #include "sbv_internal.cuh"
+#include "umma.cuh"
 
 namespace sbv {
 
@@ -40,66 +46,73 @@ static __constant__ DfConsts c_df;
 
 constexpr int MX_THREADS = 256;
 constexpr int MX_WARPS = MX_THREADS / 32;
-constexpr int NB = 16;  // diagonal tile size
+constexpr int NB = 16;  // panel width = diagonal tile size
 
 struct MixedLayout {
-  int ncap;    // largest N held (rows 0..ncap-1 plus the bordered row)
-  int ntile;   // tiles of NB columns
+  int ncap;             // largest N held (rows 0..ncap-1 plus the bordered row)
   int d;
-  size_t off_A, off_K, off_vh, off_vl, off_y, off_v, off_part, bytes;
+  int pstride;          // row stride of the FP32 column-major panel (CUDA-core update)
+  uint32_t opnd_piece;  // bytes of one BF16 operand piece (tensor-core update)
+  size_t off_y, off_v, off_u, off_vl, off_A, bytes;
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline MixedLayout mixed_layout(int ncap, int d) {
+// One shared-memory region (off_u) serves three phases in turn: the scaled
+// coordinates (covariance), the panel operand (factorisation) and the
+// residual partial sums (refinement).
+__host__ __device__ inline MixedLayout mixed_layout(int ncap, int d, bool tc) {
   MixedLayout L;
   L.ncap = ncap;
-  L.ntile = (ncap + NB - 1) / NB;
   L.d = d;
+  L.pstride = (int)align_up((size_t)ncap + 1, 4);
+  L.opnd_piece = (uint32_t)(((ncap + 1 + 127) / 128) * 128 * 32);
   size_t o = 0;
-  L.off_K = o;    o += (size_t)L.ntile * NB * NB * sizeof(float2);   // diagonal-tile originals
-  L.off_y = o;    o += align_up((size_t)(ncap + 1) * sizeof(float2), 16);
-  L.off_v = o;    o += align_up((size_t)6 * (ncap + 1) * sizeof(float), 16);  // x0 x0J r1 r2 ldiag idiag
-  L.off_vh = o;   o += align_up((size_t)d * ncap * sizeof(float), 16);
-  L.off_vl = o;   o += align_up((size_t)d * ncap * sizeof(float), 16);
-  L.off_A = o;    o += align_up((size_t)(ncap + 1) * (ncap + 2) / 2 * sizeof(float), 16);
-  L.off_part = L.off_vh;  // residual partial sums reuse the coordinate area
+  L.off_y = o;  o += align_up((size_t)(ncap + 1) * sizeof(float2), 16);
+  L.off_v = o;  o += align_up((size_t)6 * (ncap + 1) * sizeof(float), 16);  // x0 x0J r1 r2 ldiag idiag
+  o = align_up(o, 128);
+  const size_t coord = align_up((size_t)d * ncap * sizeof(float), 16);
+  size_t uni = 2 * coord;
+  const size_t panel = tc ? 3 * (size_t)L.opnd_piece : (size_t)NB * L.pstride * sizeof(float);
+  const size_t part = (size_t)(32 * MX_WARPS > ncap ? 32 * MX_WARPS : ncap) * sizeof(float4);
+  if (panel > uni) uni = panel;
+  if (part > uni) uni = part;
+  L.off_u = o;
+  L.off_vl = o + coord;
+  o += align_up(uni, 16);
+  L.off_A = o;  o += align_up((size_t)(ncap + 1) * (ncap + 2) / 2 * sizeof(float), 16);
   L.bytes = o;
   return L;
 }
 
 // ---------------------------------------------------------------------------
-// blocked FP32 triangular solves with the factor packed in A; idiag holds
-// 1/L_tt.  Two right-hand sides, one per half-warp in the diagonal steps.
+// Triangular solves with the factor packed in A, whose diagonal tiles hold
+// the inverses of the diagonal blocks.  Two right-hand sides (lanes 0-15 and
+// 16-31 of warp 0 in the diagonal steps).
 // ---------------------------------------------------------------------------
-__device__ void fwd_solve2(const float* A, const float* idiag, int N, float* b1, float* b2) {
+__device__ void fwd_solve2(const float* A, int N, float* b1, float* b2) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k0 = 0; k0 < N; k0 += NB) {
     const int k1 = min(k0 + NB, N), nbk = k1 - k0;
     if (warp == 0) {
-      const int h = lane >> 4, r = lane & 15;
-      float* b = h ? b2 : b1;
-      const int row = k0 + r;
-      const bool live = r < nbk;
-      float v = live ? b[row] : 0.0f;
-#pragma unroll
-      for (int c = 0; c < NB; ++c) {
-        if (c < nbk) {
-          float vc = __shfl_sync(0xffffffffu, v, (h << 4) + c) * idiag[k0 + c];
-          if (r == c) v = vc;
-          if (r > c && live) v = fmaf(-A[tri(row, k0 + c)], vc, v);
-        }
+      const int r = lane & 15;
+      float* b = (lane >> 4) ? b2 : b1;
+      float v = 0.0f;
+      if (r < nbk) {
+        const float* Li = A + tri(k0 + r, k0);  // row r of the tile inverse
+        for (int c = 0; c <= r; ++c) v = fmaf(Li[c], b[k0 + c], v);
       }
-      if (live) b[row] = v;
+      __syncwarp();
+      if (r < nbk) b[k0 + r] = v;
     }
     __syncthreads();
     for (int i = k1 + threadIdx.x; i < N; i += blockDim.x) {
       float s1 = 0.0f, s2 = 0.0f;
       const float* Ai = A + tri(i, 0);
       for (int k = k0; k < k1; ++k) {
-        const float a = Ai[k];
-        s1 = fmaf(a, b1[k], s1);
-        s2 = fmaf(a, b2[k], s2);
+        const float x = Ai[k];
+        s1 = fmaf(x, b1[k], s1);
+        s2 = fmaf(x, b2[k], s2);
       }
       b1[i] -= s1;
       b2[i] -= s2;
@@ -108,34 +121,27 @@ __device__ void fwd_solve2(const float* A, const float* idiag, int N, float* b1,
   }
 }
 
-__device__ void bwd_solve2(const float* A, const float* idiag, int N, float* b1, float* b2) {
+__device__ void bwd_solve2(const float* A, int N, float* b1, float* b2) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntile = (N + NB - 1) / NB;
   for (int kt = ntile - 1; kt >= 0; --kt) {
     const int k0 = kt * NB, k1 = min(k0 + NB, N), nbk = k1 - k0;
     if (warp == 0) {
-      const int h = lane >> 4, r = lane & 15;
-      float* b = h ? b2 : b1;
-      const int row = k0 + r;
-      const bool live = r < nbk;
-      float v = live ? b[row] : 0.0f;
-#pragma unroll
-      for (int c = NB - 1; c >= 0; --c) {
-        if (c < nbk) {
-          float vc = __shfl_sync(0xffffffffu, v, (h << 4) + c) * idiag[k0 + c];
-          if (r == c) v = vc;
-          if (r < c) v = fmaf(-A[tri(k0 + c, row)], vc, v);
-        }
-      }
-      if (live) b[row] = v;
+      const int r = lane & 15;
+      float* b = (lane >> 4) ? b2 : b1;
+      float v = 0.0f;
+      if (r < nbk)
+        for (int c = r; c < nbk; ++c) v = fmaf(A[tri(k0 + c, k0 + r)], b[k0 + c], v);
+      __syncwarp();
+      if (r < nbk) b[k0 + r] = v;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < k0; i += blockDim.x) {
       float s1 = 0.0f, s2 = 0.0f;
       for (int k = k0; k < k1; ++k) {
-        const float Lki = A[tri(k, i)];
-        s1 = fmaf(Lki, b1[k], s1);
-        s2 = fmaf(Lki, b2[k], s2);
+        const float x = A[tri(k, i)];
+        s1 = fmaf(x, b1[k], s1);
+        s2 = fmaf(x, b2[k], s2);
       }
       b1[i] -= s1;
       b2[i] -= s2;
@@ -175,16 +181,19 @@ struct MixedArgs {
   MixedLayout lay;
 };
 
+template <bool TC>
 __global__ void __launch_bounds__(MX_THREADS, 2)
 loglik_mixed_kernel(MixedArgs P) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   const LoglikArgs& a = P.a;
   const MixedLayout& lay = P.lay;
-  float2* Kd = (float2*)(smem + lay.off_K);
   float2* yv = (float2*)(smem + lay.off_y);
   float* vec = (float*)(smem + lay.off_v);
-  float* vh = (float*)(smem + lay.off_vh);
+  float* vh = (float*)(smem + lay.off_u);
   float* vl = (float*)(smem + lay.off_vl);
+  float* Pt = (float*)(smem + lay.off_u);                 // FP32 panel, column-major
+  unsigned char* opnd = smem + lay.off_u;                 // BF16 panel pieces
+  float4* part = (float4*)(smem + lay.off_u);             // residual partial sums
   float* A = (float*)(smem + lay.off_A);
   __shared__ float tab_h[256], tab_l[256];
   __shared__ unsigned int s_item;
@@ -192,9 +201,13 @@ loglik_mixed_kernel(MixedArgs P) {
   __shared__ double red[MX_WARPS];
   __shared__ float s_org_h[SBV_MAX_DIM], s_org_l[SBV_MAX_DIM];
   __shared__ float s_grid;
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ int s_timeout;
   const DfConsts& C = c_df;
   float2* S = P.scratch + (size_t)blockIdx.x * P.scratch_stride;
-  const int d = a.d, cap = lay.ncap;
+  const int d = a.d, cap = lay.ncap, PS = lay.pstride;
+  const uint32_t opnd_piece = lay.opnd_piece;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned int total = (unsigned int)(a.bc * a.B);
   const double log2pi = 1.8378770664093454836;
@@ -209,6 +222,18 @@ loglik_mixed_kernel(MixedArgs P) {
     tab_h[i] = C.tab_h[i];
     tab_l[i] = C.tab_l[i];
   }
+  if (threadIdx.x == 0) s_timeout = 0;
+  uint32_t tmem_base = 0, mma_phase = 0;
+  if (TC) {
+    // 256 TMEM columns: two 128 x (<= 128) FP32 accumulators
+    if (warp == 0) umma::tmem_alloc(&s_tmem, 256);
+    if (threadIdx.x == 0) umma::mbar_init(&mma_bar, 1);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    tmem_base = s_tmem;
+  }
+  __syncthreads();
 
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
@@ -239,7 +264,6 @@ loglik_mixed_kernel(MixedArgs P) {
       const float yh = (float)yy;
       yv[p] = make_float2(yh, (float)(yy - (double)yh));
     }
-    float mx = 0.0f;
     for (int e = threadIdx.x; e < N * d; e += blockDim.x) {
       const int p = e / d, t = e - p * d;
       int64_t id = p < mb ? (int64_t)a.nbr[blk * a.m + p] : (int64_t)a.pts[base + (p - mb)];
@@ -251,7 +275,7 @@ loglik_mixed_kernel(MixedArgs P) {
         x = {((const float*)a.X)[id * d + t], 0.0f};
       }
       const df u = df_mul(x, df{th.ib_h[t], th.ib_l[t]});
-      vh[t * N + p] = u.h;  // temporarily the uncentred coordinate
+      vh[t * N + p] = u.h;  // uncentred for now
       vl[t * N + p] = u.l;
     }
     __syncthreads();
@@ -260,6 +284,7 @@ loglik_mixed_kernel(MixedArgs P) {
       s_org_l[t] = vl[t * N];
     }
     __syncthreads();
+    float mx = 0.0f;
     for (int e = threadIdx.x; e < N * d; e += blockDim.x) {
       const int t = e / N;
       const df v = df_sub_acc(df{vh[e], vl[e]}, df{s_org_h[t], s_org_l[t]});
@@ -316,13 +341,8 @@ loglik_mixed_kernel(MixedArgs P) {
           const df r = df_sqrt(s);
           K = df_mul(s2, df_matern(r, s, a.nu2, C, tab_h, tab_l));
         }
-        const int ti = i / NB, tj = j / NB;
-        if (ti == tj) {
-          Kd[(size_t)ti * NB * NB + (i % NB) * NB + (j % NB)] = make_float2(K.h, K.l);
-          A[tri(i, j)] = 0.0f;
-        } else {
-          A[tri(i, j)] = K.h;
-        }
+        // diagonal-tile entries start at 0 in A: A accumulates minus the updates
+        A[tri(i, j)] = (i / NB == j / NB) ? 0.0f : K.h;
         S[(size_t)j * N + i] = make_float2(K.h, K.l);
         S[(size_t)i * N + j] = make_float2(K.h, K.l);
         j += blockDim.x;
@@ -335,16 +355,16 @@ loglik_mixed_kernel(MixedArgs P) {
     for (int k0 = 0; k0 < N; k0 += NB) {
       const int k1 = min(k0 + NB, N), nbk = k1 - k0;
       if (warp == 0) {
-        // lane r holds row r of the tile: original (double-float) plus the
-        // accumulated FP32 updates (held negated in A), one exact subtraction
-        const float2* Kt = Kd + (size_t)(k0 / NB) * NB * NB;
+        // lane r holds row r of the tile: original (double-float, from the
+        // scratch matrix) plus the accumulated FP32 updates (held negated in
+        // A), one exact subtraction, then rounded to FP32
         const int r = lane;
         float row[NB];
 #pragma unroll
         for (int c = 0; c < NB; ++c) {
           float v = 0.0f;
           if (r < nbk && c <= r) {
-            const float2 k = Kt[r * NB + c];
+            const float2 k = S[(size_t)(k0 + c) * N + (k0 + r)];
             const df s = two_sum(k.x, A[tri(k0 + r, k0 + c)]);
             v = __fadd_rn(s.h, __fadd_rn(s.l, k.y));
           }
@@ -381,7 +401,9 @@ loglik_mixed_kernel(MixedArgs P) {
       }
       __syncthreads();
       if (s_fail) break;
-      // panel solve: rows k1..N, A(i, k0:k1) <- A(i, k0:k1) L_kk^{-T}
+      // panel solve: rows k1..N, A(i, k0:k1) <- A(i, k0:k1) L_kk^{-T}; the panel
+      // is also stored as the update operand (FP32 column-major, or BF16 pieces)
+      const int T = N + 1 - k1;  // trailing rows k1..N (the last one is y)
       for (int i = k1 + threadIdx.x; i <= N; i += blockDim.x) {
         float v[NB];
         float* Ai = A + tri(i, 0) + k0;
@@ -398,83 +420,188 @@ loglik_mixed_kernel(MixedArgs P) {
             v[c] = s * idiag[k0 + c];
           }
         }
+        const int row = i - k1;
 #pragma unroll
-        for (int c = 0; c < NB; ++c)
+        for (int c = 0; c < NB; ++c) {
           if (c < nbk) Ai[c] = v[c];
-      }
-      __syncthreads();
-      // trailing update of rows k1..N, columns k1..min(i, N-1), 4x4 register blocks
-      const int T = N + 1 - k1;
-      if (T > 0) {
-        const int RB = (T + 3) >> 2;
-        const int nblk = RB * (RB + 1) / 2;
-        int bi = 0, bj = threadIdx.x;
-        while (bj > bi) { bj -= bi + 1; ++bi; }
-        for (int l = threadIdx.x; l < nblk; l += blockDim.x) {
-          const int i0 = k1 + 4 * bi, j0 = k1 + 4 * bj;
-          float acc[4][4];
-#pragma unroll
-          for (int p = 0; p < 4; ++p)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[p][q] = 0.0f;
-          const float* Ar[4];
-          const float* Ac[4];
-#pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            Ar[p] = A + tri(min(i0 + p, N), 0) + k0;
-            Ac[p] = A + tri(min(j0 + p, N), 0) + k0;
+          if (TC) {
+            const __nv_bfloat16 bh = __float2bfloat16_rn(v[c]);
+            const float rr = v[c] - __bfloat162float(bh);           // exact
+            const __nv_bfloat16 bm = __float2bfloat16_rn(rr);
+            const __nv_bfloat16 bl = __float2bfloat16_rn(rr - __bfloat162float(bm));
+            const uint32_t o = umma::op_offset(row, c);
+            *(__nv_bfloat16*)(opnd + o) = bh;
+            *(__nv_bfloat16*)(opnd + opnd_piece + o) = bm;
+            *(__nv_bfloat16*)(opnd + 2 * opnd_piece + o) = bl;
+          } else {
+            Pt[c * PS + row] = v[c];
           }
-          for (int k = 0; k < nbk; ++k) {
-            float ar[4], ac[4];
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-              ar[p] = Ar[p][k];
-              ac[p] = Ac[p][k];
-            }
+        }
+      }
+      if (!TC) {
+        // pad rows T .. round4(T) of the panel with zeros (read by the 4-row blocks)
+        for (int e = threadIdx.x; e < NB * 4; e += blockDim.x) {
+          const int c = e >> 2, row = T + (e & 3);
+          if (row < PS) Pt[c * PS + row] = 0.0f;
+        }
+      }
+      if (TC) umma::fence_proxy_async();
+      __syncthreads();
+      const int ncols_all = T - 1;  // matrix columns k1..N-1
+      if (!TC) {
+        // trailing update on the CUDA cores: 4 x 4 register blocks over the
+        // lower triangle, both operands read as float4 from the panel copy
+        if (ncols_all > 0) {
+          const int RB = (T + 3) >> 2;
+          const int nblk = RB * (RB + 1) / 2;
+          int bi = 0, bj = threadIdx.x;
+          while (bj > bi) { bj -= bi + 1; ++bi; }
+          for (int l = threadIdx.x; l < nblk; l += blockDim.x) {
+            float acc[4][4];
 #pragma unroll
             for (int p = 0; p < 4; ++p)
 #pragma unroll
-              for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(ar[p], ac[q], acc[p][q]);
-          }
+              for (int q = 0; q < 4; ++q) acc[p][q] = 0.0f;
+#pragma unroll 4
+            for (int k = 0; k < nbk; ++k) {
+              const float4 ar = *(const float4*)(Pt + k * PS + 4 * bi);
+              const float4 ac = *(const float4*)(Pt + k * PS + 4 * bj);
+              const float rr[4] = {ar.x, ar.y, ar.z, ar.w};
+              const float cc[4] = {ac.x, ac.y, ac.z, ac.w};
 #pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            const int ii = i0 + p;
-            if (ii > N) continue;
+              for (int p = 0; p < 4; ++p)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int jj = j0 + q;
-              if (jj <= ii && jj < N) A[tri(ii, jj)] -= acc[p][q];
+                for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(rr[p], cc[q], acc[p][q]);
             }
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+              const int ii = k1 + 4 * bi + p;
+              if (ii > N) continue;
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const int jj = k1 + 4 * bj + q;
+                if (jj <= ii && jj < N) A[tri(ii, jj)] -= acc[p][q];
+              }
+            }
+            bj += blockDim.x;
+            while (bj > bi) { bj -= bi + 1; ++bi; }
           }
-          bj += blockDim.x;
-          while (bj > bi) { bj -= bi + 1; ++bi; }
+        }
+      } else {
+        // trailing update on the tensor cores: for each 128-row tile of P and
+        // each chunk of <= 128 columns, BF16 MMAs accumulate in TMEM (FP32):
+        // hi.hi alone in one accumulator, the five smaller cross products
+        // (lo.hi, hi.lo, mid.mid, mid.hi, hi.mid, small first) in a second
+        // one, so that no small product is added to a large partial sum
+        // inside the tensor core; the epilogue subtracts both from A.
+        for (int r0 = 0; r0 < T && ncols_all > 0; r0 += 128) {
+          const int ncols = min(r0 + 128, ncols_all);
+          for (int c0 = 0; c0 < ncols; c0 += 128) {
+            const int nc = min(128, ((ncols - c0 + 15) / 16) * 16);
+            if (threadIdx.x == 0) {
+              umma::fence_after_sync();
+              const uint32_t sb = umma::smem_u32(opnd);
+              const uint32_t idesc = umma::idesc_bf16_f32(128, nc);
+              const uint32_t arow = (uint32_t)(r0 / 8) * 256, brow = (uint32_t)(c0 / 8) * 256;
+              const int pa[6] = {0, 2, 0, 1, 1, 0}, pb[6] = {0, 0, 2, 1, 0, 1};
+#pragma unroll
+              for (int q = 0; q < 6; ++q) {
+                const uint64_t ad = umma::smem_desc(sb + pa[q] * opnd_piece + arow, 128, 256);
+                const uint64_t bd = umma::smem_desc(sb + pb[q] * opnd_piece + brow, 128, 256);
+                umma::mma_bf16(tmem_base + (q == 0 ? 0u : 128u), ad, bd, idesc, q > 1);
+              }
+              umma::mma_commit(&mma_bar);
+            }
+            const bool done = umma::mbar_wait(&mma_bar, mma_phase, 1u << 24);
+            mma_phase ^= 1u;
+            if (!done && threadIdx.x == 0) s_timeout = 1;
+            umma::fence_after_sync();
+            if (done) {
+              const int q = warp & 3, half = warp >> 2;
+              const int ii = k1 + r0 + 32 * q + lane;  // matrix row of this lane
+              for (int cc = half * 16; cc < nc; cc += 32) {
+                float dv[16], ds[16];
+                const uint32_t ta = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)cc;
+                umma::tmem_ld16(ta, dv);
+                umma::tmem_ld16(ta + 128u, ds);
+                umma::tmem_wait_ld();
+                if (ii <= N) {
+#pragma unroll
+                  for (int e = 0; e < 16; ++e) {
+                    const int jj = k1 + c0 + cc + e;
+                    if (jj <= ii && jj < N) A[tri(ii, jj)] = (A[tri(ii, jj)] - ds[e]) - dv[e];
+                  }
+                }
+              }
+            }
+            umma::fence_before_sync();
+            __syncthreads();
+            if (s_timeout) break;
+          }
+          if (s_timeout) break;
+        }
+        if (s_timeout) {
+          if (threadIdx.x == 0) s_fail = 2;
+          break;
         }
       }
       __syncthreads();
     }
     if (s_fail) {
       if (threadIdx.x == 0) {
+        const int code = s_fail == 2 ? SBV_ETIMEOUT : SBV_ENOTSPD;
         a.terms[item] = __longlong_as_double(0x7ff8000000000000ll);
-        if (a.status) a.status[item] = SBV_ENOTSPD;
-        record_failure(a.dstat, SBV_ENOTSPD, (int)blk, th_i);
+        if (a.status) a.status[item] = code;
+        record_failure(a.dstat, code, (int)blk, th_i);
       }
       __syncthreads();
+      if (s_timeout) break;  // leave the item loop; TMEM is released below
       continue;
     }
-    // ---- 4. x0 = L^-T w0, x0J = L_JJ^-T w0_J  (w0 = row N of A)
+    // ---- 4. diagonal tiles -> their inverses (one warp per tile, lane = row)
+    for (int k0 = warp * NB; k0 < N; k0 += MX_WARPS * NB) {
+      const int nbk = min(NB, N - k0);
+      const int r = lane;
+      float Lr[NB], Xr[NB];
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        Lr[c] = (r < nbk && c <= r) ? A[tri(k0 + r, k0 + c)] : 0.0f;
+        Xr[c] = (c == r) ? 1.0f : 0.0f;
+      }
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        if (c < nbk) {
+          if (r == c) {
+#pragma unroll
+            for (int q = 0; q < NB; ++q) Xr[q] *= idiag[k0 + c];
+          }
+#pragma unroll
+          for (int q = 0; q < NB; ++q) {
+            const float xc = __shfl_sync(0xffffffffu, Xr[q], c);
+            if (r > c) Xr[q] = fmaf(-Lr[c], xc, Xr[q]);
+          }
+        }
+      }
+      if (r < nbk) {
+#pragma unroll
+        for (int c = 0; c < NB; ++c)
+          if (c <= r) A[tri(k0 + r, k0 + c)] = Xr[c];
+      }
+    }
+    __syncthreads();
+    // ---- x0 = L^-T w0, x0J = L_JJ^-T w0_J  (w0 = row N of A)
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
       const float w = A[tri(N, p)];
       x0[p] = w;
       x0J[p] = p < mb ? w : 0.0f;
     }
     __syncthreads();
-    bwd_solve2(A, idiag, N, x0, x0J);
+    bwd_solve2(A, N, x0, x0J);
     // ---- 5. residuals in double-float; all warps: (32-row group, column chunk) tasks
     {
       const int G = (N + 31) / 32;
       const int CH = max(1, MX_WARPS / G);
       const int chunk = (N + CH - 1) / CH;
-      float4* part = (float4*)(smem + lay.off_part);  // [CH][N] partial (h1, l1, h2, l2)
       for (int task = warp; task < G * CH; task += MX_WARPS) {
         const int g = task / CH, c = task % CH;
         const int i = g * 32 + lane;
@@ -520,10 +647,10 @@ loglik_mixed_kernel(MixedArgs P) {
       __syncthreads();
     }
     // corrections: (L L^T)^{-1} r and (L_JJ L_JJ^T)^{-1} r_J
-    fwd_solve2(A, idiag, N, r1, r2);
+    fwd_solve2(A, N, r1, r2);
     for (int p = mb + threadIdx.x; p < N; p += blockDim.x) r2[p] = 0.0f;
     __syncthreads();
-    bwd_solve2(A, idiag, N, r1, r2);
+    bwd_solve2(A, N, r1, r2);
     // ---- 6. log-determinant and quadratic forms, summed in FP64
     double v = 0.0;
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
@@ -545,6 +672,14 @@ loglik_mixed_kernel(MixedArgs P) {
       if (!ok) record_failure(a.dstat, SBV_ENOTSPD, (int)blk, th_i);
     }
     __syncthreads();
+  }
+  if (TC) {
+    // after a timed-out wait, give the outstanding MMAs one more bounded wait
+    // before the accumulator columns are released
+    if (s_timeout) umma::mbar_wait(&mma_bar, mma_phase ^ 1u, 1u << 24);
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_dealloc(tmem_base, 256);
   }
 }
 
@@ -568,24 +703,17 @@ static int upload_df_consts(sbv_ctx* ctx) {
   return SBV_OK;
 }
 
-int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a0, int nmax, cudaStream_t s) {
+int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a0, int nmax, int precision,
+                        cudaStream_t s) {
   int st = 0;
   if ((st = upload_df_consts(ctx))) return st;
+  const bool tc = precision == SBV_PREC_MIXED_BF16;
   MixedArgs P;
   P.a = a0;
   const int ncap = std::max(nmax, 1);
-  P.lay = mixed_layout(ncap, a0.d);
-  // residual partials (CH x N float4) reuse the coordinate area
-  const int G = (ncap + 31) / 32;
-  const int CH = std::max(1, MX_WARPS / G);
-  const size_t need_part = (size_t)CH * ncap * sizeof(float4);
-  const size_t have_part = P.lay.off_A - P.lay.off_vh;
-  if (need_part > have_part) {
-    const size_t extra = align_up(need_part - have_part, 16);
-    P.lay.off_A += extra;
-    P.lay.bytes += extra;
-  }
-  if (P.lay.bytes + 4096 > ctx->smem_optin)
+  P.lay = mixed_layout(ncap, a0.d, tc);
+  const size_t static_smem = 2 * 256 * 4 + 1024;
+  if (P.lay.bytes + static_smem > ctx->smem_optin)
     return fail(ctx, SBV_EUNSUPPORTED,
                 "mixed path: a block with N=%d (d=%d) needs %zu bytes of shared memory", nmax,
                 a0.d, P.lay.bytes);
@@ -601,18 +729,26 @@ int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a0, int nmax, cudaStream
   } else {
     P.Xs = nullptr;
   }
-  const size_t static_smem = 2 * 256 * 4 + 1024;
-  int per_sm = (int)std::max<size_t>(1, (228 * 1024) / (P.lay.bytes + static_smem + 1024));
+  // 228 KB of shared memory per SM, 1 KB reserved per resident CTA
+  const size_t per_cta = P.lay.bytes + static_smem + 1024;
+  int per_sm = (int)std::max<size_t>(1, (228 * 1024) / per_cta);
   int grid = ctx->num_sms * std::min(per_sm, 2);
   int64_t items = a0.bc * (int64_t)a0.B;
   if (grid > items) grid = (int)items;
   P.scratch_stride = align_up((size_t)ncap * ncap, 64);
   P.scratch = (float2*)ws_get(ctx, WS_MATRIX, P.scratch_stride * grid * sizeof(float2), &st);
   if (!P.scratch) return st;
-  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)P.lay.bytes));
-  loglik_mixed_kernel<<<grid, MX_THREADS, P.lay.bytes, s>>>(P);
+  if (tc) {
+    SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)P.lay.bytes));
+    loglik_mixed_kernel<true><<<grid, MX_THREADS, P.lay.bytes, s>>>(P);
+  } else {
+    SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)P.lay.bytes));
+    loglik_mixed_kernel<false><<<grid, MX_THREADS, P.lay.bytes, s>>>(P);
+  }
   SBV_LAUNCH_CHECK(ctx, "loglik_mixed_kernel");
   return SBV_OK;
 }

@@ -182,7 +182,8 @@ extern "C" int sbv_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* 
   if (m < 0) return fail(ctx, SBV_EINVAL, "m=%d must be >= 0", m);
   if ((st = check_theta(ctx, theta, B, d))) return st;
   if (!nu_ok(nu2)) return fail(ctx, SBV_EINVAL, "nu2=%d not in {1,3,5,7}", nu2);
-  if (precision != SBV_PREC_FP64 && precision != SBV_PREC_MIXED)
+  if (precision != SBV_PREC_FP64 && precision != SBV_PREC_MIXED &&
+      precision != SBV_PREC_MIXED_BF16)
     return fail(ctx, SBV_EINVAL, "precision=%d unknown", precision);
   return run_loglik(ctx, X, dtype, y, n, d, ptr, pts, nbr, cnt, bc, m, theta, B, nu2,
                     precision, ll, block_terms, status, (cudaStream_t)stream);
@@ -222,7 +223,8 @@ extern "C" int sbv_predict(sbv_ctx* ctx, const void* X, int dtype, const double*
     return fail(ctx, SBV_EUNSUPPORTED, "m_pred=%d above %d", m_pred, SBV_MAX_BLOCK_N - 1);
   if ((st = check_theta(ctx, theta, 1, d))) return st;
   if (!nu_ok(nu2)) return fail(ctx, SBV_EINVAL, "nu2=%d not in {1,3,5,7}", nu2);
-  if (precision != SBV_PREC_FP64 && precision != SBV_PREC_MIXED)
+  if (precision != SBV_PREC_FP64 && precision != SBV_PREC_MIXED &&
+      precision != SBV_PREC_MIXED_BF16)
     return fail(ctx, SBV_EINVAL, "precision=%d unknown", precision);
   cudaStream_t s = (cudaStream_t)stream;
   size_t zbytes = (size_t)(n + ntest) * d * sizeof(double);

@@ -15,7 +15,11 @@ from synth.inputs import uniform_points, standard_normal, workload
 pytestmark = pytest.mark.gpu
 
 TOL_FP64 = 1e-9    # |dl| / n, FP64 path
-TOL_MIXED = 1e-6   # |dl| / n, mixed path
+TOL_MIXED = 1e-6   # |dl| / n, mixed path (FP32 trailing updates on the CUDA cores)
+# split-BF16 tensor-core trailing updates: the tensor core's FP32 accumulation
+# rounds differently from FMA; on the tau^2 = 1e-4 workload it measures ~1e-6
+TOL_MIXED_BF16 = 3e-6
+TOLS = {"fp64": TOL_FP64, "mixed": TOL_MIXED, "mixed_bf16": TOL_MIXED_BF16}
 
 
 @pytest.fixture(scope="module")
@@ -155,7 +159,7 @@ def gpu_loglik(ctx, X, y, b, theta, nu2, precision, terms=True):
     return np_(ll), (np_(bt) if terms else None), np_(st)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("mixed", TOL_MIXED)])
+@pytest.mark.parametrize("precision,tol", list(TOLS.items()))
 def test_loglik_matches_oracle(ctx, gp5d, gp5d_oracle, precision, tol):
     b, th = gp5d_oracle, gp5d["theta"][0]
     ll, bt, st = gpu_loglik(ctx, gp5d["X"], gp5d["y"], b, th, 5, precision)
@@ -172,7 +176,7 @@ def test_loglik_matches_oracle(ctx, gp5d, gp5d_oracle, precision, tol):
     assert abs(ll[0] - want) / n <= tol
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", list(TOLS))
 def test_loglik_batched_theta(ctx, gp5d, gp5d_oracle, precision):
     b = gp5d_oracle
     rng = np.random.default_rng(2)
@@ -185,7 +189,7 @@ def test_loglik_batched_theta(ctx, gp5d, gp5d_oracle, precision):
         ths.append(th)
     ths = np.array(ths)
     ll, _, st = gpu_loglik(ctx, gp5d["X"], gp5d["y"], b, ths, 5, precision, terms=False)
-    tol = TOL_FP64 if precision == "fp64" else TOL_MIXED
+    tol = TOLS[precision]
     for i, th in enumerate(ths):
         want = sbv.loglik(gp5d["X"], gp5d["y"], b["ptr"], b["pts"], b["nbr"], b["cnt"], b["rank"], th, 5)
         assert abs(ll[i] - want) / gp5d["n"] <= tol
