@@ -145,6 +145,11 @@ int sbv_knn(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_t d,
  *   y                  device, n doubles, observations
  *   ptr, pts           device, block CSR from sbv_blocking (bc blocks)
  *   nbr, cnt           device, neighbours from sbv_knn (row stride m)
+ *   nmax               largest m_i + bs_i over the blocks, or 0: the call then
+ *                      computes it (one small kernel and a device-to-host read
+ *                      that waits for `stream`).  A value below the true
+ *                      largest size is safe: the blocks above it get status
+ *                      SBV_EUNSUPPORTED and a NaN term.
  *   theta              host, B x (2+d) doubles, rows (sigma^2, tau^2, beta_1..beta_d)
  *   nu2                2*nu in {1, 3, 5, 7}
  *   precision          SBV_PREC_FP64, SBV_PREC_MIXED or SBV_PREC_MIXED_BF16
@@ -171,8 +176,9 @@ int sbv_knn(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_t d,
 int sbv_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y,
                int64_t n, int32_t d, const int64_t* ptr, const int32_t* pts,
                const int32_t* nbr, const int32_t* cnt, int64_t bc, int32_t m,
-               const double* theta, int32_t B, int32_t nu2, int32_t precision,
-               double* ll, double* block_terms, int32_t* status, void* stream);
+               int32_t nmax, const double* theta, int32_t B, int32_t nu2,
+               int32_t precision, double* ll, double* block_terms, int32_t* status,
+               void* stream);
 
 /*
  * sbv_sync_status -- wait for `stream`, then report whether any sbv_loglik or

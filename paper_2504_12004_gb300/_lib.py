@@ -36,7 +36,7 @@ SIGNATURES = {
     "sbv_knn": (C.c_int, [_P, _P, C.c_int, _I64, _I32, _P, _P, _P, _P, _P, _I64, _I32,
                           _P, _P, _P]),
     "sbv_loglik": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64, _I32,
-                             _P, _I32, _I32, _I32, _P, _P, _P, _P]),
+                             _I32, _P, _I32, _I32, _I32, _P, _P, _P, _P]),
     "sbv_sync_status": (C.c_int, [_P, _P]),
     "sbv_predict": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _I64, _P, _I32, _P,
                               _I32, _I32, _P, _P, _P, _P, _P]),
@@ -169,8 +169,11 @@ class Context:
         return nbr[:, :m], cnt
 
     def sbv_loglik(self, X, y, ptr, pts, nbr, cnt, theta, nu2: int = 5, precision="fp64",
-                   ll=None, block_terms=None, status=None, stream=None):
-        """Enqueue the log-likelihood of every theta row; returns the device tensor ll (B)."""
+                   ll=None, block_terms=None, status=None, stream=None, nmax: int = 0):
+        """Enqueue the log-likelihood of every theta row; returns the device tensor ll (B).
+
+        nmax: largest m_i + bs_i (see max_block_size); 0 lets the call read it
+        from the device, which waits for the stream."""
         X = _dev(X, None, "X")
         n, d = X.shape
         bc = cnt.numel()
@@ -184,10 +187,15 @@ class Context:
         rc = self.lib.sbv_loglik(self.h, _ptr(X), _xdtype(X), _ptr(_dev(y, torch.float64, "y")), n, d,
                                  _ptr(_dev(ptr, torch.int64, "ptr")), _ptr(_dev(pts, torch.int32, "pts")),
                                  _ptr(nbr_c), _ptr(_dev(cnt, torch.int32, "cnt")), bc, m,
-                                 _ptr(th), B, nu2, prec, _ptr(ll), _ptr(block_terms), _ptr(status),
-                                 _stream(stream))
+                                 int(nmax), _ptr(th), B, nu2, prec, _ptr(ll), _ptr(block_terms),
+                                 _ptr(status), _stream(stream))
         self._check(rc)
         return ll
+
+    @staticmethod
+    def max_block_size(ptr, cnt) -> int:
+        """Largest m_i + bs_i, the nmax argument that spares sbv_loglik its device read."""
+        return int((torch.diff(ptr).to(torch.int64) + cnt.to(torch.int64)).max().item())
 
     def sbv_sync_status(self, stream=None):
         self._check(self.lib.sbv_sync_status(self.h, _stream(stream)))

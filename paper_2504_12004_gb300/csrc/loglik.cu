@@ -241,7 +241,25 @@ static int upload_theta(sbv_ctx* ctx, const double* h, int B, int d, ThetaDev** 
   size_t bytes = v.size() * sizeof(ThetaDev);
   ThetaDev* dth = (ThetaDev*)ws_get(ctx, WS_PARAMS, bytes, &st);
   if (!dth) return st;
-  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(dth, v.data(), bytes, cudaMemcpyHostToDevice, s));
+  // stage through a pinned ring slot so that the copy is truly asynchronous
+  if (ctx->ring_slot < bytes) {
+    SBV_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
+    ctx->h_ring = nullptr;
+    ctx->ring_slot = 0;
+    const size_t slot = ((bytes + 4095) / 4096) * 4096;
+    SBV_CUDA_TRY(ctx, cudaMallocHost((void**)&ctx->h_ring, slot * sbv_ctx::kRing));
+    ctx->ring_slot = slot;
+    for (auto& e : ctx->ring_ev)
+      if (!e) SBV_CUDA_TRY(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  const int k = ctx->ring_next;
+  ctx->ring_next = (k + 1) % sbv_ctx::kRing;
+  SBV_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ring_ev[k]));  // previous copy from this slot done
+  unsigned char* slot = ctx->h_ring + (size_t)k * ctx->ring_slot;
+  memcpy(slot, v.data(), bytes);
+  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(dth, slot, bytes, cudaMemcpyHostToDevice, s));
+  SBV_CUDA_TRY(ctx, cudaEventRecord(ctx->ring_ev[k], s));
   *out = dth;
   return SBV_OK;
 }
@@ -267,13 +285,13 @@ int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a, int nmax, int precisi
 
 int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n, int d,
                const int64_t* ptr, const int32_t* pts, const int32_t* nbr, const int32_t* cnt,
-               int64_t bc, int m, const double* h_theta, int B, int nu2, int precision,
-               double* ll, double* terms, int32_t* status, cudaStream_t s) {
+               int64_t bc, int m, int nmax_hint, const double* h_theta, int B, int nu2,
+               int precision, double* ll, double* terms, int32_t* status, cudaStream_t s) {
   int st = 0;
   if ((uint64_t)bc * (uint64_t)B >= 0xffffffffull)
     return fail(ctx, SBV_EUNSUPPORTED, "bc*B too large");
-  int nmax = 0;
-  if ((st = structure_max_n(ctx, ptr, cnt, bc, &nmax, s))) return st;
+  int nmax = nmax_hint;
+  if (nmax <= 0 && (st = structure_max_n(ctx, ptr, cnt, bc, &nmax, s))) return st;
   if (nmax > SBV_MAX_BLOCK_N)
     return fail(ctx, SBV_EUNSUPPORTED, "a block has m_i + bs_i = %d > %d", nmax, SBV_MAX_BLOCK_N);
   ThetaDev* dth = nullptr;

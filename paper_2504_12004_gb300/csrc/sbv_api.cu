@@ -87,6 +87,9 @@ extern "C" void sbv_destroy(sbv_ctx* ctx) {
   for (auto& b : ctx->ws)
     if (b.p) cudaFree(b.p);
   if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
+  for (auto& e : ctx->ring_ev)
+    if (e) cudaEventDestroy(e);
   delete ctx;
 }
 
@@ -172,8 +175,9 @@ extern "C" int sbv_knn(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_
 extern "C" int sbv_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y,
                           int64_t n, int32_t d, const int64_t* ptr, const int32_t* pts,
                           const int32_t* nbr, const int32_t* cnt, int64_t bc, int32_t m,
-                          const double* theta, int32_t B, int32_t nu2, int32_t precision,
-                          double* ll, double* block_terms, int32_t* status, void* stream) {
+                          int32_t nmax, const double* theta, int32_t B, int32_t nu2,
+                          int32_t precision, double* ll, double* block_terms,
+                          int32_t* status, void* stream) {
   int st = check_common(ctx, X, dtype, n, d);
   if (st) return st;
   if (!y || !ptr || !pts || !cnt || !ll || (m > 0 && !nbr))
@@ -185,7 +189,8 @@ extern "C" int sbv_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* 
   if (precision != SBV_PREC_FP64 && precision != SBV_PREC_MIXED &&
       precision != SBV_PREC_MIXED_BF16)
     return fail(ctx, SBV_EINVAL, "precision=%d unknown", precision);
-  return run_loglik(ctx, X, dtype, y, n, d, ptr, pts, nbr, cnt, bc, m, theta, B, nu2,
+  if (nmax < 0) return fail(ctx, SBV_EINVAL, "nmax=%d must be >= 0", nmax);
+  return run_loglik(ctx, X, dtype, y, n, d, ptr, pts, nbr, cnt, bc, m, nmax, theta, B, nu2,
                     precision, ll, block_terms, status, (cudaStream_t)stream);
 }
 

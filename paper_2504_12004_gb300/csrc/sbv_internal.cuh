@@ -34,6 +34,13 @@ struct sbv_ctx {
   std::string err;
   sbv::DevStatus* d_status = nullptr;  // device record
   sbv::DevBuf ws[16];                  // named workspace slots
+  // pinned host ring for parameter rows: slot k is reused only after the
+  // event recorded behind its previous copy has completed
+  static const int kRing = 8;
+  unsigned char* h_ring = nullptr;
+  size_t ring_slot = 0;
+  cudaEvent_t ring_ev[kRing] = {};
+  int ring_next = 0;
 };
 
 namespace sbv {
@@ -90,8 +97,8 @@ int run_knn_all(sbv_ctx* ctx, const double* Z, int64_t n, int d,
 // likelihood and prediction
 int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n,
                int d, const int64_t* ptr, const int32_t* pts, const int32_t* nbr,
-               const int32_t* cnt, int64_t bc, int m, const double* h_theta, int B,
-               int nu2, int precision, double* ll, double* terms, int32_t* status,
+               const int32_t* cnt, int64_t bc, int m, int nmax, const double* h_theta,
+               int B, int nu2, int precision, double* ll, double* terms, int32_t* status,
                cudaStream_t s);
 int run_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n,
                 int d, const void* Xt, int64_t nt, const int32_t* nbr, int m,

@@ -42,8 +42,8 @@ def test_binding_signatures_cover_header(lib):
 def test_null_context_is_rejected_without_device(lib):
     assert lib.sbv_version() >= 100
     assert lib.sbv_last_error(None) == b"null context"
-    rc = lib.sbv_loglik(None, None, 0, None, 0, 0, None, None, None, None, 0, 0, None, 0, 0, 0,
-                        None, None, None, None)
+    rc = lib.sbv_loglik(None, None, 0, None, 0, 0, None, None, None, None, 0, 0, 0, None, 0, 0,
+                        0, None, None, None, None)
     assert rc == 1  # SBV_EINVAL
     rc = lib.sbv_blocking(None, None, 0, 0, 0, None, 0, 0, 0, None, None, None, None, None, None,
                           None)
