@@ -214,6 +214,50 @@ int sbv_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y,
                 int32_t nu2, int32_t precision, double* mean, double* var,
                 double* var_latent, int32_t* nbr, void* stream);
 
+/* Limits of the fixed scratch array of sbv_loglik_fp64_noalloc (about 8.1 MB
+ * per GPU that loads the library, held until the process exits). */
+#define SBV_NOALLOC_MAX_THETA 64          /* parameter rows per call */
+#define SBV_NOALLOC_MAX_TERMS (1 << 20)   /* bc * B when block_terms is NULL */
+
+/*
+ * sbv_loglik_fp64_noalloc -- sbv_loglik in FP64 (SBV_PREC_FP64) without any
+ * allocation.  The paper has no counterpart: this entry point exists for
+ * callers that may not allocate device memory while they run, e.g. a serving
+ * loop whose device memory belongs to another allocator (a framework's
+ * caching allocator or a fixed budget, which a library-side cudaMalloc could
+ * exceed or fragment) or a latency-bound loop that cannot afford the implicit
+ * synchronisation of cudaMalloc/cudaFree.  It never calls cudaMalloc,
+ * cudaFree or any other allocating routine, on the device or the host.
+ *
+ * Arguments and results are those of sbv_loglik (same layouts, same
+ * per-block terms, bit-identical totals for the same inputs), with these
+ * differences:
+ *   - no context: the call runs on the current CUDA device and reports only
+ *     its return code (no message); device-side failures show in `status`
+ *     and as NaN terms;
+ *   - B <= SBV_NOALLOC_MAX_THETA; when block_terms is NULL, bc * B <=
+ *     SBV_NOALLOC_MAX_TERMS; every block (nmax + its coordinates) must fit in
+ *     shared memory.  Beyond these limits the call returns SBV_EUNSUPPORTED
+ *     before doing any work;
+ *   - nmax = 0 makes the call compute the largest block size with one small
+ *     kernel and a read into a host variable, which waits for `stream`.
+ * All scratch (derived parameter rows, block terms when block_terms is NULL,
+ * the work counter and the failure record) lives in one file-scope device
+ * array shared by every call; it keeps the last call's contents, and the call
+ * clears the parts that must start at zero.  Calls that overlap on the GPU
+ * (on different streams, or from different host threads) use the same array
+ * and race: serialise them.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.
+ * Errors: SBV_EINVAL, SBV_EUNSUPPORTED (limits above), SBV_ECUDA.
+ */
+int sbv_loglik_fp64_noalloc(const void* X, int dtype, const double* y, int64_t n,
+                            int32_t d, const int64_t* ptr, const int32_t* pts,
+                            const int32_t* nbr, const int32_t* cnt, int64_t bc,
+                            int32_t m, int32_t nmax, const double* theta, int32_t B,
+                            int32_t nu2, double* ll, double* block_terms,
+                            int32_t* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,6 +40,8 @@ SIGNATURES = {
     "sbv_sync_status": (C.c_int, [_P, _P]),
     "sbv_predict": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _I64, _P, _I32, _P,
                               _I32, _I32, _P, _P, _P, _P, _P]),
+    "sbv_loglik_fp64_noalloc": (C.c_int, [_P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64,
+                                          _I32, _I32, _P, _I32, _I32, _P, _P, _P, _P]),
 }
 
 
