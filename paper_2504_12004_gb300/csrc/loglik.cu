@@ -282,6 +282,9 @@ static int structure_max_n(sbv_ctx* ctx, const int64_t* ptr, const int32_t* cnt,
 
 int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a, int nmax, int precision,
                         cudaStream_t s);
+int launch_predict_mixed(sbv_ctx* ctx, const LoglikArgs& a0, const void* Xt, int64_t nt,
+                         double* mean, double* var, double* var_latent, int precision,
+                         cudaStream_t s);
 
 int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n, int d,
                const int64_t* ptr, const int32_t* pts, const int32_t* nbr, const int32_t* cnt,
@@ -448,16 +451,32 @@ int run_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t
                 const void* Xt, int64_t nt, const int32_t* nbr, int m, const double* h_theta,
                 int nu2, int precision, double* mean, double* var, double* var_latent,
                 cudaStream_t s) {
-  (void)n;
   int st = 0;
-  if (precision != SBV_PREC_FP64)
-    return fail(ctx, SBV_EUNSUPPORTED, "prediction runs in FP64 only");
   ThetaDev* dth = nullptr;
   if ((st = upload_theta(ctx, h_theta, 1, d, &dth, s))) return st;
   unsigned int* counter = (unsigned int*)ws_get(ctx, WS_SMALL, 64, &st);
   if (!counter) return st;
   counter += 4;
   SBV_CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
+  if (precision != SBV_PREC_FP64) {
+    LoglikArgs la;
+    memset(&la, 0, sizeof(la));
+    la.X = X;
+    la.dtype = dtype;
+    la.y = y;
+    la.n = n;
+    la.d = d;
+    la.nbr = nbr;
+    la.bc = nt;
+    la.m = m;
+    la.theta = dth;
+    la.B = 1;
+    la.nu2 = nu2;
+    la.ncap = m + 1;
+    la.dstat = ctx->d_status;
+    la.counter = counter;
+    return launch_predict_mixed(ctx, la, Xt, nt, mean, var, var_latent, precision, s);
+  }
   PredictArgs a;
   a.X = X;
   a.Xt = Xt;

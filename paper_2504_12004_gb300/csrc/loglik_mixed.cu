@@ -69,7 +69,8 @@ __host__ __device__ inline MixedLayout mixed_layout(int ncap, int d, bool tc) {
   L.opnd_piece = (uint32_t)(((ncap + 1 + 127) / 128) * 128 * 32);
   size_t o = 0;
   L.off_y = o;  o += align_up((size_t)(ncap + 1) * sizeof(float2), 16);
-  L.off_v = o;  o += align_up((size_t)6 * (ncap + 1) * sizeof(float), 16);  // x0 x0J r1 r2 ldiag idiag
+  // x0 x0J r1 r2 ldiag idiag c1 c2 (c: corrections accumulated over refinement steps)
+  L.off_v = o;  o += align_up((size_t)8 * (ncap + 1) * sizeof(float), 16);
   o = align_up(o, 128);
   const size_t coord = align_up((size_t)d * ncap * sizeof(float), 16);
   size_t uni = 2 * coord;
@@ -179,9 +180,15 @@ struct MixedArgs {
   float2* scratch;
   size_t scratch_stride;
   MixedLayout lay;
+  // prediction mode: one item per test point, J = its m nearest training points
+  const void* Xt;        // test points (dtype of a.X)
+  int64_t nt;
+  double* mean;
+  double* var;
+  double* var_latent;
 };
 
-template <bool TC>
+template <bool TC, bool PRED>
 __global__ void __launch_bounds__(MX_THREADS, 2)
 loglik_mixed_kernel(MixedArgs P) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -209,7 +216,7 @@ loglik_mixed_kernel(MixedArgs P) {
   const int d = a.d, cap = lay.ncap, PS = lay.pstride;
   const uint32_t opnd_piece = lay.opnd_piece;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const unsigned int total = (unsigned int)(a.bc * a.B);
+  const unsigned int total = PRED ? (unsigned int)P.nt : (unsigned int)(a.bc * a.B);
   const double log2pi = 1.8378770664093454836;
   float* x0 = vec;
   float* x0J = vec + (cap + 1);
@@ -217,6 +224,12 @@ loglik_mixed_kernel(MixedArgs P) {
   float* r2 = vec + 3 * (cap + 1);
   float* ldiag = vec + 4 * (cap + 1);
   float* idiag = vec + 5 * (cap + 1);
+  float* c1 = vec + 6 * (cap + 1);
+  float* c2 = vec + 7 * (cap + 1);
+  // refinement steps: one for the likelihood (its quadratic forms are second
+  // order in the solve error); three for prediction, whose variance
+  // sigma^2 + tau^2 - Sigma_*J z cancels and is first order in the error of z
+  constexpr int NREF = PRED ? 3 : 1;
 
   for (int i = threadIdx.x; i < 256; i += blockDim.x) {
     tab_h[i] = C.tab_h[i];
@@ -240,25 +253,38 @@ loglik_mixed_kernel(MixedArgs P) {
     __syncthreads();
     const unsigned int item = s_item;
     if (item >= total) break;
-    const int th_i = (int)(item / a.bc);
-    const int64_t blk = (int64_t)(item % a.bc);
+    // loglik: item = (theta row, block); prediction: item = test point with
+    // J = its m nearest training points and the test point as the block
+    const int th_i = PRED ? 0 : (int)(item / a.bc);
+    const int64_t blk = PRED ? (int64_t)item : (int64_t)(item % a.bc);
     const ThetaDev& th = a.theta[th_i];
-    const int bs = (int)(a.ptr[blk + 1] - a.ptr[blk]);
-    const int mb = a.cnt[blk];
+    const int bs = PRED ? 1 : (int)(a.ptr[blk + 1] - a.ptr[blk]);
+    const int mb = PRED ? a.m : a.cnt[blk];
     const int N = mb + bs;
     if (N > cap) {
       if (threadIdx.x == 0) {
-        a.terms[item] = __longlong_as_double(0x7ff8000000000000ll);
-        if (a.status) a.status[item] = SBV_EUNSUPPORTED;
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        if (PRED) {
+          P.mean[item] = nan;
+          P.var[item] = nan;
+          P.var_latent[item] = nan;
+        } else {
+          a.terms[item] = nan;
+          if (a.status) a.status[item] = SBV_EUNSUPPORTED;
+        }
         record_failure(a.dstat, SBV_EUNSUPPORTED, (int)blk, th_i);
       }
       __syncthreads();
       continue;
     }
-    const int64_t base = a.ptr[blk];
+    const int64_t base = PRED ? 0 : a.ptr[blk];
     // ---- 1. gather and scale in double-float; centre on point 0
     if (threadIdx.x == 0) s_fail = 0;
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
+      if (PRED && p == mb) {
+        yv[p] = make_float2(0.0f, 0.0f);  // the test point's observation is unknown
+        continue;
+      }
       int64_t id = p < mb ? (int64_t)a.nbr[blk * a.m + p] : (int64_t)a.pts[base + (p - mb)];
       const double yy = a.y[id];
       const float yh = (float)yy;
@@ -266,13 +292,22 @@ loglik_mixed_kernel(MixedArgs P) {
     }
     for (int e = threadIdx.x; e < N * d; e += blockDim.x) {
       const int p = e / d, t = e - p * d;
-      int64_t id = p < mb ? (int64_t)a.nbr[blk * a.m + p] : (int64_t)a.pts[base + (p - mb)];
       df x;
-      if (P.Xs) {
-        const float2 xs = P.Xs[id * d + t];
-        x = {xs.x, xs.y};
+      if (PRED && p == mb) {
+        if (a.dtype == SBV_F64) {
+          const double xv = ((const double*)P.Xt)[(int64_t)item * d + t];
+          x = df_from_double(xv);
+        } else {
+          x = {((const float*)P.Xt)[(int64_t)item * d + t], 0.0f};
+        }
       } else {
-        x = {((const float*)a.X)[id * d + t], 0.0f};
+        int64_t id = p < mb ? (int64_t)a.nbr[blk * a.m + p] : (int64_t)a.pts[base + (p - mb)];
+        if (P.Xs) {
+          const float2 xs = P.Xs[id * d + t];
+          x = {xs.x, xs.y};
+        } else {
+          x = {((const float*)a.X)[id * d + t], 0.0f};
+        }
       }
       const df u = df_mul(x, df{th.ib_h[t], th.ib_l[t]});
       vh[t * N + p] = u.h;  // uncentred for now
@@ -550,14 +585,37 @@ loglik_mixed_kernel(MixedArgs P) {
     if (s_fail) {
       if (threadIdx.x == 0) {
         const int code = s_fail == 2 ? SBV_ETIMEOUT : SBV_ENOTSPD;
-        a.terms[item] = __longlong_as_double(0x7ff8000000000000ll);
-        if (a.status) a.status[item] = code;
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        if (PRED) {
+          P.mean[item] = nan;
+          P.var[item] = nan;
+          P.var_latent[item] = nan;
+        } else {
+          a.terms[item] = nan;
+          if (a.status) a.status[item] = code;
+        }
         record_failure(a.dstat, code, (int)blk, th_i);
       }
       __syncthreads();
       if (s_timeout) break;  // leave the item loop; TMEM is released below
       continue;
     }
+    // ---- right-hand sides, read before the diagonal tiles are overwritten:
+    // x0 = w0 (row N of A, w0 = L^{-1} y) and x0J = w0_J, to become L^-T w0 and
+    // L_JJ^-T w0_J.  Prediction: x0 = w0_J (-> Sigma_JJ^-1 y_J) and x0J = l_*,
+    // the test point's row of L, which lies in the last diagonal tile
+    // (-> Sigma_JJ^-1 Sigma_J*); both vanish beyond J.
+    for (int p = threadIdx.x; p < N; p += blockDim.x) {
+      const float w = A[tri(N, p)];
+      if (PRED) {
+        x0[p] = p < mb ? w : 0.0f;
+        x0J[p] = p < mb ? A[tri(mb, p)] : 0.0f;
+      } else {
+        x0[p] = w;
+        x0J[p] = p < mb ? w : 0.0f;
+      }
+    }
+    __syncthreads();
     // ---- 4. diagonal tiles -> their inverses (one warp per tile, lane = row)
     for (int k0 = warp * NB; k0 < N; k0 += MX_WARPS * NB) {
       const int nbk = min(NB, N - k0);
@@ -589,15 +647,17 @@ loglik_mixed_kernel(MixedArgs P) {
       }
     }
     __syncthreads();
-    // ---- x0 = L^-T w0, x0J = L_JJ^-T w0_J  (w0 = row N of A)
-    for (int p = threadIdx.x; p < N; p += blockDim.x) {
-      const float w = A[tri(N, p)];
-      x0[p] = w;
-      x0J[p] = p < mb ? w : 0.0f;
-    }
     __syncthreads();
     bwd_solve2(A, N, x0, x0J);
-    // ---- 5. residuals in double-float; all warps: (32-row group, column chunk) tasks
+    for (int p = threadIdx.x; p < N; p += blockDim.x) {
+      c1[p] = 0.0f;
+      c2[p] = 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int it = 0; it < NREF; ++it) {
+    // ---- 5. residuals in double-float for x = x0 + c1 and x0J + c2; all
+    // warps: (32-row group, column chunk) tasks
     {
       const int G = (N + 31) / 32;
       const int CH = max(1, MX_WARPS / G);
@@ -616,6 +676,7 @@ loglik_mixed_kernel(MixedArgs P) {
             const float p = __fmul_rn(s.x, xj);
             float pe = __fmaf_rn(s.x, xj, -p);
             pe = __fmaf_rn(s.y, xj, pe);
+            pe = __fmaf_rn(s.x, c1[j], pe);
             const df q = two_sum(h1, p);
             h1 = q.h;
             l1 = __fadd_rn(l1, __fadd_rn(q.l, pe));
@@ -624,6 +685,7 @@ loglik_mixed_kernel(MixedArgs P) {
               const float p2 = __fmul_rn(s.x, zj);
               float pe2 = __fmaf_rn(s.x, zj, -p2);
               pe2 = __fmaf_rn(s.y, zj, pe2);
+              pe2 = __fmaf_rn(s.x, c2[j], pe2);
               const df q2 = two_sum(h2, p2);
               h2 = q2.h;
               l2 = __fadd_rn(l2, __fadd_rn(q2.l, pe2));
@@ -641,22 +703,59 @@ loglik_mixed_kernel(MixedArgs P) {
           s2 = df_add(s2, fast_two_sum(q.z, q.w));
         }
         const df y = {yv[i].x, yv[i].y};
-        r1[i] = df_sub_acc(y, s1).h;
-        r2[i] = i < mb ? df_sub_acc(y, s2).h : 0.0f;
+        if (PRED) {
+          // both systems are J-only: r1 = y_J - Sigma_JJ x0, r2 = Sigma_J* - Sigma_JJ x0J
+          const float2 kst = S[(size_t)mb * N + i];
+          r1[i] = i < mb ? df_sub_acc(y, s1).h : 0.0f;
+          r2[i] = i < mb ? df_sub_acc(df{kst.x, kst.y}, s2).h : 0.0f;
+        } else {
+          r1[i] = df_sub_acc(y, s1).h;
+          r2[i] = i < mb ? df_sub_acc(y, s2).h : 0.0f;
+        }
       }
       __syncthreads();
     }
     // corrections: (L L^T)^{-1} r and (L_JJ L_JJ^T)^{-1} r_J
     fwd_solve2(A, N, r1, r2);
-    for (int p = mb + threadIdx.x; p < N; p += blockDim.x) r2[p] = 0.0f;
+    for (int p = mb + threadIdx.x; p < N; p += blockDim.x) {
+      r2[p] = 0.0f;
+      if (PRED) r1[p] = 0.0f;
+    }
     __syncthreads();
     bwd_solve2(A, N, r1, r2);
+    for (int p = threadIdx.x; p < N; p += blockDim.x) {
+      c1[p] += r1[p];
+      c2[p] += r2[p];
+    }
+    __syncthreads();
+    }  // refinement steps
+    if (PRED) {
+      // mean = Sigma_*J x, var = sigma^2 + tau^2 - Sigma_*J z, sums in FP64
+      double vm = 0.0, vq = 0.0;
+      for (int p = threadIdx.x; p < mb; p += blockDim.x) {
+        const float2 k = S[(size_t)p * N + mb];
+        const double kp = (double)k.x + (double)k.y;
+        vm += kp * ((double)x0[p] + (double)c1[p]);
+        vq += kp * ((double)x0J[p] + (double)c2[p]);
+      }
+      const double sm = cta_sum_mx(vm, red);
+      const double sq = cta_sum_mx(vq, red);
+      if (threadIdx.x == 0) {
+        const double var = th.sigma2 + th.tau2 - sq;
+        P.mean[item] = sm;
+        P.var[item] = var;
+        P.var_latent[item] = var - th.tau2;
+        if (!isfinite(sm) || !isfinite(var)) record_failure(a.dstat, SBV_ENOTSPD, (int)blk, 0);
+      }
+      __syncthreads();
+      continue;
+    }
     // ---- 6. log-determinant and quadratic forms, summed in FP64
     double v = 0.0;
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
       const double yp = (double)yv[p].x + (double)yv[p].y;
-      v += yp * ((double)x0[p] + (double)r1[p]);
-      if (p < mb) v -= yp * ((double)x0J[p] + (double)r2[p]);
+      v += yp * ((double)x0[p] + (double)c1[p]);
+      if (p < mb) v -= yp * ((double)x0J[p] + (double)c2[p]);
       if (p >= mb) {
         int ex;
         const float mant = frexpf(ldiag[p], &ex);  // L = mant 2^ex, mant in [0.5, 1)
@@ -703,13 +802,23 @@ static int upload_df_consts(sbv_ctx* ctx) {
   return SBV_OK;
 }
 
-int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a0, int nmax, int precision,
-                        cudaStream_t s) {
+template <bool TC, bool PRED>
+static int launch_variant(sbv_ctx* ctx, const MixedArgs& P, int grid, cudaStream_t s) {
+  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<TC, PRED>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)P.lay.bytes));
+  loglik_mixed_kernel<TC, PRED><<<grid, MX_THREADS, P.lay.bytes, s>>>(P);
+  SBV_LAUNCH_CHECK(ctx, "loglik_mixed_kernel");
+  return SBV_OK;
+}
+
+// Shared launcher of the likelihood (pred = false) and prediction (pred = true) modes.
+static int launch_mixed(sbv_ctx* ctx, MixedArgs& P, int nmax, int precision, bool pred,
+                        int64_t items, cudaStream_t s) {
   int st = 0;
   if ((st = upload_df_consts(ctx))) return st;
   const bool tc = precision == SBV_PREC_MIXED_BF16;
-  MixedArgs P;
-  P.a = a0;
+  const LoglikArgs& a0 = P.a;
   const int ncap = std::max(nmax, 1);
   P.lay = mixed_layout(ncap, a0.d, tc);
   const size_t static_smem = 2 * 256 * 4 + 1024;
@@ -733,24 +842,37 @@ int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a0, int nmax, int precis
   const size_t per_cta = P.lay.bytes + static_smem + 1024;
   int per_sm = (int)std::max<size_t>(1, (228 * 1024) / per_cta);
   int grid = ctx->num_sms * std::min(per_sm, 2);
-  int64_t items = a0.bc * (int64_t)a0.B;
   if (grid > items) grid = (int)items;
   P.scratch_stride = align_up((size_t)ncap * ncap, 64);
   P.scratch = (float2*)ws_get(ctx, WS_MATRIX, P.scratch_stride * grid * sizeof(float2), &st);
   if (!P.scratch) return st;
-  if (tc) {
-    SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)P.lay.bytes));
-    loglik_mixed_kernel<true><<<grid, MX_THREADS, P.lay.bytes, s>>>(P);
-  } else {
-    SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)P.lay.bytes));
-    loglik_mixed_kernel<false><<<grid, MX_THREADS, P.lay.bytes, s>>>(P);
-  }
-  SBV_LAUNCH_CHECK(ctx, "loglik_mixed_kernel");
-  return SBV_OK;
+  if (pred) return tc ? launch_variant<true, true>(ctx, P, grid, s)
+                      : launch_variant<false, true>(ctx, P, grid, s);
+  return tc ? launch_variant<true, false>(ctx, P, grid, s)
+            : launch_variant<false, false>(ctx, P, grid, s);
+}
+
+int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a0, int nmax, int precision,
+                        cudaStream_t s) {
+  MixedArgs P;
+  memset(&P, 0, sizeof(P));
+  P.a = a0;
+  return launch_mixed(ctx, P, nmax, precision, false, a0.bc * (int64_t)a0.B, s);
+}
+
+// Prediction: a0 carries X, y, d, nbr (ntest x m), m, theta, nu2, dstat, counter.
+int launch_predict_mixed(sbv_ctx* ctx, const LoglikArgs& a0, const void* Xt, int64_t nt,
+                         double* mean, double* var, double* var_latent, int precision,
+                         cudaStream_t s) {
+  MixedArgs P;
+  memset(&P, 0, sizeof(P));
+  P.a = a0;
+  P.Xt = Xt;
+  P.nt = nt;
+  P.mean = mean;
+  P.var = var;
+  P.var_latent = var_latent;
+  return launch_mixed(ctx, P, a0.m + 1, precision, true, nt, s);
 }
 
 }  // namespace sbv

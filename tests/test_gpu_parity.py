@@ -280,7 +280,7 @@ def test_invalid_arguments_are_rejected(ctx, gp5d, gp5d_oracle):
 
 
 # ------------------------------------------------------------------ prediction
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-6)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-6), ("mixed_bf16", 3e-6)])
 def test_predict_matches_oracle(ctx, gp5d, precision, tol):
     th = gp5d["theta"][0]
     mean, var, var_lat, nbr = ctx.sbv_predict(cuda(gp5d["X"]), cuda(gp5d["y"]), cuda(gp5d["Xtest"]),
