@@ -214,6 +214,47 @@ int sbv_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y,
                 int32_t nu2, int32_t precision, double* mean, double* var,
                 double* var_latent, int32_t* nbr, void* stream);
 
+/*
+ * Captured evaluation (Sec. 5.4: all blocks of an evaluation in one batched
+ * launch).  sbv_loglik_graph_create records one evaluation of sbv_loglik --
+ * work-counter reset, the persistent block kernel over every (theta, block)
+ * item, the deterministic sum -- as a CUDA graph for fixed inputs, structure,
+ * B, nu2 and precision; the graph owns its scratch (and splits X once, in the
+ * mixed modes) and reads the B parameter rows from a device buffer of its own.
+ * sbv_loglik_graph_launch stages new rows (host, B x (2+d)) through pinned
+ * memory and replays the graph on `stream`; results land in the `ll` (and
+ * block_terms/status, if given) buffers passed at creation, which must stay
+ * valid, as must every input, until the graph is destroyed.  Launches are
+ * ordered on the stream; do not run two launches of one graph concurrently.
+ * Errors: as sbv_loglik; SBV_ENOMEM for the graph's own buffers.
+ */
+typedef struct sbv_graph sbv_graph;
+
+int sbv_loglik_graph_create(sbv_ctx* ctx, const void* X, int dtype, const double* y,
+                            int64_t n, int32_t d, const int64_t* ptr, const int32_t* pts,
+                            const int32_t* nbr, const int32_t* cnt, int64_t bc, int32_t m,
+                            int32_t nmax, int32_t B, int32_t nu2, int32_t precision,
+                            double* ll, double* block_terms, int32_t* status,
+                            sbv_graph** graph);
+int sbv_loglik_graph_launch(sbv_graph* graph, const double* theta, void* stream);
+void sbv_loglik_graph_destroy(sbv_graph* graph);
+
+/*
+ * sbv_autotune -- time the launch shapes of the block kernel for one
+ * structure (FP64: 1-4 resident CTAs of 256 threads per SM; mixed modes:
+ * 256 threads with 2 or 1 CTAs per SM, or 512 threads with 1) on the given
+ * arguments (one warm-up and two timed evaluations each, synchronising
+ * `stream`) and record the fastest on the context; later sbv_loglik calls and
+ * graphs with the same (precision, largest block size, d) use it.
+ * *threads and *ctas_per_sm (host, may be NULL) receive the choice.
+ * Errors: as sbv_loglik.
+ */
+int sbv_autotune(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n,
+                 int32_t d, const int64_t* ptr, const int32_t* pts, const int32_t* nbr,
+                 const int32_t* cnt, int64_t bc, int32_t m, int32_t nmax,
+                 const double* theta, int32_t B, int32_t nu2, int32_t precision,
+                 int32_t* threads, int32_t* ctas_per_sm, void* stream);
+
 /* Limits of the fixed scratch array of sbv_loglik_fp64_noalloc (about 8.1 MB
  * per GPU that loads the library, held until the process exits). */
 #define SBV_NOALLOC_MAX_THETA 64          /* parameter rows per call */

@@ -9,7 +9,8 @@ ABI of include/sbv.h); this package only builds it and marshals arguments.
     nbr, cnt = ctx.sbv_knn(X, beta_scale, b["ptr"], b["pts"], b["rank"], b["centres"], m)
     ll = ctx.sbv_loglik(X, y, b["ptr"], b["pts"], nbr, cnt, theta, nu2=5, precision="mixed")
 """
-from ._lib import (SBV_F32, SBV_F64, SBV_PREC_FP64, SBV_PREC_MIXED, Context, SBVError,  # noqa: F401
-                   load)
+from ._lib import (SBV_F32, SBV_F64, SBV_PREC_FP64, SBV_PREC_MIXED, Context, LoglikGraph,  # noqa: F401
+                   SBVError, load)
 
-__all__ = ["Context", "SBVError", "load", "SBV_F32", "SBV_F64", "SBV_PREC_FP64", "SBV_PREC_MIXED"]
+__all__ = ["Context", "LoglikGraph", "SBVError", "load", "SBV_F32", "SBV_F64", "SBV_PREC_FP64",
+           "SBV_PREC_MIXED"]

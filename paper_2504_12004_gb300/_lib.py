@@ -42,6 +42,13 @@ SIGNATURES = {
                               _I32, _I32, _P, _P, _P, _P, _P]),
     "sbv_loglik_fp64_noalloc": (C.c_int, [_P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64,
                                           _I32, _I32, _P, _I32, _I32, _P, _P, _P, _P]),
+    "sbv_loglik_graph_create": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64,
+                                          _I32, _I32, _I32, _I32, _I32, _P, _P, _P,
+                                          C.POINTER(_P)]),
+    "sbv_loglik_graph_launch": (C.c_int, [_P, _P, _P]),
+    "sbv_loglik_graph_destroy": (None, [_P]),
+    "sbv_autotune": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64, _I32, _I32,
+                               _P, _I32, _I32, _I32, C.POINTER(_I32), C.POINTER(_I32), _P]),
 }
 
 
@@ -194,6 +201,28 @@ class Context:
         self._check(rc)
         return ll
 
+    def sbv_autotune(self, X, y, ptr, pts, nbr, cnt, theta, nu2: int = 5, precision="mixed",
+                     nmax: int = 0, stream=None):
+        """Time the block kernel's launch shapes on this structure; returns (threads, ctas_per_sm)."""
+        X = _dev(X, None, "X")
+        n, d = X.shape
+        th = _host_f64(theta, "theta").reshape(-1, 2 + d)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        t, c = C.c_int32(0), C.c_int32(0)
+        rc = self.lib.sbv_autotune(self.h, _ptr(X), _xdtype(X), _ptr(_dev(y, torch.float64, "y")), n, d,
+                                   _ptr(_dev(ptr, torch.int64, "ptr")), _ptr(_dev(pts, torch.int32, "pts")),
+                                   _ptr(_dev(nbr, torch.int32, "nbr")), _ptr(_dev(cnt, torch.int32, "cnt")),
+                                   cnt.numel(), nbr.shape[1], int(nmax), _ptr(th), th.shape[0], nu2, prec,
+                                   C.byref(t), C.byref(c), _stream(stream))
+        self._check(rc)
+        return t.value, c.value
+
+    def sbv_loglik_graph_create(self, X, y, ptr, pts, nbr, cnt, B: int, nu2: int = 5,
+                                precision="mixed", nmax: int = 0, block_terms=None, status=None):
+        """Capture one evaluation as a CUDA graph; returns a LoglikGraph."""
+        return LoglikGraph(self, X, y, ptr, pts, nbr, cnt, B, nu2, precision, nmax, block_terms,
+                           status)
+
     @staticmethod
     def max_block_size(ptr, cnt) -> int:
         """Largest m_i + bs_i, the nmax argument that spares sbv_loglik its device read."""
@@ -221,3 +250,46 @@ class Context:
                                   _ptr(mean), _ptr(var), _ptr(var_lat), _ptr(nbr), _stream(stream))
         self._check(rc)
         return mean, var, var_lat, nbr
+
+
+class LoglikGraph:
+    """One captured evaluation (sbv_loglik_graph_*): launch(theta) replays it.
+
+    Holds references to every tensor the graph reads or writes, so they stay
+    alive as long as the graph does."""
+
+    def __init__(self, ctx: Context, X, y, ptr, pts, nbr, cnt, B, nu2, precision, nmax,
+                 block_terms, status):
+        self.ctx = ctx
+        X = _dev(X, None, "X")
+        n, d = X.shape
+        self.d, self.B = d, B
+        self.ll = torch.empty(B, dtype=torch.float64, device=X.device)
+        self._keep = (X, y, ptr, pts, nbr, cnt, block_terms, status)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        h = C.c_void_p()
+        rc = ctx.lib.sbv_loglik_graph_create(
+            ctx.h, _ptr(X), _xdtype(X), _ptr(_dev(y, torch.float64, "y")), n, d,
+            _ptr(_dev(ptr, torch.int64, "ptr")), _ptr(_dev(pts, torch.int32, "pts")),
+            _ptr(_dev(nbr, torch.int32, "nbr")), _ptr(_dev(cnt, torch.int32, "cnt")), cnt.numel(),
+            nbr.shape[1], int(nmax), B, nu2, prec, _ptr(self.ll), _ptr(block_terms), _ptr(status),
+            C.byref(h))
+        ctx._check(rc)
+        self.h = h
+
+    def launch(self, theta, stream=None):
+        """Replay with new parameter rows (host, B x (2+d)); returns the device tensor ll."""
+        th = _host_f64(theta, "theta").reshape(self.B, 2 + self.d)
+        self.ctx._check(self.ctx.lib.sbv_loglik_graph_launch(self.h, _ptr(th), _stream(stream)))
+        return self.ll
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.sbv_loglik_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

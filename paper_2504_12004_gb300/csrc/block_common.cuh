@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "sbv.h"
 #include "sbv_internal.cuh"
 
@@ -69,6 +71,21 @@ template <typename T>
 __device__ __forceinline__ double ld_x(const void* X, int64_t i) {
   return (double)((const T*)X)[i];
 }
+
+// FP64 block-kernel launch plan (loglik.cu).
+struct Fp64Plan {
+  size_t smem;         // dynamic shared memory per CTA
+  size_t gmat_stride;  // doubles per CTA of global matrix scratch, 0 when in shared memory
+  int grid;
+};
+int fp64_plan(sbv_ctx* ctx, int nmax, int d, int64_t items, Fp64Plan* o);
+int fp64_enqueue(sbv_ctx* ctx, const LoglikArgs& a, const Fp64Plan& o, cudaStream_t s);
+int fp64_prepare(sbv_ctx* ctx);
+int run_max_n(sbv_ctx* ctx, const int64_t* ptr, const int32_t* cnt, int64_t bc, int* out,
+              cudaStream_t s);
+int reduce_enqueue(sbv_ctx* ctx, const double* terms, int64_t bc, int B, double* ll,
+                   cudaStream_t s);
+std::vector<ThetaDev> derive_theta_rows(const double* h, int B, int d);
 
 // Packed lower-triangular index of (i, j), j <= i.
 __device__ __forceinline__ int tri(int i, int j) { return (i * (i + 1) >> 1) + j; }

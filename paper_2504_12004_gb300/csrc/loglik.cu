@@ -286,6 +286,76 @@ int launch_predict_mixed(sbv_ctx* ctx, const LoglikArgs& a0, const void* Xt, int
                          double* mean, double* var, double* var_latent, int precision,
                          cudaStream_t s);
 
+int run_max_n(sbv_ctx* ctx, const int64_t* ptr, const int32_t* cnt, int64_t bc, int* out,
+              cudaStream_t s) {
+  return structure_max_n(ctx, ptr, cnt, bc, out, s);
+}
+
+std::vector<ThetaDev> derive_theta_rows(const double* h, int B, int d) {
+  return derive_theta(h, B, d);
+}
+
+// FP64 kernel launch plan: shared-memory matrices when they fit (global
+// scratch slices otherwise) and resident CTAs per SM from the autotuning
+// record or the shared-memory limit (<= 4).
+int fp64_plan(sbv_ctx* ctx, int nmax, int d, int64_t items, Fp64Plan* o) {
+  const size_t ub = (size_t)(d + 1) * (nmax + 1) * sizeof(double);
+  const size_t mat = (size_t)(nmax + 1) * (nmax + 2) / 2 * sizeof(double);
+  o->gmat_stride = 0;
+  int fit, per_sm;
+  if (ub + mat + 1024 <= ctx->smem_optin) {
+    o->smem = ub + mat;
+    fit = (int)std::max<size_t>(1, (228 * 1024) / (o->smem + 2048));
+    per_sm = std::min(fit, 4);
+  } else {
+    o->smem = ub;
+    if (ub + 1024 > ctx->smem_optin)
+      return fail(ctx, SBV_EUNSUPPORTED, "d=%d with N=%d exceeds shared memory", d, nmax);
+    fit = 4;
+    per_sm = 2;
+    o->gmat_stride = (mat / sizeof(double) + 31) & ~(size_t)31;
+  }
+  if (ctx->force.threads) {
+    per_sm = ctx->force.per_sm;
+  } else {
+    for (const auto& t : ctx->tuned)
+      if (t.precision == SBV_PREC_FP64 && t.pred == 0 && t.ncap == nmax && t.d == d) per_sm = t.per_sm;
+  }
+  per_sm = std::max(1, std::min(per_sm, fit));
+  int64_t grid = (int64_t)ctx->num_sms * per_sm;
+  if (grid > items) grid = std::max<int64_t>(items, 1);
+  o->grid = (int)grid;
+  return SBV_OK;
+}
+
+static bool g_fp64_ready[64];
+
+// Once per device: allow the FP64 kernel the largest dynamic shared memory,
+// so that later launches (and captured ones) make no other API call.
+int fp64_prepare(sbv_ctx* ctx) {
+  if (ctx->device < 64 && g_fp64_ready[ctx->device]) return SBV_OK;
+  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_fp64_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ctx->smem_optin - 1024));
+  if (ctx->device < 64) g_fp64_ready[ctx->device] = true;
+  return SBV_OK;
+}
+
+int fp64_enqueue(sbv_ctx* ctx, const LoglikArgs& a, const Fp64Plan& o, cudaStream_t s) {
+  int st = fp64_prepare(ctx);
+  if (st) return st;
+  loglik_fp64_kernel<<<o.grid, LL_THREADS, o.smem, s>>>(a);
+  SBV_LAUNCH_CHECK(ctx, "loglik_fp64_kernel");
+  return SBV_OK;
+}
+
+int reduce_enqueue(sbv_ctx* ctx, const double* terms, int64_t bc, int B, double* ll,
+                   cudaStream_t s) {
+  reduce_terms_kernel<<<B, 1024, 0, s>>>(terms, bc, ll);
+  SBV_LAUNCH_CHECK(ctx, "reduce_terms_kernel");
+  return SBV_OK;
+}
+
 int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n, int d,
                const int64_t* ptr, const int32_t* pts, const int32_t* nbr, const int32_t* cnt,
                int64_t bc, int m, int nmax_hint, const double* h_theta, int B, int nu2,
@@ -334,30 +404,15 @@ int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t 
   if (precision == SBV_PREC_MIXED || precision == SBV_PREC_MIXED_BF16) {
     if ((st = launch_loglik_mixed(ctx, a, nmax, precision, s))) return st;
   } else {
-    const size_t ub = (size_t)(d + 1) * (nmax + 1) * sizeof(double);
-    const size_t mat = (size_t)(nmax + 1) * (nmax + 2) / 2 * sizeof(double);
-    size_t smem = ub + mat;
-    int grid = 0;
-    if (smem + 1024 <= ctx->smem_optin) {
-      int per_sm = (int)std::max<size_t>(1, (228 * 1024) / (smem + 2048));
-      grid = ctx->num_sms * std::min(per_sm, 4);
-    } else {
-      smem = ub;
-      if (smem + 1024 > ctx->smem_optin)
-        return fail(ctx, SBV_EUNSUPPORTED, "d=%d with N=%d exceeds shared memory", d, nmax);
-      grid = ctx->num_sms * 2;
-      size_t stride = (mat / sizeof(double) + 31) & ~(size_t)31;
-      double* g = (double*)ws_get(ctx, WS_MATRIX, stride * grid * sizeof(double), &st);
+    Fp64Plan o;
+    if ((st = fp64_plan(ctx, nmax, d, bc * (int64_t)B, &o))) return st;
+    if (o.gmat_stride) {
+      double* g = (double*)ws_get(ctx, WS_MATRIX, o.gmat_stride * o.grid * sizeof(double), &st);
       if (!g) return st;
       a.gmat = g;
-      a.gmat_stride = stride;
+      a.gmat_stride = o.gmat_stride;
     }
-    int64_t items = bc * (int64_t)B;
-    if (grid > items) grid = (int)items;
-    SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_fp64_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    loglik_fp64_kernel<<<grid, LL_THREADS, smem, s>>>(a);
-    SBV_LAUNCH_CHECK(ctx, "loglik_fp64_kernel");
+    if ((st = fp64_enqueue(ctx, a, o, s))) return st;
   }
   reduce_terms_kernel<<<B, 1024, 0, s>>>(terms, bc, ll);
   SBV_LAUNCH_CHECK(ctx, "reduce_terms_kernel");

@@ -37,54 +37,13 @@
 
 #include "block_common.cuh"
 #include "dfloat.cuh"
+#include "mixed.cuh"
 #include "sbv_internal.cuh"
 #include "umma.cuh"
 
 namespace sbv {
 
 static __constant__ DfConsts c_df;
-
-constexpr int MX_THREADS = 256;
-constexpr int MX_WARPS = MX_THREADS / 32;
-constexpr int NB = 16;  // panel width = diagonal tile size
-
-struct MixedLayout {
-  int ncap;             // largest N held (rows 0..ncap-1 plus the bordered row)
-  int d;
-  int pstride;          // row stride of the FP32 column-major panel (CUDA-core update)
-  uint32_t opnd_piece;  // bytes of one BF16 operand piece (tensor-core update)
-  size_t off_y, off_v, off_u, off_vl, off_A, bytes;
-};
-
-__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-// One shared-memory region (off_u) serves three phases in turn: the scaled
-// coordinates (covariance), the panel operand (factorisation) and the
-// residual partial sums (refinement).
-__host__ __device__ inline MixedLayout mixed_layout(int ncap, int d, bool tc) {
-  MixedLayout L;
-  L.ncap = ncap;
-  L.d = d;
-  L.pstride = (int)align_up((size_t)ncap + 1, 4);
-  L.opnd_piece = (uint32_t)(((ncap + 1 + 127) / 128) * 128 * 32);
-  size_t o = 0;
-  L.off_y = o;  o += align_up((size_t)(ncap + 1) * sizeof(float2), 16);
-  // x0 x0J r1 r2 ldiag idiag c1 c2 (c: corrections accumulated over refinement steps)
-  L.off_v = o;  o += align_up((size_t)8 * (ncap + 1) * sizeof(float), 16);
-  o = align_up(o, 128);
-  const size_t coord = align_up((size_t)d * ncap * sizeof(float), 16);
-  size_t uni = 2 * coord;
-  const size_t panel = tc ? 3 * (size_t)L.opnd_piece : (size_t)NB * L.pstride * sizeof(float);
-  const size_t part = (size_t)(32 * MX_WARPS > ncap ? 32 * MX_WARPS : ncap) * sizeof(float4);
-  if (panel > uni) uni = panel;
-  if (part > uni) uni = part;
-  L.off_u = o;
-  L.off_vl = o + coord;
-  o += align_up(uni, 16);
-  L.off_A = o;  o += align_up((size_t)(ncap + 1) * (ncap + 2) / 2 * sizeof(float), 16);
-  L.bytes = o;
-  return L;
-}
 
 // ---------------------------------------------------------------------------
 // Triangular solves with the factor packed in A, whose diagonal tiles hold
@@ -158,7 +117,7 @@ __device__ double cta_sum_mx(double v, double* red) {
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
   double s = 0.0;
-  for (int q = 0; q < MX_WARPS; ++q) s += red[q];
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
   __syncthreads();
   return s;
 }
@@ -174,23 +133,10 @@ __global__ void split_points_kernel(const double* __restrict__ X, int64_t total,
   }
 }
 
-struct MixedArgs {
-  LoglikArgs a;
-  const float2* Xs;      // split FP64 points, or NULL for FP32 points (a.X read directly)
-  float2* scratch;
-  size_t scratch_stride;
-  MixedLayout lay;
-  // prediction mode: one item per test point, J = its m nearest training points
-  const void* Xt;        // test points (dtype of a.X)
-  int64_t nt;
-  double* mean;
-  double* var;
-  double* var_latent;
-};
-
-template <bool TC, bool PRED>
-__global__ void __launch_bounds__(MX_THREADS, 2)
+template <int THREADS, bool TC, bool PRED>
+__global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
 loglik_mixed_kernel(MixedArgs P) {
+  constexpr int MX_WARPS = THREADS / 32;
   extern __shared__ __align__(128) unsigned char smem[];
   const LoglikArgs& a = P.a;
   const MixedLayout& lay = P.lay;
@@ -552,9 +498,10 @@ loglik_mixed_kernel(MixedArgs P) {
             if (!done && threadIdx.x == 0) s_timeout = 1;
             umma::fence_after_sync();
             if (done) {
-              const int q = warp & 3, half = warp >> 2;
+              // warp w reads TMEM lanes 32 (w % 4) ..; the w / 4 groups split the columns
+              const int q = warp & 3, grp = warp >> 2;
               const int ii = k1 + r0 + 32 * q + lane;  // matrix row of this lane
-              for (int cc = half * 16; cc < nc; cc += 32) {
+              for (int cc = grp * 16; cc < nc; cc += 16 * (MX_WARPS / 4)) {
                 float dv[16], ds[16];
                 const uint32_t ta = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)cc;
                 umma::tmem_ld16(ta, dv);
@@ -802,54 +749,126 @@ static int upload_df_consts(sbv_ctx* ctx) {
   return SBV_OK;
 }
 
-template <bool TC, bool PRED>
+// ---------------------------------------------------------------------------
+// Launch planning: layout, threads per CTA, grid, scratch size.  The shape
+// (threads, CTAs per SM) comes from the context's autotuning record when one
+// matches (precision, prediction mode, capacity, d), else 256 threads and as
+// many CTAs per SM (<= 2) as shared memory allows.
+// ---------------------------------------------------------------------------
+int mixed_plan(sbv_ctx* ctx, int nmax, int d, int precision, bool pred, int64_t items,
+               MixedPlan* o) {
+  const bool tc = precision == SBV_PREC_MIXED_BF16;
+  const int ncap = std::max(nmax, 1);
+  o->tc = tc;
+  o->pred = pred;
+  o->lay = mixed_layout(ncap, d, tc);
+  const size_t static_smem = 2 * 256 * 4 + 1024;
+  if (o->lay.bytes + static_smem > ctx->smem_optin)
+    return fail(ctx, SBV_EUNSUPPORTED,
+                "mixed path: a block with N=%d (d=%d) needs %zu bytes of shared memory", nmax, d,
+                o->lay.bytes);
+  // 228 KB of shared memory per SM, 1 KB reserved per resident CTA
+  const size_t per_cta = o->lay.bytes + static_smem + 1024;
+  const int fit = (int)std::max<size_t>(1, (228 * 1024) / per_cta);
+  int threads = 256, per_sm = std::min(fit, 2);
+  if (ctx->force.threads) {
+    threads = ctx->force.threads;
+    per_sm = ctx->force.per_sm;
+  } else {
+    for (const auto& t : ctx->tuned)
+      if (t.precision == precision && t.pred == (int)pred && t.ncap == ncap && t.d == d) {
+        threads = t.threads;
+        per_sm = t.per_sm;
+      }
+  }
+  if (threads == 512) per_sm = 1;               // 117 registers x 512 threads: one CTA per SM
+  per_sm = std::max(1, std::min(per_sm, fit));
+  int grid = ctx->num_sms * per_sm;
+  if (grid > items) grid = (int)std::max<int64_t>(items, 1);
+  o->threads = threads;
+  o->grid = grid;
+  o->scratch_stride = align_up((size_t)ncap * ncap, 64);
+  return SBV_OK;
+}
+
+int mixed_split(sbv_ctx* ctx, const void* X, int dtype, int64_t total, float2* xs,
+                cudaStream_t s) {
+  if (dtype != SBV_F64) return SBV_OK;
+  int g = (int)std::min<int64_t>((total + 255) / 256, (int64_t)ctx->num_sms * 16);
+  split_points_kernel<<<std::max(g, 1), 256, 0, s>>>((const double*)X, total, xs);
+  SBV_LAUNCH_CHECK(ctx, "split_points_kernel");
+  return SBV_OK;
+}
+
+template <int THREADS, bool TC, bool PRED>
 static int launch_variant(sbv_ctx* ctx, const MixedArgs& P, int grid, cudaStream_t s) {
-  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<TC, PRED>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)P.lay.bytes));
-  loglik_mixed_kernel<TC, PRED><<<grid, MX_THREADS, P.lay.bytes, s>>>(P);
+  loglik_mixed_kernel<THREADS, TC, PRED><<<grid, THREADS, P.lay.bytes, s>>>(P);
   SBV_LAUNCH_CHECK(ctx, "loglik_mixed_kernel");
   return SBV_OK;
 }
 
-// Shared launcher of the likelihood (pred = false) and prediction (pred = true) modes.
+template <int THREADS, bool TC, bool PRED>
+static int allow_smem(sbv_ctx* ctx, int bytes) {
+  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<THREADS, TC, PRED>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  return SBV_OK;
+}
+
+static bool g_mixed_ready[64];
+
+// Once per device: upload the double-float constants and allow every variant
+// the largest dynamic shared memory, so that later launches (and launches
+// captured into a CUDA graph) make no other API call.
+int mixed_prepare(sbv_ctx* ctx) {
+  int st = 0;
+  if (ctx->device < 64 && g_mixed_ready[ctx->device]) return SBV_OK;
+  if ((st = upload_df_consts(ctx))) return st;
+  const int b = (int)ctx->smem_optin - (2 * 256 * 4 + 1024);
+  if ((st = allow_smem<256, false, false>(ctx, b)) || (st = allow_smem<256, true, false>(ctx, b)) ||
+      (st = allow_smem<256, false, true>(ctx, b)) || (st = allow_smem<256, true, true>(ctx, b)) ||
+      (st = allow_smem<512, false, false>(ctx, b)) || (st = allow_smem<512, true, false>(ctx, b)) ||
+      (st = allow_smem<512, false, true>(ctx, b)) || (st = allow_smem<512, true, true>(ctx, b)))
+    return st;
+  if (ctx->device < 64) g_mixed_ready[ctx->device] = true;
+  return SBV_OK;
+}
+
+// Enqueue the kernel; P carries the arguments, Xs (or NULL) and the scratch.
+int mixed_enqueue(sbv_ctx* ctx, MixedArgs& P, const MixedPlan& o, cudaStream_t s) {
+  int st = 0;
+  if ((st = mixed_prepare(ctx))) return st;
+  P.lay = o.lay;
+  P.scratch_stride = o.scratch_stride;
+  const bool tc = o.tc, pred = o.pred;
+  if (o.threads == 512) {
+    if (pred) return tc ? launch_variant<512, true, true>(ctx, P, o.grid, s)
+                        : launch_variant<512, false, true>(ctx, P, o.grid, s);
+    return tc ? launch_variant<512, true, false>(ctx, P, o.grid, s)
+              : launch_variant<512, false, false>(ctx, P, o.grid, s);
+  }
+  if (pred) return tc ? launch_variant<256, true, true>(ctx, P, o.grid, s)
+                      : launch_variant<256, false, true>(ctx, P, o.grid, s);
+  return tc ? launch_variant<256, true, false>(ctx, P, o.grid, s)
+            : launch_variant<256, false, false>(ctx, P, o.grid, s);
+}
+
+// Plan, split the points and take the scratch from the context workspace.
 static int launch_mixed(sbv_ctx* ctx, MixedArgs& P, int nmax, int precision, bool pred,
                         int64_t items, cudaStream_t s) {
   int st = 0;
-  if ((st = upload_df_consts(ctx))) return st;
-  const bool tc = precision == SBV_PREC_MIXED_BF16;
-  const LoglikArgs& a0 = P.a;
-  const int ncap = std::max(nmax, 1);
-  P.lay = mixed_layout(ncap, a0.d, tc);
-  const size_t static_smem = 2 * 256 * 4 + 1024;
-  if (P.lay.bytes + static_smem > ctx->smem_optin)
-    return fail(ctx, SBV_EUNSUPPORTED,
-                "mixed path: a block with N=%d (d=%d) needs %zu bytes of shared memory", nmax,
-                a0.d, P.lay.bytes);
-  // split FP64 points once per call
-  const int64_t total = a0.n * a0.d;
-  if (a0.dtype == SBV_F64) {
+  MixedPlan o;
+  if ((st = mixed_plan(ctx, nmax, P.a.d, precision, pred, items, &o))) return st;
+  const int64_t total = P.a.n * P.a.d;
+  P.Xs = nullptr;
+  if (P.a.dtype == SBV_F64) {
     float2* xs = (float2*)ws_get(ctx, WS_XSPLIT, (size_t)total * sizeof(float2), &st);
     if (!xs) return st;
-    int g = (int)std::min<int64_t>((total + 255) / 256, (int64_t)ctx->num_sms * 16);
-    split_points_kernel<<<std::max(g, 1), 256, 0, s>>>((const double*)a0.X, total, xs);
-    SBV_LAUNCH_CHECK(ctx, "split_points_kernel");
+    if ((st = mixed_split(ctx, P.a.X, P.a.dtype, total, xs, s))) return st;
     P.Xs = xs;
-  } else {
-    P.Xs = nullptr;
   }
-  // 228 KB of shared memory per SM, 1 KB reserved per resident CTA
-  const size_t per_cta = P.lay.bytes + static_smem + 1024;
-  int per_sm = (int)std::max<size_t>(1, (228 * 1024) / per_cta);
-  int grid = ctx->num_sms * std::min(per_sm, 2);
-  if (grid > items) grid = (int)items;
-  P.scratch_stride = align_up((size_t)ncap * ncap, 64);
-  P.scratch = (float2*)ws_get(ctx, WS_MATRIX, P.scratch_stride * grid * sizeof(float2), &st);
+  P.scratch = (float2*)ws_get(ctx, WS_MATRIX, o.scratch_stride * o.grid * sizeof(float2), &st);
   if (!P.scratch) return st;
-  if (pred) return tc ? launch_variant<true, true>(ctx, P, grid, s)
-                      : launch_variant<false, true>(ctx, P, grid, s);
-  return tc ? launch_variant<true, false>(ctx, P, grid, s)
-            : launch_variant<false, false>(ctx, P, grid, s);
+  return mixed_enqueue(ctx, P, o, s);
 }
 
 int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a0, int nmax, int precision,

@@ -1,0 +1,83 @@
+// Types and launch helpers of the mixed-precision block kernel, shared by the
+// per-call path (loglik_mixed.cu) and the captured-graph path (graph.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "block_common.cuh"
+#include "sbv_internal.cuh"
+
+namespace sbv {
+
+// threads per CTA: 256 (two CTAs per SM when shared memory allows) or 512
+// (one CTA per SM); the autotuner picks per structure
+constexpr int MX_MAX_WARPS = 16;
+constexpr int NB = 16;  // panel width = diagonal tile size
+
+struct MixedLayout {
+  int ncap;             // largest N held (rows 0..ncap-1 plus the bordered row)
+  int d;
+  int pstride;          // row stride of the FP32 column-major panel (CUDA-core update)
+  uint32_t opnd_piece;  // bytes of one BF16 operand piece (tensor-core update)
+  size_t off_y, off_v, off_u, off_vl, off_A, bytes;
+};
+
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// One shared-memory region (off_u) serves three phases in turn: the scaled
+// coordinates (covariance), the panel operand (factorisation) and the
+// residual partial sums (refinement).
+__host__ __device__ inline MixedLayout mixed_layout(int ncap, int d, bool tc) {
+  MixedLayout L;
+  L.ncap = ncap;
+  L.d = d;
+  L.pstride = (int)align_up((size_t)ncap + 1, 4);
+  L.opnd_piece = (uint32_t)(((ncap + 1 + 127) / 128) * 128 * 32);
+  size_t o = 0;
+  L.off_y = o;  o += align_up((size_t)(ncap + 1) * sizeof(float2), 16);
+  // x0 x0J r1 r2 ldiag idiag c1 c2 (c: corrections accumulated over refinement steps)
+  L.off_v = o;  o += align_up((size_t)8 * (ncap + 1) * sizeof(float), 16);
+  o = align_up(o, 128);
+  const size_t coord = align_up((size_t)d * ncap * sizeof(float), 16);
+  size_t uni = 2 * coord;
+  const size_t panel = tc ? 3 * (size_t)L.opnd_piece : (size_t)NB * L.pstride * sizeof(float);
+  const size_t part = (size_t)(32 * MX_MAX_WARPS > ncap ? 32 * MX_MAX_WARPS : ncap) * sizeof(float4);
+  if (panel > uni) uni = panel;
+  if (part > uni) uni = part;
+  L.off_u = o;
+  L.off_vl = o + coord;
+  o += align_up(uni, 16);
+  L.off_A = o;  o += align_up((size_t)(ncap + 1) * (ncap + 2) / 2 * sizeof(float), 16);
+  L.bytes = o;
+  return L;
+}
+
+struct MixedArgs {
+  LoglikArgs a;
+  const float2* Xs;      // split FP64 points, or NULL for FP32 points (a.X read directly)
+  float2* scratch;
+  size_t scratch_stride;
+  MixedLayout lay;
+  // prediction mode: one item per test point, J = its m nearest training points
+  const void* Xt;        // test points (dtype of a.X)
+  int64_t nt;
+  double* mean;
+  double* var;
+  double* var_latent;
+};
+
+struct MixedPlan {
+  MixedLayout lay;
+  bool tc, pred;
+  int threads, grid;
+  size_t scratch_stride;  // float2 elements per CTA slice
+};
+
+int mixed_plan(sbv_ctx* ctx, int nmax, int d, int precision, bool pred, int64_t items,
+               MixedPlan* o);
+int mixed_split(sbv_ctx* ctx, const void* X, int dtype, int64_t total, float2* xs,
+                cudaStream_t s);
+int mixed_enqueue(sbv_ctx* ctx, MixedArgs& P, const MixedPlan& o, cudaStream_t s);
+int mixed_prepare(sbv_ctx* ctx);
+
+}  // namespace sbv

@@ -25,6 +25,18 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+// Launch shape of the block kernels: threads per CTA and resident CTAs per SM.
+struct LaunchShape {
+  int threads = 0;  // 0: no forced shape
+  int per_sm = 0;
+};
+
+// Autotuning record: the fastest shape measured for one kind of launch.
+struct TunedShape {
+  int precision, pred, ncap, d;
+  int threads, per_sm;
+};
+
 }  // namespace sbv
 
 struct sbv_ctx {
@@ -34,6 +46,8 @@ struct sbv_ctx {
   std::string err;
   sbv::DevStatus* d_status = nullptr;  // device record
   sbv::DevBuf ws[16];                  // named workspace slots
+  sbv::LaunchShape force;              // set while the autotuner times a shape
+  std::vector<sbv::TunedShape> tuned;  // autotuning records
   // pinned host ring for parameter rows: slot k is reused only after the
   // event recorded behind its previous copy has completed
   static const int kRing = 8;
@@ -60,6 +74,7 @@ enum WsSlot {
   WS_CENTRES,
   WS_EXTRA,
   WS_XSPLIT,      // points split into float pairs for the mixed path
+  WS_TUNE,        // results of the autotuner's timing runs
   WS_COUNT
 };
 
