@@ -12,7 +12,10 @@ Modules
             earlier-ordered m-NN (Alg. 4 / Eq. mmsearchingBV), the scaled Matern
             kernel (Eqs. scale, maternkernel), the batched block log-likelihood
             (Alg. 5), the total (Alg. 1 Step 5) and prediction (Sec. 4.2, 5.5).
-  mlp    -- FP64 forward/backward of the surrogate network and Adam.
+  mlp    -- FP64 forward/backward of the surrogate network (GELU, MSE) and Adam,
+            with an emulation of the GPU's BF16 operand rounding.
+  mle    -- maximum-likelihood estimation over log theta (library optimiser),
+            with the scale-family closed form used as a pin.
 
 Parity status: every function is pinned by a test in tests/test_oracle_*.py
 except the blocking trajectory itself (RAC anchors, Lloyd iterations, block
