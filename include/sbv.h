@@ -299,6 +299,63 @@ int sbv_loglik_fp64_noalloc(const void* X, int dtype, const double* y, int64_t n
                             int32_t nu2, double* ll, double* block_terms,
                             int32_t* status, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Likelihood surrogate network.  The paper has no learned component; this
+ * network s(x) regresses (standardised) log-likelihood values on
+ * (standardised) log parameters so that the maximisation of the likelihood
+ * (Alg. 1 Step 5 evaluated once per optimiser iteration, Sec. 5.4) can ask it
+ * for candidates, which the exact likelihood then judges.
+ *
+ * Architecture: in_dim -> 256 -> 256 -> 256 -> 1, GELU(z) = z Phi(z) after
+ * each hidden layer; loss L = (1/K) sum_k (s(x_k) - t_k)^2; Adam (Kingma &
+ * Ba 2015) with bias correction.  The 256 x 256 layers (forward, backward and
+ * weight gradients) run on the tensor cores with BF16 operands and FP32
+ * accumulation; the rest in FP32.
+ *
+ * Parameters are FP32, packed in the order W1 (256 x in_dim), b1 (256),
+ * W2 (256 x 256), b2, W3 (256 x 256), b3, w4 (256), b4 (1); weights are
+ * [out][in] row-major, a layer computes z = h W^T + b.
+ * Inputs X: device FP32, K x in_dim row-major; targets t: device FP32 (K).
+ * Calls are ordered on `stream`; sbv_mlp_grad, sbv_mlp_train and
+ * sbv_mlp_predict wait for it before returning (they check a device-side
+ * timeout flag).  Errors: SBV_EINVAL, SBV_ENOMEM, SBV_ECUDA, SBV_ETIMEOUT
+ * (a bounded tensor-core wait gave up; the results are then invalid).
+ * ---------------------------------------------------------------------- */
+#define SBV_MLP_WIDTH 256
+#define SBV_MLP_MAX_IN 16
+
+typedef struct sbv_mlp sbv_mlp;
+
+/* Number of packed parameters for in_dim inputs (-1 if in_dim is out of range). */
+int64_t sbv_mlp_num_params(int32_t in_dim);
+/* Create a network on ctx's device with parameters drawn from one SplitMix64
+ * stream seeded by `seed`: for each tensor in packed order, element by
+ * element, u = (next() >> 11) * 2^-53 and value (2u - 1) / sqrt(fan_in)
+ * rounded to FP32 (fan_in = in_dim for W1 and b1, 256 otherwise). */
+int sbv_mlp_create(sbv_ctx* ctx, int32_t in_dim, uint64_t seed, sbv_mlp** mlp);
+void sbv_mlp_destroy(sbv_mlp* mlp);
+/* Copy the FP32 parameters from / to host memory (n = sbv_mlp_num_params);
+ * set_params also clears the Adam state. */
+int sbv_mlp_set_params(sbv_mlp* mlp, const float* params, int64_t n);
+int sbv_mlp_get_params(sbv_mlp* mlp, float* params, int64_t n);
+/* Gradient of L over all K rows: grads (device FP32, packed like the
+ * parameters) and loss (device FP32 scalar), each may be NULL. */
+int sbv_mlp_grad(sbv_mlp* mlp, const float* X, const float* t, int64_t K, float* grads,
+                 float* loss, void* stream);
+/* One Adam step on the gradient of the last sbv_mlp_grad call. */
+int sbv_mlp_adam(sbv_mlp* mlp, float lr, float beta1, float beta2, float eps, void* stream);
+/* `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8) on mini-batches of
+ * `batch` rows: consecutive slices of Fisher-Yates permutations of [0, K)
+ * drawn from SplitMix64(seed), a new permutation after each pass (the last
+ * slice of a pass may be shorter).  *loss_out (host, may be NULL) receives the
+ * loss of the last mini-batch. */
+int sbv_mlp_train(sbv_mlp* mlp, const float* X, const float* t, int64_t K, int32_t steps,
+                  int32_t batch, float lr, uint64_t seed, float* loss_out, void* stream);
+/* s(x) for K rows into s (device FP32, K) and, if dsdx is not NULL, the
+ * input gradients ds/dx (device FP32, K x in_dim). */
+int sbv_mlp_predict(sbv_mlp* mlp, const float* X, int64_t K, float* s, float* dsdx,
+                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

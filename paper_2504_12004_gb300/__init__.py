@@ -10,7 +10,7 @@ ABI of include/sbv.h); this package only builds it and marshals arguments.
     ll = ctx.sbv_loglik(X, y, b["ptr"], b["pts"], nbr, cnt, theta, nu2=5, precision="mixed")
 """
 from ._lib import (SBV_F32, SBV_F64, SBV_PREC_FP64, SBV_PREC_MIXED, Context, LoglikGraph,  # noqa: F401
-                   SBVError, load)
+                   Mlp, SBVError, load)
 
-__all__ = ["Context", "LoglikGraph", "SBVError", "load", "SBV_F32", "SBV_F64", "SBV_PREC_FP64",
+__all__ = ["Context", "LoglikGraph", "Mlp", "SBVError", "load", "SBV_F32", "SBV_F64", "SBV_PREC_FP64",
            "SBV_PREC_MIXED"]

@@ -49,6 +49,16 @@ SIGNATURES = {
     "sbv_loglik_graph_destroy": (None, [_P]),
     "sbv_autotune": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64, _I32, _I32,
                                _P, _I32, _I32, _I32, C.POINTER(_I32), C.POINTER(_I32), _P]),
+    "sbv_mlp_num_params": (_I64, [_I32]),
+    "sbv_mlp_create": (C.c_int, [_P, _I32, _U64, C.POINTER(_P)]),
+    "sbv_mlp_destroy": (None, [_P]),
+    "sbv_mlp_set_params": (C.c_int, [_P, _P, _I64]),
+    "sbv_mlp_get_params": (C.c_int, [_P, _P, _I64]),
+    "sbv_mlp_grad": (C.c_int, [_P, _P, _P, _I64, _P, _P, _P]),
+    "sbv_mlp_adam": (C.c_int, [_P, C.c_float, C.c_float, C.c_float, C.c_float, _P]),
+    "sbv_mlp_train": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, C.c_float, _U64, C.POINTER(C.c_float),
+                                _P]),
+    "sbv_mlp_predict": (C.c_int, [_P, _P, _I64, _P, _P, _P]),
 }
 
 
@@ -293,3 +303,72 @@ class LoglikGraph:
             self.close()
         except Exception:
             pass
+
+
+class Mlp:
+    """The likelihood surrogate network (sbv_mlp_*): FP32 masters on the device."""
+
+    def __init__(self, ctx: Context, in_dim: int, seed: int = 0):
+        self.ctx = ctx
+        self.in_dim = in_dim
+        self.n_params = ctx.lib.sbv_mlp_num_params(in_dim)
+        if self.n_params < 0:
+            raise SBVError(SBV_EINVAL, f"in_dim={in_dim} out of range")
+        h = C.c_void_p()
+        ctx._check(ctx.lib.sbv_mlp_create(ctx.h, in_dim, seed, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.sbv_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        self.ctx._check(self.ctx.lib.sbv_mlp_get_params(self.h, _ptr(out), self.n_params))
+        return out
+
+    def set_params(self, params):
+        v = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        self.ctx._check(self.ctx.lib.sbv_mlp_set_params(self.h, _ptr(v), v.size))
+
+    def _rows(self, X):
+        X = _dev(X, torch.float32, "X")
+        if X.dim() != 2 or X.shape[1] != self.in_dim:
+            raise ValueError(f"X must be K x {self.in_dim}")
+        return X
+
+    def grad(self, X, t, stream=None):
+        """Returns (grads, loss) as device tensors."""
+        X = self._rows(X)
+        t = _dev(t, torch.float32, "t")
+        g = torch.empty(self.n_params, dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        self.ctx._check(self.ctx.lib.sbv_mlp_grad(self.h, _ptr(X), _ptr(t), X.shape[0], _ptr(g),
+                                                  _ptr(loss), _stream(stream)))
+        return g, loss
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        self.ctx._check(self.ctx.lib.sbv_mlp_adam(self.h, lr, beta1, beta2, eps, _stream(stream)))
+
+    def train(self, X, t, steps: int, batch: int, lr: float, seed: int = 0, stream=None) -> float:
+        X = self._rows(X)
+        t = _dev(t, torch.float32, "t")
+        loss = C.c_float(0.0)
+        self.ctx._check(self.ctx.lib.sbv_mlp_train(self.h, _ptr(X), _ptr(t), X.shape[0], steps, batch,
+                                                   lr, seed, C.byref(loss), _stream(stream)))
+        return loss.value
+
+    def predict(self, X, want_grad=False, stream=None):
+        X = self._rows(X)
+        s = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        g = torch.empty(X.shape[0], self.in_dim, dtype=torch.float32, device=X.device) if want_grad else None
+        self.ctx._check(self.ctx.lib.sbv_mlp_predict(self.h, _ptr(X), X.shape[0], _ptr(s), _ptr(g),
+                                                     _stream(stream)))
+        return (s, g) if want_grad else s
