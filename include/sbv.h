@@ -356,6 +356,86 @@ int sbv_mlp_train(sbv_mlp* mlp, const float* X, const float* t, int64_t K, int32
 int sbv_mlp_predict(sbv_mlp* mlp, const float* X, int64_t K, float* s, float* dsdx,
                     void* stream);
 
+/* ------------------------------------------------------------------------
+ * Maximum-likelihood estimation.  The paper maximises the SBV log-likelihood
+ * over theta with a library optimiser that re-evaluates Alg. 5 (summed as in
+ * Alg. 1 Step 5) once per iteration while the data stay on the GPU
+ * (Sec. 5.4; Sec. 7 runs 500 iterations); it does not name the algorithm.
+ * sbv_mle runs BFGS on u = log theta inside box bounds: each iteration is one
+ * batched call for a line search over `line_points` step lengths
+ * 1, 1/2, 1/4, ... along the quasi-Newton direction (capped to `max_step` in
+ * the max norm) and one batched call for the central-difference gradient
+ * (2 (2 + d) rows) at the accepted point.  It stops when an accepted step
+ * gains less than ftol |l|, when no step length improves l along a fresh
+ * (reset) direction, or before a call would exceed max_evals rows.
+ * A parameter row whose block matrices are not positive definite counts as
+ * l = -inf.  Rows: theta = (sigma^2, tau^2, beta_1..beta_d), natural scale.
+ * Bounds lower/upper (host, 2 + d, NULL = defaults (1e-6, 1e-10, 1e-4 ...)
+ * and (1e6, 1e3, 1e3 ...)) must satisfy 0 < lower <= upper < inf; starting
+ * entries that are 0 or outside are moved to the nearest bound.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int32_t max_evals;     /* budget of exact parameter rows per start (4000) */
+  double fd_step;        /* central-difference step in log theta (1e-3) */
+  double ftol;           /* relative gain below which an iteration converges (1e-10) */
+  double max_step;       /* largest step in log theta, max norm (1.0) */
+  int32_t line_points;   /* step lengths per line-search call, 1..64 (8) */
+  int32_t precision;     /* SBV_PREC_* (SBV_PREC_MIXED) */
+  int32_t nu2;           /* 2 nu in {1, 3, 5, 7} (5) */
+} sbv_mle_opts;
+
+typedef struct {
+  double ll;             /* log-likelihood at the returned parameters */
+  int32_t evals;         /* exact parameter rows evaluated */
+  int32_t calls;         /* batched likelihood calls */
+  int32_t iterations;    /* accepted steps */
+  int32_t converged;     /* 1 gain < ftol, 2 stationary, 0 budget exhausted */
+} sbv_mle_result;
+
+/* theta0, theta_out: host, 2 + d.  opts may be NULL (defaults above).  If
+ * hist_len is not NULL, up to hist_cap evaluated rows are written to hist_u
+ * (log theta, hist_cap x (2 + d)) and hist_l (their l) and their number to
+ * *hist_len.  Waits for `stream` after every call. */
+int sbv_mle(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n, int32_t d,
+            const int64_t* ptr, const int32_t* pts, const int32_t* nbr, const int32_t* cnt,
+            int64_t bc, int32_t m, int32_t nmax, const double* theta0, const double* lower,
+            const double* upper, const sbv_mle_opts* opts, double* theta_out,
+            sbv_mle_result* result, double* hist_u, double* hist_l, int64_t hist_cap,
+            int64_t* hist_len, void* stream);
+
+/* Surrogate proposals for restarts (no counterpart in the paper). */
+typedef struct {
+  int32_t exact_starts;  /* starts run from their given point before proposals (4) */
+  int32_t train_steps;   /* Adam steps of each fit, from the network's initial parameters (4000) */
+  int32_t batch;         /* rows per Adam step (512) */
+  float lr;              /* Adam step size (1e-3) */
+  int32_t ascent_starts; /* points of the gradient ascent on the network (256) */
+  int32_t ascent_iters;  /* sign-gradient steps of 1/200 of the data's box (300) */
+  int32_t candidates;    /* distinct maximisers judged by the exact likelihood (8) */
+  double ascent_radius;  /* ascent points drawn uniformly within this max-norm radius (1.0) */
+  uint64_t seed;         /* SplitMix64 seed of those draws and of the mini-batches (1) */
+} sbv_surrogate_opts;
+
+/*
+ * sbv_mle_multistart -- sbv_mle from each of S starts (host, S x (2 + d)) in
+ * turn, sharing one history of exact evaluations.  With mlp == NULL every
+ * start runs from its given point.  With a network (in_dim = 2 + d), start
+ * i >= exact_starts first fits the network to the standardised history
+ * (inputs: log theta per coordinate, target: l), climbs it from
+ * `ascent_starts` points around start i, and evaluates the best distinct
+ * `candidates` maximisers together with start i in one exact call; BFGS then
+ * runs from the best of them.  theta_out (S x (2 + d)) and results (S) report
+ * each start; results[i].evals includes the proposal call.  The network keeps
+ * its last fit.  sopts may be NULL (defaults above).
+ */
+int sbv_mle_multistart(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n,
+                       int32_t d, const int64_t* ptr, const int32_t* pts, const int32_t* nbr,
+                       const int32_t* cnt, int64_t bc, int32_t m, int32_t nmax,
+                       const double* starts, int32_t S, const double* lower,
+                       const double* upper, const sbv_mle_opts* opts, sbv_mlp* mlp,
+                       const sbv_surrogate_opts* sopts, double* theta_out,
+                       sbv_mle_result* results, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

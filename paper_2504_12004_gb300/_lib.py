@@ -24,6 +24,41 @@ ERRNAMES = {1: "SBV_EINVAL", 2: "SBV_ENOTSPD", 3: "SBV_ENOMEM", 4: "SBV_ECUDA",
 
 _lib = None
 
+
+class MleOpts(C.Structure):
+    """sbv_mle_opts"""
+    _fields_ = [("max_evals", C.c_int32), ("fd_step", C.c_double), ("ftol", C.c_double),
+                ("max_step", C.c_double), ("line_points", C.c_int32), ("precision", C.c_int32),
+                ("nu2", C.c_int32)]
+
+
+class MleResult(C.Structure):
+    """sbv_mle_result"""
+    _fields_ = [("ll", C.c_double), ("evals", C.c_int32), ("calls", C.c_int32),
+                ("iterations", C.c_int32), ("converged", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SurrogateOpts(C.Structure):
+    """sbv_surrogate_opts"""
+    _fields_ = [("exact_starts", C.c_int32), ("train_steps", C.c_int32), ("batch", C.c_int32),
+                ("lr", C.c_float), ("ascent_starts", C.c_int32), ("ascent_iters", C.c_int32),
+                ("candidates", C.c_int32), ("ascent_radius", C.c_double), ("seed", C.c_uint64)]
+
+
+def mle_opts(max_evals=4000, fd_step=1e-3, ftol=1e-10, max_step=1.0, line_points=8,
+             precision="mixed", nu2=5) -> MleOpts:
+    return MleOpts(max_evals, fd_step, ftol, max_step, line_points,
+                   PRECISIONS[precision] if isinstance(precision, str) else int(precision), nu2)
+
+
+def surrogate_opts(exact_starts=4, train_steps=4000, batch=512, lr=1e-3, ascent_starts=256,
+                   ascent_iters=300, candidates=8, ascent_radius=1.0, seed=1) -> SurrogateOpts:
+    return SurrogateOpts(exact_starts, train_steps, batch, lr, ascent_starts, ascent_iters,
+                         candidates, ascent_radius, seed)
+
 # (name, restype, argtypes) of every exported symbol
 _P, _I32, _I64, _U64, _D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
 SIGNATURES = {
@@ -59,6 +94,10 @@ SIGNATURES = {
     "sbv_mlp_train": (C.c_int, [_P, _P, _P, _I64, _I32, _I32, C.c_float, _U64, C.POINTER(C.c_float),
                                 _P]),
     "sbv_mlp_predict": (C.c_int, [_P, _P, _I64, _P, _P, _P]),
+    "sbv_mle": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64, _I32, _I32, _P, _P,
+                          _P, _P, _P, _P, _P, _P, _I64, C.POINTER(_I64), _P]),
+    "sbv_mle_multistart": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64, _I32,
+                                     _I32, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 
 
@@ -232,6 +271,53 @@ class Context:
         """Capture one evaluation as a CUDA graph; returns a LoglikGraph."""
         return LoglikGraph(self, X, y, ptr, pts, nbr, cnt, B, nu2, precision, nmax, block_terms,
                            status)
+
+    def _structure(self, X, y, ptr, pts, nbr, cnt):
+        X = _dev(X, None, "X")
+        return (_ptr(X), _xdtype(X), _ptr(_dev(y, torch.float64, "y")), X.shape[0], X.shape[1],
+                _ptr(_dev(ptr, torch.int64, "ptr")), _ptr(_dev(pts, torch.int32, "pts")),
+                _ptr(_dev(nbr, torch.int32, "nbr")), _ptr(_dev(cnt, torch.int32, "cnt")),
+                cnt.numel(), nbr.shape[1])
+
+    def sbv_mle(self, X, y, ptr, pts, nbr, cnt, theta0, lower=None, upper=None, opts=None,
+                nmax: int = 0, history: int = 0, stream=None):
+        """BFGS maximum-likelihood estimate; returns (theta, MleResult[, (hist_u, hist_l)])."""
+        st = self._structure(X, y, ptr, pts, nbr, cnt)
+        d = st[4]
+        th0 = _host_f64(theta0, "theta0").reshape(2 + d)
+        lo = None if lower is None else _host_f64(lower, "lower").reshape(2 + d)
+        hi = None if upper is None else _host_f64(upper, "upper").reshape(2 + d)
+        out = np.empty(2 + d)
+        res = MleResult()
+        hu = np.empty((max(history, 1), 2 + d))
+        hl = np.empty(max(history, 1))
+        hlen = C.c_int64(0)
+        rc = self.lib.sbv_mle(self.h, *st, int(nmax), _ptr(th0), _ptr(lo), _ptr(hi),
+                              C.byref(opts) if opts is not None else None, _ptr(out), C.byref(res),
+                              _ptr(hu) if history else None, _ptr(hl) if history else None, history,
+                              C.byref(hlen) if history else None, _stream(stream))
+        self._check(rc)
+        if history:
+            return out, res, (hu[:hlen.value], hl[:hlen.value])
+        return out, res
+
+    def sbv_mle_multistart(self, X, y, ptr, pts, nbr, cnt, starts, lower=None, upper=None,
+                           opts=None, mlp=None, sopts=None, nmax: int = 0, stream=None):
+        """MLE from every row of starts; returns (thetas, [MleResult])."""
+        st = self._structure(X, y, ptr, pts, nbr, cnt)
+        d = st[4]
+        S0 = _host_f64(starts, "starts").reshape(-1, 2 + d)
+        lo = None if lower is None else _host_f64(lower, "lower").reshape(2 + d)
+        hi = None if upper is None else _host_f64(upper, "upper").reshape(2 + d)
+        out = np.empty_like(S0)
+        res = (MleResult * len(S0))()
+        rc = self.lib.sbv_mle_multistart(self.h, *st, int(nmax), _ptr(S0), len(S0), _ptr(lo), _ptr(hi),
+                                         C.byref(opts) if opts is not None else None,
+                                         mlp.h if mlp is not None else None,
+                                         C.byref(sopts) if sopts is not None else None, _ptr(out),
+                                         C.cast(res, C.c_void_p), _stream(stream))
+        self._check(rc)
+        return out, [r for r in res]
 
     @staticmethod
     def max_block_size(ptr, cnt) -> int:
