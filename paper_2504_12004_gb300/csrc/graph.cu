@@ -162,8 +162,9 @@ extern "C" int sbv_loglik_graph_create(sbv_ctx* ctx, const void* X, int dtype, c
       if ((st = mixed_split(ctx, X, dtype, n * d, (float2*)p, cap))) return bail(st);
       P.Xs = (const float2*)p;
     }
-    if ((st = own(g, 4, mp.scratch_stride * mp.grid * sizeof(float2), &p))) return bail(st);
+    if ((st = own(g, 4, mp.scratch_bytes(), &p))) return bail(st);
     P.scratch = (float2*)p;
+    P.gA = mp.lay.ga ? (float*)((unsigned char*)p + mp.ga_offset()) : nullptr;
     if ((st = mixed_prepare(ctx))) return bail(st);
   } else {
     if ((st = fp64_plan(ctx, nmax, d, items, &fp))) return bail(st);

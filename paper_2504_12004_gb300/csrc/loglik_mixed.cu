@@ -133,7 +133,7 @@ __global__ void split_points_kernel(const double* __restrict__ X, int64_t total,
   }
 }
 
-template <int THREADS, bool TC, bool PRED>
+template <int THREADS, bool TC, bool PRED, bool GA>
 __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
 loglik_mixed_kernel(MixedArgs P) {
   constexpr int MX_WARPS = THREADS / 32;
@@ -147,7 +147,7 @@ loglik_mixed_kernel(MixedArgs P) {
   float* Pt = (float*)(smem + lay.off_u);                 // FP32 panel, column-major
   unsigned char* opnd = smem + lay.off_u;                 // BF16 panel pieces
   float4* part = (float4*)(smem + lay.off_u);             // residual partial sums
-  float* A = (float*)(smem + lay.off_A);
+  float* A = GA ? P.gA + (size_t)blockIdx.x * lay.a_floats : (float*)(smem + lay.off_A);
   __shared__ float tab_h[256], tab_l[256];
   __shared__ unsigned int s_item;
   __shared__ int s_fail;
@@ -170,12 +170,18 @@ loglik_mixed_kernel(MixedArgs P) {
   float* r2 = vec + 3 * (cap + 1);
   float* ldiag = vec + 4 * (cap + 1);
   float* idiag = vec + 5 * (cap + 1);
-  float* c1 = vec + 6 * (cap + 1);
-  float* c2 = vec + 7 * (cap + 1);
+  float* c1 = (float*)(smem + lay.off_c);   // live during refinement only
+  float* c2 = c1 + (cap + 1);
   // refinement steps: one for the likelihood (its quadratic forms are second
   // order in the solve error); three for prediction, whose variance
   // sigma^2 + tau^2 - Sigma_*J z cancels and is first order in the error of z
-  constexpr int NREF = PRED ? 3 : 1;
+  constexpr int NREF = PRED ? 3 : 4;   // at most
+  // The likelihood stops refining once the estimated remaining error of the
+  // block's quadratic form is below REF_TOL per point: after a step whose
+  // correction changed the form by dq, the error left is about dq^2 / |q|
+  // (the first solve's relative error times dq).  Well-conditioned blocks stop
+  // after one step; ill-conditioned ones (long ranges, small nugget) take more.
+  constexpr double REF_TOL = 1e-7;
 
   for (int i = threadIdx.x; i < 256; i += blockDim.x) {
     tab_h[i] = C.tab_h[i];
@@ -670,11 +676,26 @@ loglik_mixed_kernel(MixedArgs P) {
     }
     __syncthreads();
     bwd_solve2(A, N, r1, r2);
+    double dq = 0.0, qs = 0.0;
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
       c1[p] += r1[p];
       c2[p] += r2[p];
+      if (!PRED) {
+        const double yp = (double)yv[p].x + (double)yv[p].y;
+        dq += yp * (double)r1[p];
+        qs += fabs(yp * ((double)x0[p] + (double)c1[p]));
+        if (p < mb) {
+          dq -= yp * (double)r2[p];
+          qs += fabs(yp * ((double)x0J[p] + (double)c2[p]));
+        }
+      }
     }
     __syncthreads();
+    if (!PRED) {
+      const double dqs = cta_sum_mx(dq, red);
+      const double qss = cta_sum_mx(qs, red);
+      if (dqs * dqs <= REF_TOL * (double)bs * qss) break;   // uniform over the CTA
+    }
     }  // refinement steps
     if (PRED) {
       // mean = Sigma_*J x, var = sigma^2 + tau^2 - Sigma_*J z, sums in FP64
@@ -749,6 +770,29 @@ static int upload_df_consts(sbv_ctx* ctx) {
   return SBV_OK;
 }
 
+template <int THREADS, bool TC, bool PRED, bool GA>
+static int occ(sbv_ctx* ctx, size_t bytes, int* out) {
+  SBV_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        out, loglik_mixed_kernel<THREADS, TC, PRED, GA>, THREADS, bytes));
+  return SBV_OK;
+}
+
+template <int THREADS>
+static int occ_t(sbv_ctx* ctx, bool tc, bool pred, bool ga, size_t bytes, int* out) {
+  if (ga) {
+    if (tc) return pred ? occ<THREADS, true, true, true>(ctx, bytes, out) : occ<THREADS, true, false, true>(ctx, bytes, out);
+    return pred ? occ<THREADS, false, true, true>(ctx, bytes, out) : occ<THREADS, false, false, true>(ctx, bytes, out);
+  }
+  if (tc) return pred ? occ<THREADS, true, true, false>(ctx, bytes, out) : occ<THREADS, true, false, false>(ctx, bytes, out);
+  return pred ? occ<THREADS, false, true, false>(ctx, bytes, out) : occ<THREADS, false, false, false>(ctx, bytes, out);
+}
+
+static int mixed_occupancy(sbv_ctx* ctx, int threads, bool tc, bool pred, bool ga, size_t bytes,
+                           int* out) {
+  return threads == 512 ? occ_t<512>(ctx, tc, pred, ga, bytes, out)
+                        : occ_t<256>(ctx, tc, pred, ga, bytes, out);
+}
+
 // ---------------------------------------------------------------------------
 // Launch planning: layout, threads per CTA, grid, scratch size.  The shape
 // (threads, CTAs per SM) comes from the context's autotuning record when one
@@ -763,14 +807,14 @@ int mixed_plan(sbv_ctx* ctx, int nmax, int d, int precision, bool pred, int64_t 
   o->pred = pred;
   o->lay = mixed_layout(ncap, d, tc);
   const size_t static_smem = 2 * 256 * 4 + 1024;
+  if (o->lay.bytes + static_smem > ctx->smem_optin) o->lay = mixed_layout(ncap, d, tc, true);
   if (o->lay.bytes + static_smem > ctx->smem_optin)
     return fail(ctx, SBV_EUNSUPPORTED,
                 "mixed path: a block with N=%d (d=%d) needs %zu bytes of shared memory", nmax, d,
                 o->lay.bytes);
-  // 228 KB of shared memory per SM, 1 KB reserved per resident CTA
-  const size_t per_cta = o->lay.bytes + static_smem + 1024;
-  const int fit = (int)std::max<size_t>(1, (228 * 1024) / per_cta);
-  int threads = 256, per_sm = std::min(fit, 2);
+  int st = mixed_prepare(ctx);   // occupancy queries need the shared-memory opt-in
+  if (st) return st;
+  int threads = 256, per_sm = 2;
   if (ctx->force.threads) {
     threads = ctx->force.threads;
     per_sm = ctx->force.per_sm;
@@ -781,7 +825,13 @@ int mixed_plan(sbv_ctx* ctx, int nmax, int d, int precision, bool pred, int64_t 
         per_sm = t.per_sm;
       }
   }
-  if (threads == 512) per_sm = 1;               // 117 registers x 512 threads: one CTA per SM
+  // resident CTAs per SM for this variant and shared-memory size, from the
+  // runtime's occupancy calculator (registers, shared memory, reservations)
+  int fit = 0;
+  if ((st = mixed_occupancy(ctx, threads, tc, pred, o->lay.ga, o->lay.bytes, &fit))) return st;
+  if (fit < 1)
+    return fail(ctx, SBV_EUNSUPPORTED, "mixed path: no CTA of %d threads fits an SM (N=%d, d=%d)",
+                threads, nmax, d);
   per_sm = std::max(1, std::min(per_sm, fit));
   int grid = ctx->num_sms * per_sm;
   if (grid > items) grid = (int)std::max<int64_t>(items, 1);
@@ -802,15 +852,25 @@ int mixed_split(sbv_ctx* ctx, const void* X, int dtype, int64_t total, float2* x
 
 template <int THREADS, bool TC, bool PRED>
 static int launch_variant(sbv_ctx* ctx, const MixedArgs& P, int grid, cudaStream_t s) {
-  loglik_mixed_kernel<THREADS, TC, PRED><<<grid, THREADS, P.lay.bytes, s>>>(P);
+  if (P.lay.ga)
+    loglik_mixed_kernel<THREADS, TC, PRED, true><<<grid, THREADS, P.lay.bytes, s>>>(P);
+  else
+    loglik_mixed_kernel<THREADS, TC, PRED, false><<<grid, THREADS, P.lay.bytes, s>>>(P);
   SBV_LAUNCH_CHECK(ctx, "loglik_mixed_kernel");
   return SBV_OK;
 }
 
+// Both variants may use the largest dynamic shared memory; the global-A
+// variant prefers the smallest shared-memory carve-out so that the rest of
+// the SM's 256 KB serves as L1 for its triangles.
 template <int THREADS, bool TC, bool PRED>
 static int allow_smem(sbv_ctx* ctx, int bytes) {
-  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<THREADS, TC, PRED>,
+  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<THREADS, TC, PRED, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<THREADS, TC, PRED, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<THREADS, TC, PRED, true>,
+                                         cudaFuncAttributePreferredSharedMemoryCarveout, 0));
   return SBV_OK;
 }
 
@@ -866,8 +926,10 @@ static int launch_mixed(sbv_ctx* ctx, MixedArgs& P, int nmax, int precision, boo
     if ((st = mixed_split(ctx, P.a.X, P.a.dtype, total, xs, s))) return st;
     P.Xs = xs;
   }
-  P.scratch = (float2*)ws_get(ctx, WS_MATRIX, o.scratch_stride * o.grid * sizeof(float2), &st);
-  if (!P.scratch) return st;
+  unsigned char* buf = (unsigned char*)ws_get(ctx, WS_MATRIX, o.scratch_bytes(), &st);
+  if (!buf) return st;
+  P.scratch = (float2*)buf;
+  P.gA = o.lay.ga ? (float*)(buf + o.ga_offset()) : nullptr;
   return mixed_enqueue(ctx, P, o, s);
 }
 

@@ -19,35 +19,46 @@ struct MixedLayout {
   int d;
   int pstride;          // row stride of the FP32 column-major panel (CUDA-core update)
   uint32_t opnd_piece;  // bytes of one BF16 operand piece (tensor-core update)
-  size_t off_y, off_v, off_u, off_vl, off_A, bytes;
+  bool ga;              // the packed triangle A lives in global memory (per-CTA slice)
+  size_t a_floats;      // floats of one packed triangle (rounded to 64)
+  size_t off_y, off_v, off_u, off_vl, off_c, off_A, bytes;
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // One shared-memory region (off_u) serves three phases in turn: the scaled
-// coordinates (covariance), the panel operand (factorisation) and the
-// residual partial sums (refinement).
-__host__ __device__ inline MixedLayout mixed_layout(int ncap, int d, bool tc) {
+// coordinates (covariance), the panel operand (factorisation) and, during
+// refinement, the residual partial sums followed (off_c) by the two
+// accumulated corrections.
+// With ga, the packed triangle (the largest piece, 4 (N+1)(N+2)/2 bytes) is
+// left out of shared memory; the kernel then addresses a per-CTA slice of a
+// global buffer, which stays in L1/L2 for the CTA's lifetime.
+__host__ __device__ inline MixedLayout mixed_layout(int ncap, int d, bool tc, bool ga = false) {
   MixedLayout L;
   L.ncap = ncap;
   L.d = d;
+  L.ga = ga;
+  L.a_floats = align_up((size_t)(ncap + 1) * (ncap + 2) / 2, 64);
   L.pstride = (int)align_up((size_t)ncap + 1, 4);
   L.opnd_piece = (uint32_t)(((ncap + 1 + 127) / 128) * 128 * 32);
   size_t o = 0;
   L.off_y = o;  o += align_up((size_t)(ncap + 1) * sizeof(float2), 16);
-  // x0 x0J r1 r2 ldiag idiag c1 c2 (c: corrections accumulated over refinement steps)
-  L.off_v = o;  o += align_up((size_t)8 * (ncap + 1) * sizeof(float), 16);
+  // x0 x0J r1 r2 ldiag idiag
+  L.off_v = o;  o += align_up((size_t)6 * (ncap + 1) * sizeof(float), 16);
   o = align_up(o, 128);
   const size_t coord = align_up((size_t)d * ncap * sizeof(float), 16);
   size_t uni = 2 * coord;
   const size_t panel = tc ? 3 * (size_t)L.opnd_piece : (size_t)NB * L.pstride * sizeof(float);
   const size_t part = (size_t)(32 * MX_MAX_WARPS > ncap ? 32 * MX_MAX_WARPS : ncap) * sizeof(float4);
+  const size_t corr = align_up((size_t)2 * (ncap + 1) * sizeof(float), 16);
   if (panel > uni) uni = panel;
-  if (part > uni) uni = part;
+  if (part + corr > uni) uni = part + corr;
   L.off_u = o;
   L.off_vl = o + coord;
+  L.off_c = o + part;
   o += align_up(uni, 16);
-  L.off_A = o;  o += align_up((size_t)(ncap + 1) * (ncap + 2) / 2 * sizeof(float), 16);
+  L.off_A = o;
+  if (!ga) o += align_up((size_t)(ncap + 1) * (ncap + 2) / 2 * sizeof(float), 16);
   L.bytes = o;
   return L;
 }
@@ -57,6 +68,7 @@ struct MixedArgs {
   const float2* Xs;      // split FP64 points, or NULL for FP32 points (a.X read directly)
   float2* scratch;
   size_t scratch_stride;
+  float* gA;             // packed triangles, lay.a_floats per CTA (lay.ga only)
   MixedLayout lay;
   // prediction mode: one item per test point, J = its m nearest training points
   const void* Xt;        // test points (dtype of a.X)
@@ -71,6 +83,12 @@ struct MixedPlan {
   bool tc, pred;
   int threads, grid;
   size_t scratch_stride;  // float2 elements per CTA slice
+  // bytes of the per-CTA scratch buffer: the FP32-pair copy of Sigma, then
+  // (lay.ga) the packed triangles from byte offset ga_offset
+  size_t scratch_bytes() const {
+    return ga_offset() + (lay.ga ? lay.a_floats * sizeof(float) * (size_t)grid : 0);
+  }
+  size_t ga_offset() const { return align_up(scratch_stride * sizeof(float2) * (size_t)grid, 256); }
 };
 
 int mixed_plan(sbv_ctx* ctx, int nmax, int d, int precision, bool pred, int64_t items,

@@ -226,18 +226,30 @@ def test_loglik_degenerate_structures(ctx):
     assert abs(ll[0] - want) / 300 <= TOL_FP64
 
 
-def test_loglik_large_blocks_use_global_scratch(ctx):
-    # N = m + bs above the shared-memory capacity of the FP64 kernel
+# Smooth nu = 5/2 kernel with long ranges over blocks of 500-870 points
+# (kappa ~ 1e5): the log-determinant of the FP32 factor carries ~2e-6 per
+# point here (a plain FP32 Cholesky: up to 1.3e-5, measured on the CPU), so
+# the mixed paths are held to 3e-6 in this regime.  The 1e-6 bar of the
+# benchmark workloads is asserted elsewhere, including blocks past shared
+# memory at d = 20 (test_gpu_batched.py).
+LARGE_TOLS = {"fp64": TOL_FP64, "mixed": 3e-6, "mixed_bf16": 3e-6}
+
+
+@pytest.mark.parametrize("precision,tol", list(LARGE_TOLS.items()))
+def test_loglik_large_blocks_use_global_scratch(ctx, precision, tol):
+    # N = m + bs (up to ~870) above the shared-memory capacity of both
+    # kernels: the FP64 kernel factors in global scratch, the mixed kernel
+    # keeps its packed triangle in a per-CTA global slice
     X = uniform_points(3000, 4, 51)
     y = standard_normal(3000, 52)
     beta = np.array([0.3, 0.5, 0.7, 0.9])
     b = sbv.blocking(X, beta, 12, 2, 1)
     b["nbr"], b["cnt"] = sbv.knn(b["Z"], b["blk"], b["rank"], b["centres"], 400)
     th = np.array([1.0, 0.01, 0.3, 0.5, 0.7, 0.9])
-    ll, bt, st = gpu_loglik(ctx, X, y, b, th, 5, "fp64")
+    ll, bt, st = gpu_loglik(ctx, X, y, b, th, 5, precision)
     want = sbv.loglik(X, y, b["ptr"], b["pts"], b["nbr"], b["cnt"], b["rank"], th, 5)
     assert np.all(st == 0)
-    assert abs(ll[0] - want) / 3000 <= TOL_FP64
+    assert abs(ll[0] - want) / 3000 <= tol
 
 
 def test_loglik_deterministic(ctx, gp5d, gp5d_oracle):
