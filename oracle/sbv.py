@@ -81,30 +81,99 @@ def centroids(Z: np.ndarray, blk: np.ndarray, k: int, prev: np.ndarray | None = 
     return C
 
 
-def blocking(X, beta_scale, bc: int, kmeans_iters: int, seed: int):
-    """Scale, pick bc random anchors (RAC), run up to T Lloyd iterations, order blocks.
+def slabs(X, beta_scale, P: int):
+    """Alg. 2: slab of each point along d_max = argmax_j 1/beta_j.
 
-    Readings: anchors are the first bc entries of a Fisher-Yates shuffle of the
-    point indices drawn from SplitMix64(seed); T = 0 is RAC exactly as in
-    Alg. 3; iteration stops early when no assignment changes; empty blocks are
-    dropped keeping the relative order of the others; the random block order
-    of Alg. 1 Step 2 is a full Fisher-Yates shuffle drawn from the same stream
-    after the anchors; block perm[r] receives rank r.
+    The slab index is int(x_dmax * P) on the unscaled coordinate (FP64
+    product, then floor), clamped to [0, P-1] for points outside [0, 1);
+    ties in 1/beta go to the first dimension.
+    """
+    beta = np.asarray(beta_scale, dtype=np.float64)
+    dmax = int(np.argmax(1.0 / beta))
+    x = np.asarray(X, dtype=np.float64)[:, dmax]
+    q = np.floor(x * float(P))
+    return np.clip(q, 0, P - 1).astype(np.int64), dmax
+
+
+def slab_quota(counts, bc: int) -> np.ndarray:
+    """Anchors per slab (Alg. 3 chooses k_p per partition; the paper does not
+    say how many).  Reading: one anchor for every non-empty slab, the other
+    bc - (#non-empty) shared in proportion to the slab sizes by the largest
+    remainder method (exact integers; ties to the lower slab), and never more
+    anchors than points in a slab."""
+    counts = [int(c) for c in counts]
+    n = sum(counts)
+    k = [1 if c > 0 else 0 for c in counts]
+    R = max(bc - sum(k), 0)
+    base = [R * c // n for c in counts]
+    rem = [R * c % n for c in counts]
+    extra = R - sum(base)
+    order = sorted(range(len(counts)), key=lambda q: (-rem[q], q))
+    for q in range(len(counts)):
+        k[q] += base[q]
+    for q in order[:extra]:
+        k[q] += 1
+    return np.array([min(kq, c) for kq, c in zip(k, counts)], dtype=np.int64)
+
+
+def assign_within(Z: np.ndarray, C: np.ndarray, pslab: np.ndarray, cslab: np.ndarray) -> np.ndarray:
+    """Alg. 3 assignment inside each slab: argmin over the slab's own centres."""
+    blk = np.zeros(Z.shape[0], dtype=np.int64)
+    for q in np.unique(pslab):
+        pi = np.flatnonzero(pslab == q)
+        ci = np.flatnonzero(cslab == q)
+        blk[pi] = ci[assign(Z[pi], C[ci])]
+    return blk
+
+
+def blocking(X, beta_scale, bc: int, kmeans_iters: int, seed: int, partitions: int = 1):
+    """Scale, pick random anchors (RAC), run up to T Lloyd iterations, order blocks.
+
+    With partitions = P > 1 the points are first split into P slabs along the
+    most relevant dimension (Alg. 2) and RAC (and the Lloyd iterations) run in
+    every slab on its own points and anchors (Alg. 3, per worker); P = 1 is
+    the single-partition case.
+
+    Readings: the anchors of slab q are the first k_q entries of a
+    Fisher-Yates shuffle of that slab's points (listed in increasing index),
+    slabs taken in increasing q, all draws from one SplitMix64(seed) stream;
+    the k_q follow slab_quota.  Centres are numbered slab by slab.  T = 0 is
+    RAC exactly as in Alg. 3; iteration stops early when no assignment
+    changes; empty blocks are dropped keeping the relative order of the
+    others; the random block order of Alg. 1 Step 2 is a full Fisher-Yates
+    shuffle drawn from the same stream after the anchors; block perm[r]
+    receives rank r.
 
     Returns dict(blk, ptr, pts, rank, centres, bc_eff, Z).
     """
     Z = scale(X, beta_scale)
     n = Z.shape[0]
+    if partitions > 1:
+        pslab, _ = slabs(X, beta_scale, partitions)
+    else:
+        pslab = np.zeros(n, dtype=np.int64)
+    P = max(int(partitions), 1)
+    kq = slab_quota(np.bincount(pslab, minlength=P), bc)
     rng = SplitMix64(seed)
-    anchors = partial_shuffle_prefix(n, bc, rng)
+    anchors, cslab = [], []
+    for q in range(P):
+        if kq[q] == 0:
+            continue
+        members = np.flatnonzero(pslab == q)
+        pos = partial_shuffle_prefix(members.size, int(kq[q]), rng)
+        anchors.extend(members[np.asarray(pos, dtype=np.int64)])
+        cslab.extend([q] * int(kq[q]))
+    K = len(anchors)
+    cslab = np.asarray(cslab, dtype=np.int64)
     C = Z[np.asarray(anchors, dtype=np.int64)].copy()
-    blk = assign(Z, C)
+    blk = assign_within(Z, C, pslab, cslab)
     for _ in range(kmeans_iters):
-        C = centroids(Z, blk, bc, prev=C)
-        new = assign(Z, C)
+        C = centroids(Z, blk, K, prev=C)
+        new = assign_within(Z, C, pslab, cslab)
         if np.array_equal(new, blk):
             break
         blk = new
+    bc = K
     used = np.unique(blk)
     remap = np.full(bc, -1, dtype=np.int64)
     remap[used] = np.arange(used.size)
