@@ -115,6 +115,26 @@ int sbv_blocking(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_t d,
                  int32_t* rank, double* centres, int64_t* bc_eff, void* stream);
 
 /*
+ * sbv_blocking_partitioned -- sbv_blocking with the partitioning of Alg. 2
+ * first: points go to `partitions` = P slabs by int(x_dmax * P) on the
+ * unscaled coordinate of the most relevant dimension d_max = argmax_j
+ * 1/beta_scale_j (FP64 product and floor, clamped to [0, P-1]; ties to the
+ * first dimension), then RAC and the Lloyd iterations run inside every slab
+ * on its own points (Alg. 3 per partition).  Anchors per slab: one for every
+ * non-empty slab, the rest of bc in proportion to the slab sizes (largest
+ * remainder, ties to the lower slab), never more than the slab's points; the
+ * anchors of slab q are the first k_q entries of a Fisher-Yates shuffle of
+ * the slab's points in increasing index, slabs in increasing q, all from one
+ * SplitMix64(seed) stream, followed by the block-order shuffle.  P = 1 is
+ * sbv_blocking exactly.  1 <= P <= bc.  Outputs and errors as sbv_blocking.
+ */
+int sbv_blocking_partitioned(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_t d,
+                             const double* beta_scale, int64_t bc, int32_t kmeans_iters,
+                             uint64_t seed, int32_t partitions, int32_t* blk, int64_t* ptr,
+                             int32_t* pts, int32_t* rank, double* centres, int64_t* bc_eff,
+                             void* stream);
+
+/*
  * sbv_knn -- earlier-ordered m nearest neighbours of every block (Alg. 4,
  * Eq. mmsearchingBV).
  *
@@ -136,6 +156,17 @@ int sbv_knn(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_t d,
             const double* beta_scale, const int64_t* ptr, const int32_t* pts,
             const int32_t* rank, const double* centres, int64_t bc, int32_t m,
             int32_t* nbr, int32_t* cnt, void* stream);
+
+/*
+ * sbv_set_knn_mode -- how sbv_knn searches: 0 (default) chooses by size,
+ * 1 always scans every earlier candidate, 2 always uses the pruned search
+ * (blocks as clusters with centre and radius bounds, a 2-D grid over block
+ * centres, a per-query radius standing in for the lambda of Eq.
+ * distancethreshold and a check that the m-th key lies inside it, with
+ * retries and the full scan as fallbacks).  All modes return the same
+ * neighbours key for key.  Errors: SBV_EINVAL.
+ */
+int sbv_set_knn_mode(sbv_ctx* ctx, int32_t mode);
 
 /*
  * sbv_loglik -- Block Vecchia log-likelihood for B parameter rows (Alg. 5

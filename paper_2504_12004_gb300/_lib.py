@@ -68,11 +68,14 @@ SIGNATURES = {
     "sbv_last_error": (C.c_char_p, [_P]),
     "sbv_blocking": (C.c_int, [_P, _P, C.c_int, _I64, _I32, _P, _I64, _I32, _U64,
                                _P, _P, _P, _P, _P, C.POINTER(_I64), _P]),
+    "sbv_blocking_partitioned": (C.c_int, [_P, _P, C.c_int, _I64, _I32, _P, _I64, _I32, _U64, _I32,
+                                           _P, _P, _P, _P, _P, C.POINTER(_I64), _P]),
     "sbv_knn": (C.c_int, [_P, _P, C.c_int, _I64, _I32, _P, _P, _P, _P, _P, _I64, _I32,
                           _P, _P, _P]),
     "sbv_loglik": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64, _I32,
                              _I32, _P, _I32, _I32, _I32, _P, _P, _P, _P]),
     "sbv_sync_status": (C.c_int, [_P, _P]),
+    "sbv_set_knn_mode": (C.c_int, [_P, _I32]),
     "sbv_predict": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _I64, _P, _I32, _P,
                               _I32, _I32, _P, _P, _P, _P, _P]),
     "sbv_loglik_fp64_noalloc": (C.c_int, [_P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64,
@@ -192,7 +195,8 @@ class Context:
             raise SBVError(rc, self.lib.sbv_last_error(self.h).decode())
 
     # ---- entry points -------------------------------------------------------
-    def sbv_blocking(self, X, beta_scale, bc: int, kmeans_iters: int, seed: int, stream=None):
+    def sbv_blocking(self, X, beta_scale, bc: int, kmeans_iters: int, seed: int, stream=None,
+                     partitions: int = 1):
         X = _dev(X, None, "X")
         n, d = X.shape
         beta = _host_f64(beta_scale, "beta_scale")
@@ -203,13 +207,23 @@ class Context:
         rank = torch.empty(bc, dtype=torch.int32, device=dev)
         centres = torch.empty(bc, d, dtype=torch.float64, device=dev)
         bc_eff = C.c_int64(0)
-        rc = self.lib.sbv_blocking(self.h, _ptr(X), _xdtype(X), n, d, _ptr(beta), bc, kmeans_iters,
-                                   seed, _ptr(blk), _ptr(ptr), _ptr(pts), _ptr(rank), _ptr(centres),
-                                   C.byref(bc_eff), _stream(stream))
+        if partitions == 1:
+            rc = self.lib.sbv_blocking(self.h, _ptr(X), _xdtype(X), n, d, _ptr(beta), bc,
+                                       kmeans_iters, seed, _ptr(blk), _ptr(ptr), _ptr(pts),
+                                       _ptr(rank), _ptr(centres), C.byref(bc_eff), _stream(stream))
+        else:
+            rc = self.lib.sbv_blocking_partitioned(self.h, _ptr(X), _xdtype(X), n, d, _ptr(beta), bc,
+                                                   kmeans_iters, seed, partitions, _ptr(blk),
+                                                   _ptr(ptr), _ptr(pts), _ptr(rank), _ptr(centres),
+                                                   C.byref(bc_eff), _stream(stream))
         self._check(rc)
         k = bc_eff.value
         return dict(blk=blk, ptr=ptr[:k + 1].contiguous(), pts=pts, rank=rank[:k].contiguous(),
                     centres=centres[:k].contiguous(), bc_eff=k)
+
+    def sbv_set_knn_mode(self, mode: int):
+        """0 automatic, 1 full scan, 2 pruned search (identical results)."""
+        self._check(self.lib.sbv_set_knn_mode(self.h, mode))
 
     def sbv_knn(self, X, beta_scale, ptr, pts, rank, centres, m: int, stream=None):
         X = _dev(X, None, "X")

@@ -162,6 +162,130 @@ assign_kernel(const double* __restrict__ Z, int64_t n, int d, const double* __re
   }
 }
 
+// Alg. 2: slab of each point, int(x_dmax * P) on the unscaled coordinate
+// (FP64 product, floor), clamped to [0, P-1].
+template <typename T>
+__global__ void slab_kernel(const T* __restrict__ X, int64_t n, int d, int dmax, int P,
+                            int32_t* __restrict__ slab) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double q = floor(__dmul_rn((double)X[i * d + dmax], (double)P));
+    slab[i] = q >= (double)(P - 1) ? P - 1 : (q > 0.0 ? (int32_t)q : 0);
+  }
+}
+
+// Assignment inside slabs (Alg. 3 per partition): the thread of sorted
+// position i handles point order[i]; its candidates are the centres
+// [cstart[s], cstart[s+1]) of its slab s.  Points are sorted by slab, so a
+// CTA usually meets one slab; centre tiles cover the union of its slabs'
+// ranges and every thread skips the centres of other slabs.  Same two-pass
+// screen and exact FP64 decision (ties to the smaller index) as assign_kernel.
+template <int DM>
+__global__ void __launch_bounds__(ASSIGN_THREADS)
+assign_slab_kernel(const double* __restrict__ Z, int64_t n, int d, const double* __restrict__ C,
+                   const int32_t* __restrict__ order, const int32_t* __restrict__ pslab,
+                   const int64_t* __restrict__ cstart, ScreenBound sb,
+                   const int32_t* __restrict__ old_blk, int32_t* __restrict__ blk,
+                   unsigned long long* __restrict__ changed) {
+  __shared__ float cf[ASSIGN_TILE * DM];
+  __shared__ unsigned long long s_lo, s_hi;
+  const int64_t i = blockIdx.x * (int64_t)ASSIGN_THREADS + threadIdx.x;
+  const bool live = i < n;
+  const int64_t p = live ? (int64_t)order[i] : 0;
+  int64_t c0 = 0, c1 = 0;
+  if (live) {
+    const int sl = pslab[p];
+    c0 = cstart[sl];
+    c1 = cstart[sl + 1];
+  }
+  if (threadIdx.x == 0) {
+    s_lo = ~0ull;
+    s_hi = 0ull;
+  }
+  __syncthreads();
+  if (live && c1 > c0) {
+    atomicMin(&s_lo, (unsigned long long)c0);
+    atomicMax(&s_hi, (unsigned long long)c1);
+  }
+  __syncthreads();
+  const int64_t lo = (int64_t)s_lo, hi = (int64_t)s_hi;
+  float zf[DM];
+#pragma unroll
+  for (int t = 0; t < DM; ++t) zf[t] = (live && t < d) ? (float)Z[p * d + t] : 0.0f;
+  float best_ub = INFINITY;
+  for (int64_t j0 = lo; j0 < hi; j0 += ASSIGN_TILE) {
+    const int nt = (int)min((int64_t)ASSIGN_TILE, hi - j0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nt * d; e += ASSIGN_THREADS) {
+      const int jj = e / d, t = e % d;
+      cf[jj * DM + t] = (float)C[(j0 + jj) * d + t];
+    }
+    __syncthreads();
+    if (live) {
+      for (int jj = 0; jj < nt; ++jj) {
+        const int64_t j = j0 + jj;
+        if (j < c0 || j >= c1) continue;
+        float acc = 0.0f;
+#pragma unroll
+        for (int t = 0; t < DM; ++t) {
+          if (t < d) {
+            const float df = zf[t] - cf[jj * DM + t];
+            acc = fmaf(df, df, acc);
+          }
+        }
+        best_ub = fminf(best_ub, acc + screen_margin(acc, sb));
+      }
+    }
+  }
+  double best = INFINITY;
+  int64_t arg = c0;
+  double zi[DM];
+#pragma unroll
+  for (int t = 0; t < DM; ++t) zi[t] = (live && t < d) ? Z[p * d + t] : 0.0;
+  for (int64_t j0 = lo; j0 < hi; j0 += ASSIGN_TILE) {
+    const int nt = (int)min((int64_t)ASSIGN_TILE, hi - j0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nt * d; e += ASSIGN_THREADS) {
+      const int jj = e / d, t = e % d;
+      cf[jj * DM + t] = (float)C[(j0 + jj) * d + t];
+    }
+    __syncthreads();
+    if (live) {
+      for (int jj = 0; jj < nt; ++jj) {
+        const int64_t j = j0 + jj;
+        if (j < c0 || j >= c1) continue;
+        float acc = 0.0f;
+#pragma unroll
+        for (int t = 0; t < DM; ++t) {
+          if (t < d) {
+            const float df = zf[t] - cf[jj * DM + t];
+            acc = fmaf(df, df, acc);
+          }
+        }
+        if (acc - screen_margin(acc, sb) <= best_ub) {
+          const double D = dist2_exact<DM>(zi, C + j * d, d);
+          if (D < best) {  // strict: ties keep the smaller index
+            best = D;
+            arg = j;
+          }
+        }
+      }
+    }
+  }
+  if (live) {
+    const int32_t a = (int32_t)arg;
+    if (old_blk && old_blk[p] != a) atomicAdd(changed, 1ull);
+    blk[p] = a;
+  }
+}
+
+__global__ void take_kernel(const int32_t* __restrict__ src, const int64_t* __restrict__ pos,
+                            int64_t k, int32_t* __restrict__ out) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < k;
+       j += (int64_t)gridDim.x * blockDim.x)
+    out[j] = src[pos[j]];
+}
+
 __global__ void iota_kernel(int32_t* __restrict__ v, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -277,6 +401,73 @@ static int launch_assign(sbv_ctx* ctx, const double* Z, int64_t n, int d, const 
   return SBV_OK;
 }
 
+static int launch_assign_slab(sbv_ctx* ctx, const double* Z, int64_t n, int d, const double* C,
+                              const int32_t* order, const int32_t* pslab, const int64_t* cstart,
+                              ScreenBound sb, const int32_t* old_blk, int32_t* blk,
+                              unsigned long long* changed, cudaStream_t s) {
+  int g = (int)((n + ASSIGN_THREADS - 1) / ASSIGN_THREADS);
+#define SBV_ASSIGN(DM)                                                                   \
+  assign_slab_kernel<DM><<<g, ASSIGN_THREADS, 0, s>>>(Z, n, d, C, order, pslab, cstart, sb, \
+                                                      old_blk, blk, changed)
+  if (d <= 4) SBV_ASSIGN(4);
+  else if (d <= 8) SBV_ASSIGN(8);
+  else if (d <= 12) SBV_ASSIGN(12);
+  else if (d <= 16) SBV_ASSIGN(16);
+  else if (d <= 24) SBV_ASSIGN(24);
+  else if (d <= 32) SBV_ASSIGN(32);
+  else SBV_ASSIGN(64);
+#undef SBV_ASSIGN
+  SBV_LAUNCH_CHECK(ctx, "assign_slab_kernel");
+  return SBV_OK;
+}
+
+// Anchors per slab (the reading for Alg. 3's k_p): one for every non-empty
+// slab, the remaining bc - #non-empty in proportion to the slab sizes by the
+// largest remainder (exact integers, ties to the lower slab), capped at the
+// slab's size.
+static std::vector<int64_t> slab_quota(const std::vector<int64_t>& cnt, int64_t bc) {
+  const size_t P = cnt.size();
+  int64_t n = 0, nonempty = 0;
+  for (int64_t c : cnt) {
+    n += c;
+    nonempty += c > 0;
+  }
+  std::vector<int64_t> k(P, 0), rem(P, 0);
+  const int64_t R = std::max<int64_t>(bc - nonempty, 0);
+  int64_t given = 0;
+  for (size_t q = 0; q < P; ++q) {
+    const unsigned __int128 prod = (unsigned __int128)R * (uint64_t)cnt[q];
+    const int64_t base = (int64_t)(prod / (uint64_t)n);
+    rem[q] = (int64_t)(prod % (uint64_t)n);
+    k[q] = (cnt[q] > 0 ? 1 : 0) + base;
+    given += base;
+  }
+  std::vector<size_t> ord(P);
+  for (size_t q = 0; q < P; ++q) ord[q] = q;
+  std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return rem[a] > rem[b]; });
+  for (int64_t e = 0; e < R - given && e < (int64_t)P; ++e) k[ord[e]] += 1;
+  for (size_t q = 0; q < P; ++q) k[q] = std::min(k[q], cnt[q]);
+  return k;
+}
+
+// First k entries of a Fisher-Yates shuffle of [0, n) (step j swaps a[j] and
+// a[j + U(n - j)]), from the caller's stream.
+static void partial_shuffle(int64_t n, int64_t k, SplitMix64& rng, int64_t* out) {
+  std::unordered_map<int64_t, int64_t> sw;
+  sw.reserve((size_t)k * 2);
+  auto get = [&](int64_t i) {
+    auto it = sw.find(i);
+    return it == sw.end() ? i : it->second;
+  };
+  for (int64_t j = 0; j < k; ++j) {
+    const int64_t r = j + (int64_t)rng.below((uint64_t)(n - j));
+    const int64_t aj = get(j), ar = get(r);
+    sw[j] = ar;
+    sw[r] = aj;
+    out[j] = ar;
+  }
+}
+
 // Sort point ids by block (stable: increasing index inside a block) and build
 // counts and CSR offsets for k blocks.
 static int group_by_block(sbv_ctx* ctx, const int32_t* blk, int64_t n, int64_t k,
@@ -301,9 +492,10 @@ static int group_by_block(sbv_ctx* ctx, const int32_t* blk, int64_t n, int64_t k
   return SBV_OK;
 }
 
-int run_blocking(sbv_ctx* ctx, const double* Z, int64_t n, int d, int64_t bc, int kmeans_iters,
-                 uint64_t seed, int32_t* blk, int64_t* ptr, int32_t* pts, int32_t* rank,
-                 double* centres, int64_t* bc_eff, cudaStream_t s) {
+int run_blocking(sbv_ctx* ctx, const double* Z, const void* X, int dtype, const double* h_beta,
+                 int64_t n, int d, int64_t bc, int kmeans_iters, uint64_t seed, int partitions,
+                 int32_t* blk, int64_t* ptr, int32_t* pts, int32_t* rank, double* centres,
+                 int64_t* bc_eff, cudaStream_t s) {
   int st = 0;
   // workspace: two centre buffers, old assignment, sort scratch, counts, ptr
   size_t cbytes = (size_t)bc * d * sizeof(double);
@@ -329,32 +521,75 @@ int run_blocking(sbv_ctx* ctx, const double* Z, int64_t n, int d, int64_t bc, in
   if ((st = absmax(ctx, Z, n * d, &M, s))) return st;
   ScreenBound sb = make_screen(M, d);
 
-  // RAC anchors: first bc entries of a Fisher-Yates shuffle of [0, n)
   SplitMix64 rng(seed);
-  std::vector<int32_t> anchors(bc);
-  {
-    std::unordered_map<int64_t, int64_t> sw;
-    sw.reserve((size_t)bc * 2);
-    auto get = [&](int64_t i) {
-      auto it = sw.find(i);
-      return it == sw.end() ? i : it->second;
-    };
-    for (int64_t j = 0; j < bc; ++j) {
-      int64_t r = j + (int64_t)rng.below((uint64_t)(n - j));
-      int64_t aj = get(j), ar = get(r);
-      sw[j] = ar;
-      sw[r] = aj;
-      anchors[j] = (int32_t)ar;
-    }
-  }
   int32_t* d_anchor = newid;  // reuse (bc entries) before compaction needs it
-  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(d_anchor, anchors.data(), bc * sizeof(int32_t),
-                                    cudaMemcpyHostToDevice, s));
+  // partitioned blocking (Alg. 2 then Alg. 3 per slab): slab of every point,
+  // points sorted by slab, anchors drawn slab by slab
+  int32_t* pslab = nullptr;
+  int32_t* sorder = nullptr;
+  int64_t* cstart = nullptr;
+  if (partitions > 1) {
+    const int P = partitions;
+    char* wsD = (char*)ws_get(ctx, WS_SORT_C, (size_t)n * 3 * sizeof(int32_t) + (size_t)(P + 1) * 16 + 1024, &st);
+    if (!wsD) return st;
+    pslab = (int32_t*)wsD;
+    sorder = pslab + n;
+    int32_t* skeys = sorder + n;
+    int64_t* scount = (int64_t*)(((uintptr_t)(skeys + n) + 15) & ~(uintptr_t)15);
+    cstart = scount + (P + 1);
+    int dmax = 0;
+    for (int t = 1; t < d; ++t)
+      if (1.0 / h_beta[t] > 1.0 / h_beta[dmax]) dmax = t;
+    const int g = grid_for(n, 256, ctx->num_sms);
+    if (dtype == SBV_F64)
+      slab_kernel<double><<<g, 256, 0, s>>>((const double*)X, n, d, dmax, P, pslab);
+    else
+      slab_kernel<float><<<g, 256, 0, s>>>((const float*)X, n, d, dmax, P, pslab);
+    SBV_LAUNCH_CHECK(ctx, "slab_kernel");
+    // stable sort of point ids by slab and slab sizes
+    if ((st = group_by_block(ctx, pslab, n, P, ids_tmp, skeys, sorder, scount, ptr_tmp, s)))
+      return st;
+    std::vector<int64_t> cnt(P), off(P + 1);
+    SBV_CUDA_TRY(ctx, cudaMemcpyAsync(cnt.data(), scount, P * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    off[0] = 0;
+    for (int q = 0; q < P; ++q) off[q + 1] = off[q] + cnt[q];
+    const std::vector<int64_t> kq = slab_quota(cnt, bc);
+    std::vector<int64_t> cs(P + 1, 0), pos;
+    for (int q = 0; q < P; ++q) cs[q + 1] = cs[q] + kq[q];
+    const int64_t K = cs[P];
+    pos.resize((size_t)K);
+    for (int q = 0; q < P; ++q) {
+      if (kq[q] == 0) continue;
+      partial_shuffle(cnt[q], kq[q], rng, pos.data() + cs[q]);
+      for (int64_t j = cs[q]; j < cs[q + 1]; ++j) pos[j] += off[q];
+    }
+    int64_t* d_pos = (int64_t*)ws_get(ctx, WS_EXTRA, (size_t)K * sizeof(int64_t) + 64, &st);
+    if (!d_pos) return st;
+    SBV_CUDA_TRY(ctx, cudaMemcpyAsync(d_pos, pos.data(), K * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    SBV_CUDA_TRY(ctx, cudaMemcpyAsync(cstart, cs.data(), (P + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    take_kernel<<<grid_for(K, 256, ctx->num_sms), 256, 0, s>>>(sorder, d_pos, K, d_anchor);
+    SBV_LAUNCH_CHECK(ctx, "take_kernel");
+    SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));  // host vectors copied before they go
+    bc = K;
+  } else {
+    // RAC anchors: first bc entries of a Fisher-Yates shuffle of [0, n)
+    std::vector<int64_t> a64(bc);
+    partial_shuffle(n, bc, rng, a64.data());
+    std::vector<int32_t> anchors(a64.begin(), a64.end());
+    SBV_CUDA_TRY(ctx, cudaMemcpyAsync(d_anchor, anchors.data(), bc * sizeof(int32_t),
+                                      cudaMemcpyHostToDevice, s));
+    SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  }
   gather_rows_kernel<<<grid_for(bc * d, 256, ctx->num_sms), 256, 0, s>>>(Z, d_anchor, bc, d, Ca);
   SBV_LAUNCH_CHECK(ctx, "gather_rows_kernel");
   SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));  // anchors buffer reused below
 
-  if ((st = launch_assign(ctx, Z, n, d, Ca, bc, sb, nullptr, blk, changed, s))) return st;
+  auto assign = [&](const double* Cc, const int32_t* old, int32_t* out) {
+    return pslab ? launch_assign_slab(ctx, Z, n, d, Cc, sorder, pslab, cstart, sb, old, out, changed, s)
+                 : launch_assign(ctx, Z, n, d, Cc, bc, sb, old, out, changed, s);
+  };
+  if ((st = assign(Ca, nullptr, blk))) return st;
   double* C = Ca;
   double* Cn = Cb;
   for (int it = 0; it < kmeans_iters; ++it) {
@@ -367,7 +602,7 @@ int run_blocking(sbv_ctx* ctx, const double* Z, int64_t n, int d, int64_t bc, in
     SBV_CUDA_TRY(ctx, cudaMemcpyAsync(old_blk, blk, n * sizeof(int32_t),
                                       cudaMemcpyDeviceToDevice, s));
     SBV_CUDA_TRY(ctx, cudaMemsetAsync(changed, 0, 8, s));
-    if ((st = launch_assign(ctx, Z, n, d, C, bc, sb, old_blk, blk, changed, s))) return st;
+    if ((st = assign(C, old_blk, blk))) return st;
     unsigned long long h_changed = 0;
     SBV_CUDA_TRY(ctx, cudaMemcpyAsync(&h_changed, changed, 8, cudaMemcpyDeviceToHost, s));
     SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));

@@ -253,6 +253,268 @@ __global__ void rank_sorted_blocks_kernel(const int32_t* __restrict__ rank, int6
     by_rank[bc - 1 - rank[j]] = (int32_t)j;  // longest prefixes first
 }
 
+// ---------------------------------------------------------------------------
+// Pruned exact search for large inputs.  The candidates are grouped in
+// blocks (the Vecchia blocks, listed by rank) with a centre c_b and a radius
+// rho_b >= max over members |x - c_b|; a 2-D grid over the two longest
+// scaled dimensions indexes the block centres.  A query with search radius R
+// scans only the blocks with |q - c_b| <= R + rho_b (the grid window has
+// half-width R + max rho); every other candidate lies farther than R.  If
+// the m-th smallest key found has D < R^2 (1 - 1e-9), no skipped candidate
+// can enter the m nearest, and the result equals the brute-force one key for
+// key.  Queries that fail this test are retried with a larger R and finally
+// sent to the brute-force kernel.  The radius plays the part of the
+// paper's lambda (Eq. distancethreshold), made exact by the check.
+// ---------------------------------------------------------------------------
+constexpr int PK_WARPS = 8;
+
+struct PrunedArgs {
+  const float* Z32;        // d x n, candidate (rank) order
+  const double* Z64;
+  const int32_t* cid;      // candidate position -> point index
+  int64_t n;
+  int d;
+  const int64_t* rptr;     // block of rank r: candidates [rptr[r], rptr[r+1])
+  const float* bcen;       // block centres by rank, nb x d
+  const float* brad;       // block radii by rank (rounded up)
+  float rad_max;
+  float slack;             // absolute slack of the float32 centre tests
+  int g0, g1;              // grid dimensions
+  double gmin0, gmin1, cell;
+  int nc0, nc1;
+  const int64_t* cell_ptr; // nc0 * nc1 + 1
+  const int32_t* cell_blk; // block ranks per cell, ascending
+  const double* Q;         // nq x d query coordinates
+  const int32_t* qlimit_rank;  // NULL: every block is a candidate
+  const int64_t* qlist;    // queries to process
+  int64_t nlist;
+  const float* qR;         // search radius per list entry
+  int m;
+  int cap;
+  ScreenBound sb;
+  int32_t* nbr;            // nq x m
+  int32_t* cnt;            // nq (or NULL)
+  int64_t* failed;         // queries whose check failed
+  unsigned long long* nfailed;
+};
+
+// sort the warp's buffer, keep the m smallest, update threshold and limit
+__device__ __forceinline__ void pk_compact(unsigned long long* kd, int32_t* ki, int cap, int m,
+                                           int& fill, double& thr, int32_t& thr_id, float& lim,
+                                           ScreenBound sb) {
+  const int lane = threadIdx.x & 31;
+  warp_sort(kd, ki, cap);
+  const int keep = min(fill, m);
+  fill = keep;
+  if (keep == m && keep > 0) {
+    thr = __longlong_as_double((long long)kd[keep - 1]);
+    thr_id = ki[keep - 1];
+    lim = screen_limit(thr, sb);
+  }
+  for (int e = keep + lane; e < cap; e += 32) {
+    kd[e] = ~0ull;
+    ki[e] = 0x7fffffff;
+  }
+  __syncwarp();
+}
+
+template <int DM>
+__global__ void __launch_bounds__(PK_WARPS * 32) knn_pruned_kernel(PrunedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cap = a.cap;
+  unsigned long long* kd = (unsigned long long*)smem + (size_t)warp * cap;
+  int32_t* ki = (int32_t*)((unsigned long long*)smem + (size_t)PK_WARPS * cap) + (size_t)warp * cap;
+  const int64_t li = (int64_t)blockIdx.x * PK_WARPS + warp;
+  if (li >= a.nlist) return;   // warp-uniform; the kernel uses no CTA barrier
+  const int64_t qi = a.qlist[li];
+  double qc[DM];
+  float qf[DM];
+#pragma unroll
+  for (int t = 0; t < DM; ++t) {
+    qc[t] = t < a.d ? a.Q[qi * a.d + t] : 0.0;
+    qf[t] = (float)qc[t];
+  }
+  const int64_t nb_lim = a.qlimit_rank ? (int64_t)a.qlimit_rank[qi] : INT64_MAX;
+  const float R = a.qR[li];
+  for (int e = lane; e < cap; e += 32) {
+    kd[e] = ~0ull;
+    ki[e] = 0x7fffffff;
+  }
+  __syncwarp();
+  int fill = 0;
+  double thr = INFINITY;
+  int32_t thr_id = 0x7fffffff;
+  float lim = INFINITY;
+  const double W = (double)R + (double)a.rad_max + (double)a.slack;
+  auto cell_of = [&](double v, double gmin, int nc) {
+    double c = floor((v - gmin) / a.cell);
+    return c < 0.0 ? 0 : (c > (double)(nc - 1) ? nc - 1 : (int)c);
+  };
+  // one extra cell on each side absorbs rounding of the cell indices
+  const int i0 = max(cell_of(qc[a.g0] - W, a.gmin0, a.nc0) - 1, 0);
+  const int i1 = min(cell_of(qc[a.g0] + W, a.gmin0, a.nc0) + 1, a.nc0 - 1);
+  const int j0 = max(cell_of(qc[a.g1] - W, a.gmin1, a.nc1) - 1, 0);
+  const int j1 = min(cell_of(qc[a.g1] + W, a.gmin1, a.nc1) + 1, a.nc1 - 1);
+  for (int ci = i0; ci <= i1; ++ci) {
+    for (int cj = j0; cj <= j1; ++cj) {
+      const int64_t cs = a.cell_ptr[(int64_t)ci * a.nc1 + cj], ce = a.cell_ptr[(int64_t)ci * a.nc1 + cj + 1];
+      for (int64_t base = cs; base < ce; base += 32) {
+        const int64_t idx = base + lane;
+        const int32_t b = idx < ce ? a.cell_blk[idx] : 0x7fffffff;
+        bool ok = idx < ce && (int64_t)b < nb_lim;
+        const bool past = __any_sync(0xffffffffu, idx < ce && (int64_t)b >= nb_lim);
+        if (ok) {
+          float acc = 0.0f;
+#pragma unroll
+          for (int t = 0; t < DM; ++t) {
+            if (t < a.d) {
+              const float df = qf[t] - a.bcen[(int64_t)b * a.d + t];
+              acc = fmaf(df, df, acc);
+            }
+          }
+          ok = sqrtf(acc) <= R + a.brad[b] + a.slack;
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, ok);
+        while (mask) {
+          const int src = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const int32_t bb = __shfl_sync(0xffffffffu, b, src);
+          const int64_t p0 = a.rptr[bb], p1 = a.rptr[bb + 1];
+          for (int64_t pb = p0; pb < p1; pb += 32) {
+            if (fill > cap - 32) pk_compact(kd, ki, cap, a.m, fill, thr, thr_id, lim, a.sb);
+            const int64_t p = pb + lane;
+            bool take = false;
+            unsigned long long db = 0;
+            int32_t id = 0;
+            if (p < p1) {
+              float acc = 0.0f;
+#pragma unroll
+              for (int t = 0; t < DM; ++t) {
+                if (t < a.d) {
+                  const float df = a.Z32[(size_t)t * a.n + p] - qf[t];
+                  acc = fmaf(df, df, acc);
+                }
+              }
+              if (acc <= lim) {
+                const double D = dist2_exact_strided(a.Z64 + p, (size_t)a.n, qc, a.d);
+                id = a.cid[p];
+                db = (unsigned long long)__double_as_longlong(D);
+                take = key_less(db, id, (unsigned long long)__double_as_longlong(thr), thr_id);
+              }
+            }
+            const unsigned tm = __ballot_sync(0xffffffffu, take);
+            if (take) {
+              const int pos = fill + __popc(tm & ((1u << lane) - 1u));
+              kd[pos] = db;
+              ki[pos] = id;
+            }
+            fill += __popc(tm);
+            __syncwarp();
+          }
+        }
+        if (past) break;   // ranks ascend inside a cell
+      }
+    }
+  }
+  pk_compact(kd, ki, cap, a.m, fill, thr, thr_id, lim, a.sb);
+  const double R2 = (double)R * (double)R * (1.0 - 1e-9);
+  const bool exact = fill == a.m && thr < R2;
+  if (exact) {
+    for (int e = lane; e < a.m; e += 32) a.nbr[qi * a.m + e] = ki[e];
+    if (lane == 0 && a.cnt) a.cnt[qi] = a.m;
+  } else if (lane == 0) {
+    a.failed[atomicAdd(a.nfailed, 1ull)] = qi;
+  }
+}
+
+// Centre (float32) and radius (max member distance, rounded up, float32) of
+// the block of every rank; one warp per block.
+__global__ void block_bounds_kernel(const double* __restrict__ Z64, int64_t n, int d,
+                                    const int64_t* __restrict__ rptr,
+                                    const double* __restrict__ centres,
+                                    const int32_t* __restrict__ blk_of_rank, int64_t nb,
+                                    float* __restrict__ bcen, float* __restrict__ brad) {
+  int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (; w < nb; w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const double* c = centres + (int64_t)blk_of_rank[w] * d;
+    double mx = 0.0;
+    for (int64_t p = rptr[w] + lane; p < rptr[w + 1]; p += 32)
+      mx = fmax(mx, dist2_exact_strided(Z64 + p, (size_t)n, c, d));
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane < d) bcen[w * d + lane] = (float)c[lane];
+    for (int t = 32 + lane; t < d; t += 32) bcen[w * d + t] = (float)c[t];
+    if (lane == 0) brad[w] = __double2float_ru(sqrt(mx) * (1.0 + 1e-6));
+  }
+}
+
+__global__ void iota_i32_kernel(int32_t* __restrict__ v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = (int32_t)i;
+}
+
+__global__ void cell_count_kernel(const int32_t* __restrict__ keys, int64_t n,
+                                  int64_t* __restrict__ counts) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd((unsigned long long*)&counts[keys[i]], 1ull);
+}
+
+__global__ void block_of_rank_kernel(const int32_t* __restrict__ rank, int64_t nb,
+                                     int32_t* __restrict__ out) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nb;
+       j += (int64_t)gridDim.x * blockDim.x)
+    out[rank[j]] = (int32_t)j;
+}
+
+__global__ void cell_key_kernel(const float* __restrict__ bcen, int64_t nb, int d, int g0, int g1,
+                                double gmin0, double gmin1, double cell, int nc0, int nc1,
+                                int32_t* __restrict__ key) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nb;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double c0 = floor(((double)bcen[j * d + g0] - gmin0) / cell);
+    double c1 = floor(((double)bcen[j * d + g1] - gmin1) / cell);
+    int i = c0 < 0.0 ? 0 : (c0 > nc0 - 1 ? nc0 - 1 : (int)c0);
+    int k = c1 < 0.0 ? 0 : (c1 > nc1 - 1 ? nc1 - 1 : (int)c1);
+    key[j] = i * nc1 + k;
+  }
+}
+
+// search radius per listed query: the ball expected to hold alpha * m of its
+// candidates at the average density, times `grow`
+__global__ void radius_kernel(const int64_t* __restrict__ qlist, int64_t nlist,
+                              const int32_t* __restrict__ qlimit_rank,
+                              const int64_t* __restrict__ rptr, int64_t n, double vol_over_vd,
+                              int m, int d, double grow, float* __restrict__ qR) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nlist;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ne = qlimit_rank ? rptr[qlimit_rank[qlist[i]]] : n;
+    const double r = pow(3.0 * m * vol_over_vd / (double)(ne > 0 ? ne : 1), 1.0 / d);
+    qR[i] = (float)(r * grow);
+  }
+}
+
+__global__ void minmax_kernel(const float* __restrict__ v, int64_t nb, int d,
+                              unsigned int* __restrict__ mn, unsigned int* __restrict__ mx) {
+  // order-preserving map of float bits to unsigned
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nb * d;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    unsigned int u = __float_as_uint(v[e]);
+    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    atomicMin(&mn[e % d], u);
+    atomicMax(&mx[e % d], u);
+  }
+}
+
+static float unmap_float(unsigned int u) {
+  u = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+}
+
 static int grid_for(int64_t work, int threads, int sms) {
   int64_t g = (work + threads - 1) / threads;
   int64_t cap = (int64_t)sms * 32;
@@ -292,6 +554,217 @@ static int launch_knn(sbv_ctx* ctx, KnnArgs& a, cudaStream_t s) {
   }
 #undef SBV_KNN
   SBV_LAUNCH_CHECK(ctx, "knn_kernel");
+  return SBV_OK;
+}
+
+__global__ void split_queries_kernel(const int32_t* __restrict__ qlimit_rank,
+                                     const int64_t* __restrict__ rptr, int64_t nq, int64_t small,
+                                     int64_t* __restrict__ big_list, unsigned long long* __restrict__ nbig,
+                                     int64_t* __restrict__ small_list,
+                                     unsigned long long* __restrict__ nsmall) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ne = rptr[qlimit_rank[q]];
+    if (ne > small) big_list[atomicAdd(nbig, 1ull)] = q;
+    else small_list[atomicAdd(nsmall, 1ull)] = q;
+  }
+}
+
+__global__ void i64_to_i32_kernel(const int64_t* __restrict__ a, int64_t k, int32_t* __restrict__ b) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < k;
+       j += (int64_t)gridDim.x * blockDim.x)
+    b[j] = (int32_t)a[j];
+}
+
+// The pruned search over the blocks of `base` (candidates in rank order):
+// queries whose candidate prefix is short, or whose check fails three times
+// with growing radius, go to the brute-force kernel.  Results are those of
+// the brute-force search for every query.
+static int knn_pruned(sbv_ctx* ctx, KnnArgs base, const int32_t* rank_of_block, int64_t nb,
+                      const double* centres, cudaStream_t s) {
+  int st = 0;
+  const int64_t n = base.n, nq = base.nq;
+  const int d = base.d, m = base.m;
+  const int sms = ctx->num_sms;
+  size_t bytes = (size_t)nb * 4 + (size_t)nb * d * 4 + (size_t)nb * 4 + (size_t)nb * 4 * 3 +
+                 (size_t)(nq + 8) * 8 * 4 + (size_t)nq * 4 * 2 + 4096 + (size_t)64 * 8;
+  char* wp = (char*)ws_get(ctx, WS_SORT_D, bytes, &st);
+  if (!wp) return st;
+  auto take = [&](size_t b) {
+    char* r = wp;
+    wp += (b + 255) / 256 * 256;
+    return r;
+  };
+  int32_t* blk_of_rank = (int32_t*)take((size_t)nb * 4);
+  float* bcen = (float*)take((size_t)nb * d * 4);
+  float* brad = (float*)take((size_t)nb * 4);
+  int32_t* keys = (int32_t*)take((size_t)nb * 4);
+  int32_t* keys_sorted = (int32_t*)take((size_t)nb * 4);
+  int32_t* iota = (int32_t*)take((size_t)nb * 4);
+  int64_t* listA = (int64_t*)take((size_t)(nq + 8) * 8);
+  int64_t* listB = (int64_t*)take((size_t)(nq + 8) * 8);
+  int64_t* small_list = (int64_t*)take((size_t)(nq + 8) * 8);
+  int64_t* spare = (int64_t*)take((size_t)(nq + 8) * 8);
+  float* qR = (float*)take((size_t)nq * 4);
+  int32_t* brute = (int32_t*)take((size_t)nq * 4);
+  unsigned long long* counters = (unsigned long long*)take(1024);
+  unsigned int* mm = (unsigned int*)(counters + 8);  // 64 mins, 64 maxima, radius min and max
+  (void)spare;
+  block_of_rank_kernel<<<grid_for(nb, 256, sms), 256, 0, s>>>(rank_of_block, nb, blk_of_rank);
+  block_bounds_kernel<<<grid_for(nb * 32, 256, sms), 256, 0, s>>>(base.Z64, n, d, base.rptr, centres,
+                                                                 blk_of_rank, nb, bcen, brad);
+  SBV_LAUNCH_CHECK(ctx, "block_bounds_kernel");
+  // extents of the block centres and the largest radius
+  std::vector<unsigned int> init(130);
+  for (int t = 0; t < 130; ++t) init[t] = (t < 64 || t == 128) ? 0xffffffffu : 0u;
+  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(mm, init.data(), 130 * 4, cudaMemcpyHostToDevice, s));
+  minmax_kernel<<<grid_for(nb * d, 256, sms), 256, 0, s>>>(bcen, nb, d, mm, mm + 64);
+  minmax_kernel<<<grid_for(nb, 256, sms), 256, 0, s>>>(brad, nb, 1, mm + 128, mm + 129);
+  SBV_LAUNCH_CHECK(ctx, "minmax_kernel");
+  std::vector<unsigned int> hm(130);
+  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(hm.data(), mm, 130 * 4, cudaMemcpyDeviceToHost, s));
+  SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  std::vector<double> lo(d), ext(d);
+  for (int t = 0; t < d; ++t) {
+    lo[t] = unmap_float(hm[t]);
+    ext[t] = std::max((double)unmap_float(hm[64 + t]) - lo[t], 1e-30);
+  }
+  const double rad_max = unmap_float(hm[129]);
+  int g0 = 0, g1 = d > 1 ? 1 : 0;
+  for (int t = 0; t < d; ++t)
+    if (ext[t] > ext[g0]) g0 = t;
+  if (d > 1) {
+    g1 = g0 == 0 ? 1 : 0;
+    for (int t = 0; t < d; ++t)
+      if (t != g0 && ext[t] > ext[g1]) g1 = t;
+  }
+  // density: points spread over the centres' box grown by the largest radius
+  double vol = 1.0;
+  for (int t = 0; t < d; ++t) vol *= ext[t] + 2.0 * rad_max;
+  const double vd = pow(M_PI, 0.5 * d) / tgamma(0.5 * d + 1.0);
+  const double vol_over_vd = vol / vd;
+  const double r_typ = pow(3.0 * m * vol_over_vd / std::max<double>(n / 2, 1), 1.0 / d);
+  double cell = r_typ + rad_max;
+  int nc0 = std::max(1, (int)ceil(ext[g0] / cell)), nc1 = std::max(1, (int)ceil(ext[g1] / cell));
+  while ((int64_t)nc0 * nc1 > (1 << 22)) {
+    cell *= 2.0;
+    nc0 = std::max(1, (int)ceil(ext[g0] / cell));
+    nc1 = std::max(1, (int)ceil(ext[g1] / cell));
+  }
+  const int ncell = nc0 * nc1;
+  cell_key_kernel<<<grid_for(nb, 256, sms), 256, 0, s>>>(bcen, nb, d, g0, g1, lo[g0], lo[g1], cell, nc0,
+                                                        nc1, keys);
+  iota_i32_kernel<<<grid_for(nb, 256, sms), 256, 0, s>>>(iota, nb);
+  SBV_LAUNCH_CHECK(ctx, "cell_key_kernel");
+  int32_t* cell_blk = (int32_t*)ws_get(ctx, WS_EXTRA, (size_t)nb * 4 + (size_t)(ncell + 1) * 8 * 2 + 1024, &st);
+  if (!cell_blk) return st;
+  int64_t* ccount = (int64_t*)(((uintptr_t)(cell_blk + nb) + 15) & ~(uintptr_t)15);
+  int64_t* cell_ptr = ccount + (ncell + 1);
+  {
+    int end_bit = 1;
+    while ((1ll << end_bit) < ncell) ++end_bit;
+    size_t tb = 0, tb2 = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, tb, keys, keys_sorted, iota, cell_blk, (int)nb, 0, end_bit, s);
+    cub::DeviceScan::ExclusiveSum(nullptr, tb2, ccount, cell_ptr, ncell + 1, s);
+    void* tmp = ws_get(ctx, WS_CUB, std::max(tb, tb2), &st);
+    if (!tmp) return st;
+    SBV_CUDA_TRY(ctx, cub::DeviceRadixSort::SortPairs(tmp, tb, keys, keys_sorted, iota, cell_blk, (int)nb,
+                                                      0, end_bit, s));
+    SBV_CUDA_TRY(ctx, cudaMemsetAsync(ccount, 0, (ncell + 1) * 8, s));
+    cell_count_kernel<<<grid_for(nb, 256, sms), 256, 0, s>>>(keys, nb, ccount);
+    SBV_LAUNCH_CHECK(ctx, "cell_count_kernel");
+    SBV_CUDA_TRY(ctx, cub::DeviceScan::ExclusiveSum(tmp, tb2, ccount, cell_ptr, ncell + 1, s));
+  }
+  // queries: short candidate prefixes go straight to the brute-force kernel
+  SBV_CUDA_TRY(ctx, cudaMemsetAsync(counters, 0, 8 * 8, s));
+  const int64_t small = (int64_t)64 * m;
+  split_queries_kernel<<<grid_for(nq, 256, sms), 256, 0, s>>>(base.qlimit_rank, base.rptr, nq, small,
+                                                              listA, counters, small_list, counters + 1);
+  SBV_LAUNCH_CHECK(ctx, "split_queries_kernel");
+  unsigned long long hc[2];
+  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(hc, counters, 16, cudaMemcpyDeviceToHost, s));
+  SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  int64_t nlist = (int64_t)hc[0], nsmall = (int64_t)hc[1];
+  int cap = 1;
+  while (cap < m + 96) cap <<= 1;
+  const size_t smem = (size_t)PK_WARPS * cap * 12;
+  if (smem > ctx->smem_optin) return fail(ctx, SBV_EUNSUPPORTED, "pruned kNN: m=%d too large", m);
+  PrunedArgs a;
+  a.Z32 = base.Z32;
+  a.Z64 = base.Z64;
+  a.cid = base.cid;
+  a.n = n;
+  a.d = d;
+  a.rptr = base.rptr;
+  a.bcen = bcen;
+  a.brad = brad;
+  a.rad_max = (float)rad_max;
+  double zmax = 0.0;
+  for (int t = 0; t < d; ++t) zmax = std::max(zmax, std::max(fabs(lo[t]), fabs(lo[t] + ext[t])));
+  a.slack = (float)(1e-5 * (zmax + rad_max + 1.0) * d);
+  a.g0 = g0;
+  a.g1 = g1;
+  a.gmin0 = lo[g0];
+  a.gmin1 = lo[g1];
+  a.cell = cell;
+  a.nc0 = nc0;
+  a.nc1 = nc1;
+  a.cell_ptr = cell_ptr;
+  a.cell_blk = cell_blk;
+  a.Q = base.Q;
+  a.qlimit_rank = base.qlimit_rank;
+  a.qR = qR;
+  a.m = m;
+  a.cap = cap;
+  a.sb = base.sb;
+  a.nbr = base.nbr;
+  a.cnt = base.cnt;
+  int64_t* cur = listA;
+  int64_t* nxt = listB;
+  for (int attempt = 0; attempt < 3 && nlist > 0; ++attempt) {
+    radius_kernel<<<grid_for(nlist, 256, sms), 256, 0, s>>>(cur, nlist, base.qlimit_rank, base.rptr, n,
+                                                           vol_over_vd, m, d, (double)(1 << attempt), qR);
+    SBV_CUDA_TRY(ctx, cudaMemsetAsync(counters + 2, 0, 8, s));
+    a.qlist = cur;
+    a.nlist = nlist;
+    a.failed = nxt;
+    a.nfailed = counters + 2;
+    const unsigned grid = (unsigned)((nlist + PK_WARPS - 1) / PK_WARPS);
+#define SBV_PK(DM)                                                                                   \
+  do {                                                                                               \
+    SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(knn_pruned_kernel<DM>,                                    \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    knn_pruned_kernel<DM><<<grid, PK_WARPS * 32, smem, s>>>(a);                                      \
+  } while (0)
+    if (d <= 4) SBV_PK(4);
+    else if (d <= 8) SBV_PK(8);
+    else if (d <= 12) SBV_PK(12);
+    else if (d <= 16) SBV_PK(16);
+    else if (d <= 24) SBV_PK(24);
+    else if (d <= 32) SBV_PK(32);
+    else SBV_PK(64);
+#undef SBV_PK
+    SBV_LAUNCH_CHECK(ctx, "knn_pruned_kernel");
+    unsigned long long hf = 0;
+    SBV_CUDA_TRY(ctx, cudaMemcpyAsync(&hf, counters + 2, 8, cudaMemcpyDeviceToHost, s));
+    SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    nlist = (int64_t)hf;
+    std::swap(cur, nxt);
+  }
+  // brute force: short prefixes and queries that failed every attempt
+  const int64_t nbrute = nsmall + nlist;
+  if (nbrute > 0) {
+    if (nsmall > 0)
+      i64_to_i32_kernel<<<grid_for(nsmall, 256, sms), 256, 0, s>>>(small_list, nsmall, brute);
+    if (nlist > 0)
+      i64_to_i32_kernel<<<grid_for(nlist, 256, sms), 256, 0, s>>>(cur, nlist, brute + nsmall);
+    SBV_LAUNCH_CHECK(ctx, "i64_to_i32_kernel");
+    KnnArgs b = base;
+    b.qorder = brute;
+    b.nq = nbrute;
+    if ((st = launch_knn(ctx, b, s))) return st;
+  }
+  SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
   return SBV_OK;
 }
 
@@ -351,6 +824,10 @@ int run_knn(sbv_ctx* ctx, const double* Z, int64_t n, int d, const int64_t* ptr,
   a.sb = make_screen(M > Mc ? M : Mc, d);
   a.nbr = nbr;
   a.cnt = cnt;
+  // brute force scans sum_r rptr[r] ~ n bc / 2 candidates; above ~1e11 the
+  // pruned search is used (or as the context's mode says)
+  const bool pruned = ctx->knn_mode == 2 || (ctx->knn_mode == 0 && (double)n * (double)bc > 2e11);
+  if (pruned) return knn_pruned(ctx, a, rank, bc, centres, s);
   if ((st = launch_knn(ctx, a, s))) return st;
   SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
   return SBV_OK;

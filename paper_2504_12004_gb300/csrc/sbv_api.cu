@@ -134,23 +134,41 @@ static int check_theta(sbv_ctx* ctx, const double* theta, int B, int d) {
 
 static bool nu_ok(int nu2) { return nu2 == 1 || nu2 == 3 || nu2 == 5 || nu2 == 7; }
 
-extern "C" int sbv_blocking(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_t d,
-                            const double* beta_scale, int64_t bc, int32_t kmeans_iters,
-                            uint64_t seed, int32_t* blk, int64_t* ptr, int32_t* pts,
-                            int32_t* rank, double* centres, int64_t* bc_eff, void* stream) {
+extern "C" int sbv_blocking_partitioned(sbv_ctx* ctx, const void* X, int dtype, int64_t n,
+                                        int32_t d, const double* beta_scale, int64_t bc,
+                                        int32_t kmeans_iters, uint64_t seed, int32_t partitions,
+                                        int32_t* blk, int64_t* ptr, int32_t* pts, int32_t* rank,
+                                        double* centres, int64_t* bc_eff, void* stream) {
   int st = check_common(ctx, X, dtype, n, d);
   if (st) return st;
   if ((st = check_beta(ctx, beta_scale, d, "beta_scale"))) return st;
   if (bc < 1 || bc > n) return fail(ctx, SBV_EINVAL, "bc=%lld outside [1, n]", (long long)bc);
   if (kmeans_iters < 0) return fail(ctx, SBV_EINVAL, "kmeans_iters must be >= 0");
+  if (partitions < 1 || (int64_t)partitions > bc)
+    return fail(ctx, SBV_EINVAL, "partitions=%d outside [1, bc]", partitions);
   if (!blk || !ptr || !pts || !rank || !centres || !bc_eff)
     return fail(ctx, SBV_EINVAL, "null output pointer");
   cudaStream_t s = (cudaStream_t)stream;
   double* Z = (double*)ws_get(ctx, WS_Z, (size_t)n * d * sizeof(double), &st);
   if (!Z) return st;
   if ((st = scale_points(ctx, X, dtype, n, d, nullptr, beta_scale, Z, s))) return st;
-  return run_blocking(ctx, Z, n, d, bc, kmeans_iters, seed, blk, ptr, pts, rank, centres,
-                      bc_eff, s);
+  return run_blocking(ctx, Z, X, dtype, beta_scale, n, d, bc, kmeans_iters, seed, partitions, blk,
+                      ptr, pts, rank, centres, bc_eff, s);
+}
+
+extern "C" int sbv_blocking(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_t d,
+                            const double* beta_scale, int64_t bc, int32_t kmeans_iters,
+                            uint64_t seed, int32_t* blk, int64_t* ptr, int32_t* pts,
+                            int32_t* rank, double* centres, int64_t* bc_eff, void* stream) {
+  return sbv_blocking_partitioned(ctx, X, dtype, n, d, beta_scale, bc, kmeans_iters, seed, 1,
+                                  blk, ptr, pts, rank, centres, bc_eff, stream);
+}
+
+extern "C" int sbv_set_knn_mode(sbv_ctx* ctx, int32_t mode) {
+  if (!ctx) return SBV_EINVAL;
+  if (mode < 0 || mode > 2) return fail(ctx, SBV_EINVAL, "knn mode %d not in {0, 1, 2}", mode);
+  ctx->knn_mode = mode;
+  return SBV_OK;
 }
 
 extern "C" int sbv_knn(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_t d,

@@ -48,6 +48,7 @@ struct sbv_ctx {
   sbv::DevBuf ws[16];                  // named workspace slots
   sbv::LaunchShape force;              // set while the autotuner times a shape
   std::vector<sbv::TunedShape> tuned;  // autotuning records
+  int knn_mode = 0;                    // 0 automatic, 1 brute force, 2 pruned search
   // pinned host ring for parameter rows: slot k is reused only after the
   // event recorded behind its previous copy has completed
   static const int kRing = 8;
@@ -99,10 +100,10 @@ void* ws_get(sbv_ctx* ctx, int slot, size_t bytes, int* status);
 int scale_points(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int d,
                  const double* d_inv_unused, const double* h_beta, double* Z,
                  cudaStream_t s);
-int run_blocking(sbv_ctx* ctx, const double* Z, int64_t n, int d, int64_t bc,
-                 int kmeans_iters, uint64_t seed, int32_t* blk, int64_t* ptr,
-                 int32_t* pts, int32_t* rank, double* centres, int64_t* bc_eff,
-                 cudaStream_t s);
+int run_blocking(sbv_ctx* ctx, const double* Z, const void* X, int dtype, const double* h_beta,
+                 int64_t n, int d, int64_t bc, int kmeans_iters, uint64_t seed, int partitions,
+                 int32_t* blk, int64_t* ptr, int32_t* pts, int32_t* rank, double* centres,
+                 int64_t* bc_eff, cudaStream_t s);
 // kNN
 int run_knn(sbv_ctx* ctx, const double* Z, int64_t n, int d, const int64_t* ptr,
             const int32_t* pts, const int32_t* rank, const double* centres,

@@ -96,6 +96,16 @@ def test_blocking_float32_points(ctx):
     check_blocking_equal(got, sbv.blocking(X, beta, 150, 6, 5))
 
 
+@pytest.mark.parametrize("n,d,bc,T,P,f32", [(3000, 4, 120, 3, 4, False), (2500, 6, 97, 0, 7, False),
+                                             (2000, 3, 64, 20, 3, True), (1500, 5, 40, 2, 40, False)])
+def test_partitioned_blocking_bit_exact(ctx, n, d, bc, T, P, f32):
+    # slabs along the most relevant dimension (Alg. 2), RAC + Lloyd per slab
+    X = uniform_points(n, d, 60 + P, np.float32 if f32 else np.float64)
+    beta = np.linspace(0.9, 0.2, d)
+    got = ctx.sbv_blocking(cuda(X), beta, bc, T, 17, partitions=P)
+    check_blocking_equal(got, sbv.blocking(X, beta, bc, T, 17, partitions=P))
+
+
 def test_blocking_with_duplicate_points(ctx):
     # many exactly equal points and ties in distance: smaller block index wins everywhere
     rng = np.random.default_rng(3)
@@ -129,6 +139,26 @@ def test_knn_m_edges(ctx, m):
     assert np.array_equal(np_(cnt), oc)
     if m:
         assert np.array_equal(np_(nbr), on)
+
+
+@pytest.mark.parametrize("n,d,bc,m,P", [(20000, 4, 400, 30, 1), (30000, 10, 600, 120, 6),
+                                         (12000, 3, 1500, 60, 1)])
+def test_knn_pruned_equals_full_scan(ctx, n, d, bc, m, P):
+    # the pruned search (block bounds, grid over centres, radius check with
+    # retries) returns the full scan's neighbours key for key
+    X = uniform_points(n, d, 70 + d)
+    beta = np.linspace(0.15, 1.0, d)
+    b = ctx.sbv_blocking(cuda(X), beta, bc, 2, 5, partitions=P)
+    args = (cuda(X), beta, b["ptr"], b["pts"], b["rank"], b["centres"], m)
+    ctx.sbv_set_knn_mode(1)
+    nb1, c1 = ctx.sbv_knn(*args)
+    ctx.sbv_set_knn_mode(2)
+    try:
+        nb2, c2 = ctx.sbv_knn(*args)
+    finally:
+        ctx.sbv_set_knn_mode(0)
+    assert torch.equal(c1, c2)
+    assert torch.equal(nb1, nb2)
 
 
 def test_knn_ties(ctx):
