@@ -246,6 +246,22 @@ int sbv_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y,
                 double* var_latent, int32_t* nbr, void* stream);
 
 /*
+ * sbv_predict_blocks -- sbv_predict with the neighbour search over the
+ * training blocks (ptr, pts, rank, centres: device, bc blocks, as returned by
+ * sbv_blocking or sbv_blocking_partitioned on the same X and beta_scale).
+ * The blocks only prune the search (see sbv_set_knn_mode): the neighbours,
+ * and therefore every output, equal those of sbv_predict.  Intended for large
+ * n, where scanning all training points for every test point is too slow.
+ * Errors: as sbv_predict, SBV_EINVAL for an incomplete block structure.
+ */
+int sbv_predict_blocks(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n,
+                       int32_t d, const void* Xtest, int64_t ntest, const double* beta_scale,
+                       int32_t m_pred, const double* theta, int32_t nu2, int32_t precision,
+                       const int64_t* ptr, const int32_t* pts, const int32_t* rank,
+                       const double* centres, int64_t bc, double* mean, double* var,
+                       double* var_latent, int32_t* nbr, void* stream);
+
+/*
  * Captured evaluation (Sec. 5.4: all blocks of an evaluation in one batched
  * launch).  sbv_loglik_graph_create records one evaluation of sbv_loglik --
  * work-counter reset, the persistent block kernel over every (theta, block)

@@ -78,6 +78,8 @@ SIGNATURES = {
     "sbv_set_knn_mode": (C.c_int, [_P, _I32]),
     "sbv_predict": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _I64, _P, _I32, _P,
                               _I32, _I32, _P, _P, _P, _P, _P]),
+    "sbv_predict_blocks": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _I64, _P, _I32, _P,
+                                     _I32, _I32, _P, _P, _P, _P, _I64, _P, _P, _P, _P, _P]),
     "sbv_loglik_fp64_noalloc": (C.c_int, [_P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64,
                                           _I32, _I32, _P, _I32, _I32, _P, _P, _P, _P]),
     "sbv_loglik_graph_create": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64,
@@ -342,7 +344,9 @@ class Context:
         self._check(self.lib.sbv_sync_status(self.h, _stream(stream)))
 
     def sbv_predict(self, X, y, Xtest, beta_scale, m_pred: int, theta, nu2: int = 5,
-                    precision="fp64", want_nbr=False, stream=None):
+                    precision="fp64", want_nbr=False, stream=None, blocks=None):
+        """Predictive mean and variances; `blocks` (a dict from sbv_blocking on the
+        same X) switches the neighbour search to sbv_predict_blocks."""
         X = _dev(X, None, "X")
         Xtest = _dev(Xtest, X.dtype, "Xtest")
         n, d = X.shape
@@ -355,9 +359,18 @@ class Context:
         var_lat = torch.empty(nt, dtype=torch.float64, device=dev)
         nbr = torch.empty(nt, m_pred, dtype=torch.int32, device=dev) if want_nbr else None
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        rc = self.lib.sbv_predict(self.h, _ptr(X), _xdtype(X), _ptr(_dev(y, torch.float64, "y")), n, d,
-                                  _ptr(Xtest), nt, _ptr(beta), m_pred, _ptr(th), nu2, prec,
-                                  _ptr(mean), _ptr(var), _ptr(var_lat), _ptr(nbr), _stream(stream))
+        if blocks is None:
+            rc = self.lib.sbv_predict(self.h, _ptr(X), _xdtype(X), _ptr(_dev(y, torch.float64, "y")),
+                                      n, d, _ptr(Xtest), nt, _ptr(beta), m_pred, _ptr(th), nu2, prec,
+                                      _ptr(mean), _ptr(var), _ptr(var_lat), _ptr(nbr), _stream(stream))
+        else:
+            b = blocks
+            rc = self.lib.sbv_predict_blocks(
+                self.h, _ptr(X), _xdtype(X), _ptr(_dev(y, torch.float64, "y")), n, d, _ptr(Xtest), nt,
+                _ptr(beta), m_pred, _ptr(th), nu2, prec, _ptr(_dev(b["ptr"], torch.int64, "ptr")),
+                _ptr(_dev(b["pts"], torch.int32, "pts")), _ptr(_dev(b["rank"], torch.int32, "rank")),
+                _ptr(_dev(b["centres"], torch.float64, "centres")), b["rank"].numel(), _ptr(mean),
+                _ptr(var), _ptr(var_lat), _ptr(nbr), _stream(stream))
         self._check(rc)
         return mean, var, var_lat, nbr
 

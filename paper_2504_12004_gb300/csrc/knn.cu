@@ -255,11 +255,11 @@ __global__ void rank_sorted_blocks_kernel(const int32_t* __restrict__ rank, int6
 
 // ---------------------------------------------------------------------------
 // Pruned exact search for large inputs.  The candidates are grouped in
-// blocks (the Vecchia blocks, listed by rank) with a centre c_b and a radius
-// rho_b >= max over members |x - c_b|; a 2-D grid over the two longest
-// scaled dimensions indexes the block centres.  A query with search radius R
-// scans only the blocks with |q - c_b| <= R + rho_b (the grid window has
-// half-width R + max rho); every other candidate lies farther than R.  If
+// blocks (the Vecchia blocks, listed by rank) with a centre and a bounding
+// box; a 2-D grid over the two longest scaled dimensions indexes the block
+// centres.  A query with search radius R scans only the blocks whose box lies
+// within R of it (the grid window has half-width R plus the largest box
+// half-extent); every other candidate lies farther than R.  If
 // the m-th smallest key found has D < R^2 (1 - 1e-9), no skipped candidate
 // can enter the m nearest, and the result equals the brute-force one key for
 // key.  Queries that fail this test are retried with a larger R and finally
@@ -276,8 +276,9 @@ struct PrunedArgs {
   int d;
   const int64_t* rptr;     // block of rank r: candidates [rptr[r], rptr[r+1])
   const float* bcen;       // block centres by rank, nb x d
-  const float* brad;       // block radii by rank (rounded up)
-  float rad_max;
+  const float* blo;        // block bounding boxes by rank, nb x d (rounded outwards)
+  const float* bhi;
+  float rad_max;           // largest half-extent of a box in the grid dimensions
   float slack;             // absolute slack of the float32 centre tests
   int g0, g1;              // grid dimensions
   double gmin0, gmin1, cell;
@@ -365,15 +366,17 @@ __global__ void __launch_bounds__(PK_WARPS * 32) knn_pruned_kernel(PrunedArgs a)
         bool ok = idx < ce && (int64_t)b < nb_lim;
         const bool past = __any_sync(0xffffffffu, idx < ce && (int64_t)b >= nb_lim);
         if (ok) {
+          // distance from the query to the block's bounding box
           float acc = 0.0f;
 #pragma unroll
           for (int t = 0; t < DM; ++t) {
             if (t < a.d) {
-              const float df = qf[t] - a.bcen[(int64_t)b * a.d + t];
+              const float l = a.blo[(int64_t)b * a.d + t], h = a.bhi[(int64_t)b * a.d + t];
+              const float df = fmaxf(fmaxf(l - qf[t], qf[t] - h), 0.0f);
               acc = fmaf(df, df, acc);
             }
           }
-          ok = sqrtf(acc) <= R + a.brad[b] + a.slack;
+          ok = sqrtf(acc) <= R + a.slack;
         }
         unsigned mask = __ballot_sync(0xffffffffu, ok);
         while (mask) {
@@ -428,24 +431,39 @@ __global__ void __launch_bounds__(PK_WARPS * 32) knn_pruned_kernel(PrunedArgs a)
   }
 }
 
-// Centre (float32) and radius (max member distance, rounded up, float32) of
-// the block of every rank; one warp per block.
+// Centre and bounding box (float32, rounded outwards) of the block of every
+// rank, and the largest box half-extent over the grid candidates; one warp
+// per block.
 __global__ void block_bounds_kernel(const double* __restrict__ Z64, int64_t n, int d,
                                     const int64_t* __restrict__ rptr,
                                     const double* __restrict__ centres,
                                     const int32_t* __restrict__ blk_of_rank, int64_t nb,
-                                    float* __restrict__ bcen, float* __restrict__ brad) {
+                                    float* __restrict__ bcen, float* __restrict__ blo,
+                                    float* __restrict__ bhi, float* __restrict__ bhalf) {
   int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   for (; w < nb; w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const double* c = centres + (int64_t)blk_of_rank[w] * d;
-    double mx = 0.0;
-    for (int64_t p = rptr[w] + lane; p < rptr[w + 1]; p += 32)
-      mx = fmax(mx, dist2_exact_strided(Z64 + p, (size_t)n, c, d));
-    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane < d) bcen[w * d + lane] = (float)c[lane];
-    for (int t = 32 + lane; t < d; t += 32) bcen[w * d + t] = (float)c[t];
-    if (lane == 0) brad[w] = __double2float_ru(sqrt(mx) * (1.0 + 1e-6));
+    float half = 0.0f;
+    for (int t = 0; t < d; ++t) {
+      double lo = INFINITY, hi = -INFINITY;
+      for (int64_t p = rptr[w] + lane; p < rptr[w + 1]; p += 32) {
+        const double v = Z64[(size_t)t * n + p];
+        lo = fmin(lo, v);
+        hi = fmax(hi, v);
+      }
+      for (int o = 16; o; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      }
+      if (lane == 0) {
+        blo[w * d + t] = __double2float_rd(lo);
+        bhi[w * d + t] = __double2float_ru(hi);
+        bcen[w * d + t] = (float)c[t];
+        half = fmaxf(half, __double2float_ru(fmax(c[t] - lo, hi - c[t])));
+      }
+    }
+    if (lane == 0) bhalf[w] = half;
   }
 }
 
@@ -558,13 +576,14 @@ static int launch_knn(sbv_ctx* ctx, KnnArgs& a, cudaStream_t s) {
 }
 
 __global__ void split_queries_kernel(const int32_t* __restrict__ qlimit_rank,
-                                     const int64_t* __restrict__ rptr, int64_t nq, int64_t small,
-                                     int64_t* __restrict__ big_list, unsigned long long* __restrict__ nbig,
+                                     const int64_t* __restrict__ rptr, int64_t n, int64_t nq,
+                                     int64_t small, int64_t* __restrict__ big_list,
+                                     unsigned long long* __restrict__ nbig,
                                      int64_t* __restrict__ small_list,
                                      unsigned long long* __restrict__ nsmall) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
        q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t ne = rptr[qlimit_rank[q]];
+    const int64_t ne = qlimit_rank ? rptr[qlimit_rank[q]] : n;
     if (ne > small) big_list[atomicAdd(nbig, 1ull)] = q;
     else small_list[atomicAdd(nsmall, 1ull)] = q;
   }
@@ -586,7 +605,7 @@ static int knn_pruned(sbv_ctx* ctx, KnnArgs base, const int32_t* rank_of_block, 
   const int64_t n = base.n, nq = base.nq;
   const int d = base.d, m = base.m;
   const int sms = ctx->num_sms;
-  size_t bytes = (size_t)nb * 4 + (size_t)nb * d * 4 + (size_t)nb * 4 + (size_t)nb * 4 * 3 +
+  size_t bytes = (size_t)nb * 4 + (size_t)nb * d * 4 * 3 + (size_t)nb * 4 + (size_t)nb * 4 * 3 +
                  (size_t)(nq + 8) * 8 * 4 + (size_t)nq * 4 * 2 + 4096 + (size_t)64 * 8;
   char* wp = (char*)ws_get(ctx, WS_SORT_D, bytes, &st);
   if (!wp) return st;
@@ -597,7 +616,9 @@ static int knn_pruned(sbv_ctx* ctx, KnnArgs base, const int32_t* rank_of_block, 
   };
   int32_t* blk_of_rank = (int32_t*)take((size_t)nb * 4);
   float* bcen = (float*)take((size_t)nb * d * 4);
-  float* brad = (float*)take((size_t)nb * 4);
+  float* blo = (float*)take((size_t)nb * d * 4);
+  float* bhi = (float*)take((size_t)nb * d * 4);
+  float* brad = (float*)take((size_t)nb * 4);   // largest half-extent of each box
   int32_t* keys = (int32_t*)take((size_t)nb * 4);
   int32_t* keys_sorted = (int32_t*)take((size_t)nb * 4);
   int32_t* iota = (int32_t*)take((size_t)nb * 4);
@@ -612,7 +633,7 @@ static int knn_pruned(sbv_ctx* ctx, KnnArgs base, const int32_t* rank_of_block, 
   (void)spare;
   block_of_rank_kernel<<<grid_for(nb, 256, sms), 256, 0, s>>>(rank_of_block, nb, blk_of_rank);
   block_bounds_kernel<<<grid_for(nb * 32, 256, sms), 256, 0, s>>>(base.Z64, n, d, base.rptr, centres,
-                                                                 blk_of_rank, nb, bcen, brad);
+                                                                 blk_of_rank, nb, bcen, blo, bhi, brad);
   SBV_LAUNCH_CHECK(ctx, "block_bounds_kernel");
   // extents of the block centres and the largest radius
   std::vector<unsigned int> init(130);
@@ -678,7 +699,7 @@ static int knn_pruned(sbv_ctx* ctx, KnnArgs base, const int32_t* rank_of_block, 
   // queries: short candidate prefixes go straight to the brute-force kernel
   SBV_CUDA_TRY(ctx, cudaMemsetAsync(counters, 0, 8 * 8, s));
   const int64_t small = (int64_t)64 * m;
-  split_queries_kernel<<<grid_for(nq, 256, sms), 256, 0, s>>>(base.qlimit_rank, base.rptr, nq, small,
+  split_queries_kernel<<<grid_for(nq, 256, sms), 256, 0, s>>>(base.qlimit_rank, base.rptr, n, nq, small,
                                                               listA, counters, small_list, counters + 1);
   SBV_LAUNCH_CHECK(ctx, "split_queries_kernel");
   unsigned long long hc[2];
@@ -697,7 +718,8 @@ static int knn_pruned(sbv_ctx* ctx, KnnArgs base, const int32_t* rank_of_block, 
   a.d = d;
   a.rptr = base.rptr;
   a.bcen = bcen;
-  a.brad = brad;
+  a.blo = blo;
+  a.bhi = bhi;
   a.rad_max = (float)rad_max;
   double zmax = 0.0;
   for (int t = 0; t < d; ++t) zmax = std::max(zmax, std::max(fabs(lo[t]), fabs(lo[t] + ext[t])));
@@ -762,6 +784,7 @@ static int knn_pruned(sbv_ctx* ctx, KnnArgs base, const int32_t* rank_of_block, 
     KnnArgs b = base;
     b.qorder = brute;
     b.nq = nbrute;
+    if (!base.qlimit_rank) b.rptr = nullptr;   // all-points mode: every candidate
     if ((st = launch_knn(ctx, b, s))) return st;
   }
   SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
@@ -831,6 +854,56 @@ int run_knn(sbv_ctx* ctx, const double* Z, int64_t n, int d, const int64_t* ptr,
   if ((st = launch_knn(ctx, a, s))) return st;
   SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
   return SBV_OK;
+}
+
+// m nearest training points of every query over all n points, using the
+// training blocks (ptr, pts, rank, centres) as the clusters of the pruned
+// search; the result equals run_knn_all key for key.
+int run_knn_blocks_all(sbv_ctx* ctx, const double* Z, int64_t n, int d, const int64_t* ptr,
+                       const int32_t* pts, const int32_t* rank, const double* centres,
+                       int64_t bc, const double* Q, int64_t nq, int m, int32_t* nbr,
+                       cudaStream_t s) {
+  int st = 0;
+  char* w = (char*)ws_get(ctx, WS_ORDER,
+                          (size_t)n * d * (8 + 4) + (size_t)n * 4 + (size_t)(bc + 1) * 16 + 4096, &st);
+  if (!w) return st;
+  double* Z64 = (double*)w;
+  float* Z32 = (float*)(Z64 + (size_t)n * d);
+  int32_t* rorder = (int32_t*)(Z32 + (size_t)n * d);
+  int64_t* rcount = (int64_t*)(((uintptr_t)(rorder + n) + 15) & ~(uintptr_t)15);
+  int64_t* rptr = rcount + (bc + 1);
+  SBV_CUDA_TRY(ctx, cudaMemsetAsync(rcount, 0, (bc + 1) * sizeof(int64_t), s));
+  rank_counts_kernel<<<grid_for(bc, 256, ctx->num_sms), 256, 0, s>>>(ptr, rank, bc, rcount);
+  SBV_LAUNCH_CHECK(ctx, "rank_counts_kernel");
+  size_t tb = 0;
+  cub::DeviceScan::ExclusiveSum(nullptr, tb, rcount, rptr, (int)(bc + 1), s);
+  void* tmp = ws_get(ctx, WS_CUB, tb, &st);
+  if (!tmp) return st;
+  SBV_CUDA_TRY(ctx, cub::DeviceScan::ExclusiveSum(tmp, tb, rcount, rptr, (int)(bc + 1), s));
+  rank_scatter_kernel<<<grid_for(bc * 32, 256, ctx->num_sms), 256, 0, s>>>(ptr, pts, rank, rptr, bc,
+                                                                           rorder);
+  SBV_LAUNCH_CHECK(ctx, "rank_scatter_kernel");
+  soa_kernel<<<grid_for(n * d, 256, ctx->num_sms), 256, 0, s>>>(Z, rorder, n, d, Z64, Z32);
+  SBV_LAUNCH_CHECK(ctx, "soa_kernel");
+  double M = 0.0, Mq = 0.0;
+  if ((st = absmax(ctx, Z, n * d, &M, s))) return st;
+  if ((st = absmax(ctx, Q, nq * d, &Mq, s))) return st;
+  KnnArgs a;
+  a.Z32 = Z32;
+  a.Z64 = Z64;
+  a.cid = rorder;
+  a.n = n;
+  a.d = d;
+  a.Q = Q;
+  a.nq = nq;
+  a.qlimit_rank = nullptr;
+  a.rptr = rptr;
+  a.qorder = nullptr;
+  a.m = m;
+  a.sb = make_screen(M > Mq ? M : Mq, d);
+  a.nbr = nbr;
+  a.cnt = nullptr;
+  return knn_pruned(ctx, a, rank, bc, centres, s);
 }
 
 int run_knn_all(sbv_ctx* ctx, const double* Z, int64_t n, int d, const double* Q, int64_t nq,

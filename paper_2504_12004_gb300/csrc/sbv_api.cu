@@ -230,11 +230,12 @@ extern "C" int sbv_sync_status(sbv_ctx* ctx, void* stream) {
   return SBV_OK;
 }
 
-extern "C" int sbv_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y,
-                           int64_t n, int32_t d, const void* Xtest, int64_t ntest,
-                           const double* beta_scale, int32_t m_pred, const double* theta,
-                           int32_t nu2, int32_t precision, double* mean, double* var,
-                           double* var_latent, int32_t* nbr, void* stream) {
+static int predict_common(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n,
+                          int32_t d, const void* Xtest, int64_t ntest, const double* beta_scale,
+                          int32_t m_pred, const double* theta, int32_t nu2, int32_t precision,
+                          const int64_t* ptr, const int32_t* pts, const int32_t* rank,
+                          const double* centres, int64_t bc, double* mean, double* var,
+                          double* var_latent, int32_t* nbr, void* stream) {
   int st = check_common(ctx, X, dtype, n, d);
   if (st) return st;
   if (!y || !Xtest || !mean || !var || !var_latent)
@@ -249,6 +250,8 @@ extern "C" int sbv_predict(sbv_ctx* ctx, const void* X, int dtype, const double*
   if (precision != SBV_PREC_FP64 && precision != SBV_PREC_MIXED &&
       precision != SBV_PREC_MIXED_BF16)
     return fail(ctx, SBV_EINVAL, "precision=%d unknown", precision);
+  if (ptr && (!pts || !rank || !centres || bc < 1 || bc > n))
+    return fail(ctx, SBV_EINVAL, "incomplete block structure");
   cudaStream_t s = (cudaStream_t)stream;
   size_t zbytes = (size_t)(n + ntest) * d * sizeof(double);
   double* Z = (double*)ws_get(ctx, WS_Z, zbytes, &st);
@@ -258,13 +261,39 @@ extern "C" int sbv_predict(sbv_ctx* ctx, const void* X, int dtype, const double*
   if ((st = scale_points(ctx, Xtest, dtype, ntest, d, nullptr, beta_scale, Zt, s))) return st;
   int32_t* knbr = nbr;
   if (!knbr) {
-    knbr = (int32_t*)ws_get(ctx, WS_EXTRA, (size_t)ntest * m_pred * sizeof(int32_t), &st);
+    knbr = (int32_t*)ws_get(ctx, WS_PRED, (size_t)ntest * m_pred * sizeof(int32_t), &st);
     if (!knbr) return st;
   }
-  if ((st = run_knn_all(ctx, Z, n, d, Zt, ntest, m_pred, knbr, s))) return st;
+  if (ptr)
+    st = run_knn_blocks_all(ctx, Z, n, d, ptr, pts, rank, centres, bc, Zt, ntest, m_pred, knbr, s);
+  else
+    st = run_knn_all(ctx, Z, n, d, Zt, ntest, m_pred, knbr, s);
+  if (st) return st;
   if ((st = run_predict(ctx, X, dtype, y, n, d, Xtest, ntest, knbr, m_pred, theta, nu2,
                         precision, mean, var, var_latent, s)))
     return st;
   SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
   return sbv_sync_status(ctx, stream);
+}
+
+extern "C" int sbv_predict_blocks(sbv_ctx* ctx, const void* X, int dtype, const double* y,
+                                  int64_t n, int32_t d, const void* Xtest, int64_t ntest,
+                                  const double* beta_scale, int32_t m_pred, const double* theta,
+                                  int32_t nu2, int32_t precision, const int64_t* ptr,
+                                  const int32_t* pts, const int32_t* rank, const double* centres,
+                                  int64_t bc, double* mean, double* var, double* var_latent,
+                                  int32_t* nbr, void* stream) {
+  if (ctx && !ptr) return fail(ctx, SBV_EINVAL, "ptr is null");
+  return predict_common(ctx, X, dtype, y, n, d, Xtest, ntest, beta_scale, m_pred, theta, nu2,
+                        precision, ptr, pts, rank, centres, bc, mean, var, var_latent, nbr, stream);
+}
+
+extern "C" int sbv_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y,
+                           int64_t n, int32_t d, const void* Xtest, int64_t ntest,
+                           const double* beta_scale, int32_t m_pred, const double* theta,
+                           int32_t nu2, int32_t precision, double* mean, double* var,
+                           double* var_latent, int32_t* nbr, void* stream) {
+  return predict_common(ctx, X, dtype, y, n, d, Xtest, ntest, beta_scale, m_pred, theta, nu2,
+                        precision, nullptr, nullptr, nullptr, nullptr, 0, mean, var, var_latent,
+                        nbr, stream);
 }

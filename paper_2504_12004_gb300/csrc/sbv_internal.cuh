@@ -76,6 +76,7 @@ enum WsSlot {
   WS_EXTRA,
   WS_XSPLIT,      // points split into float pairs for the mixed path
   WS_TUNE,        // results of the autotuner's timing runs
+  WS_PRED,        // prediction neighbour lists when the caller passes NULL
   WS_COUNT
 };
 
@@ -110,6 +111,10 @@ int run_knn(sbv_ctx* ctx, const double* Z, int64_t n, int d, const int64_t* ptr,
             int64_t bc, int m, int32_t* nbr, int32_t* cnt, cudaStream_t s);
 int run_knn_all(sbv_ctx* ctx, const double* Z, int64_t n, int d,
                 const double* Q, int64_t nq, int m, int32_t* nbr, cudaStream_t s);
+int run_knn_blocks_all(sbv_ctx* ctx, const double* Z, int64_t n, int d, const int64_t* ptr,
+                       const int32_t* pts, const int32_t* rank, const double* centres,
+                       int64_t bc, const double* Q, int64_t nq, int m, int32_t* nbr,
+                       cudaStream_t s);
 // likelihood and prediction
 int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n,
                int d, const int64_t* ptr, const int32_t* pts, const int32_t* nbr,

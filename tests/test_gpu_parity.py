@@ -161,6 +161,23 @@ def test_knn_pruned_equals_full_scan(ctx, n, d, bc, m, P):
     assert torch.equal(nb1, nb2)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_predict_blocks_equals_predict(ctx, precision):
+    # the pruned neighbour search over training blocks gives the same
+    # neighbours, hence bit-identical predictions
+    X = uniform_points(30000, 6, 81)
+    Xt = uniform_points(700, 6, 82)
+    y = standard_normal(30000, 83)
+    beta = np.linspace(0.2, 1.0, 6)
+    th = np.r_[1.0, 0.01, beta]
+    b = ctx.sbv_blocking(cuda(X), beta, 600, 1, 3)
+    a = ctx.sbv_predict(cuda(X), cuda(y), cuda(Xt), beta, 80, th, 5, precision, want_nbr=True)
+    c = ctx.sbv_predict(cuda(X), cuda(y), cuda(Xt), beta, 80, th, 5, precision, want_nbr=True,
+                        blocks=b)
+    for u, v in zip(a, c):
+        assert torch.equal(u, v)
+
+
 def test_knn_ties(ctx):
     rng = np.random.default_rng(11)
     X = rng.integers(0, 3, size=(400, 3)).astype(np.float64)
