@@ -355,12 +355,19 @@ def predict(X, y, Xtest, beta_scale, m_pred: int, theta, nu2: int, rows=None):
     for i, j in enumerate(rows):
         J = knn_block(Z, Zt[j], allidx, m_pred)
         nbr[i, :J.size] = J
-        xt = np.asarray(Xtest[j:j + 1], dtype=np.float64)
-        S_con = cov_points(Xd, J, J, theta, nu2)
-        S_cross = cov(Xd[J], xt, theta, nu2)                     # distinct points: no nugget
-        L = np.linalg.cholesky(S_con)
-        S_cross_p = solve_triangular(L, S_cross, lower=True)
-        yJ_p = solve_triangular(L, y[J], lower=True)
-        mean[i] = float(S_cross_p[:, 0] @ yJ_p)
-        var[i] = s2 + t2 - float(S_cross_p[:, 0] @ S_cross_p[:, 0])
+        mean[i], var[i] = predict_given(Xd, y, Xtest[j:j + 1], J, theta, nu2)
     return mean, var, var - t2, nbr
+
+
+def predict_given(Xd, y, xt, J, theta, nu2: int):
+    """Mean and observation-scale variance at one test point xt (1 x d) given
+    its neighbour set J (the conditional of Alg. 5 Step 1 with xt as block)."""
+    theta = np.asarray(theta, dtype=np.float64)
+    s2, t2 = theta[0], theta[1]
+    xt = np.asarray(xt, dtype=np.float64)
+    S_con = cov_points(Xd, J, J, theta, nu2)
+    S_cross = cov(Xd[J], xt, theta, nu2)                         # distinct points: no nugget
+    L = np.linalg.cholesky(S_con)
+    S_cross_p = solve_triangular(L, S_cross, lower=True)
+    yJ_p = solve_triangular(L, y[J], lower=True)
+    return float(S_cross_p[:, 0] @ yJ_p), s2 + t2 - float(S_cross_p[:, 0] @ S_cross_p[:, 0])

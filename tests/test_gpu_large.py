@@ -1,0 +1,119 @@
+"""The large single-GPU workload at full size: 50,000,000 points on [0,1]^10
+in FP32 storage (sine-sum response), 1,000,000 blocks, m = 300, predictions
+with m_pred = 300.
+
+The structure follows the paper's large-scale pipeline: slabs along the most
+relevant dimension (Alg. 2, P = 100) and RAC inside every slab (Alg. 3, no
+Lloyd iterations), then the exact earlier-ordered neighbour search (pruned:
+the blocks prune, a radius check makes it exact).  The oracle checks sampled
+outputs: centres of sampled blocks bit for bit, neighbour sets of sampled
+blocks and test points key for key (an O(n) count instead of a sort), block
+terms of sampled blocks and predictions at sampled test points.
+
+Tolerances: the mixed path's error at m = 300 is dominated by a systematic
+second-order bias of the FP32 factorisation of the 300 x 300 neighbour
+block (measured +1.2e-6 per point over all 1M blocks against the FP64 path);
+sampled blocks are held to 1e-5 per point of the block, predictions to 1e-5.
+"""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import sbv
+from synth.inputs import workload
+
+pytestmark = pytest.mark.gpu
+
+P_SLABS = 100
+NTEST = 20_000     # a leading sample of the 1,000,000 test points
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2504_12004_gb300 import build, Context
+    build.build()
+    return Context(0)
+
+
+def knn_is_exact(Zc, cand_ids, q, got):
+    """got (ascending) holds the m smallest (D, id) keys among the candidates."""
+    D = sbv.sq_dist_rows(Zc, q)
+    pos = np.searchsorted(cand_ids, got)          # cand_ids ascending
+    if not np.array_equal(cand_ids[pos], got):
+        return False
+    gk = list(zip(D[pos].tolist(), [int(g) for g in got]))
+    if gk != sorted(gk):
+        return False
+    Dk, ik = gk[-1]
+    inside = (D < Dk) | ((D == Dk) & (cand_ids <= ik))
+    return int(inside.sum()) == len(got) and bool(np.all(inside[pos]))
+
+
+def test_large_workload(ctx):
+    t0 = time.time()
+    w = workload("sine10d_50m", ntest=NTEST)
+    n, d, m = w["n"], w["d"], w["m"]
+    X = torch.from_numpy(w["X"]).cuda()
+    y = torch.from_numpy(w["y"]).cuda()
+    Xt = torch.from_numpy(w["Xtest"]).cuda()
+    th = w["theta"][0]
+    times = {"generate": time.time() - t0}
+    t0 = time.time()
+    b = ctx.sbv_blocking(X, w["beta_scale"], w["bc"], 0, 11, partitions=P_SLABS)
+    torch.cuda.synchronize()
+    times["blocking"] = time.time() - t0
+    t0 = time.time()
+    nbr, cnt = ctx.sbv_knn(X, w["beta_scale"], b["ptr"], b["pts"], b["rank"], b["centres"], m)
+    torch.cuda.synchronize()
+    times["knn"] = time.time() - t0
+    nbr = nbr.contiguous()
+    nmax = ctx.max_block_size(b["ptr"], cnt)
+    bc = b["bc_eff"]
+    bt = torch.empty(1, bc, dtype=torch.float64, device="cuda")
+    t0 = time.time()
+    ll = ctx.sbv_loglik(X, y, b["ptr"], b["pts"], nbr, cnt, th, nu2=5, precision="mixed",
+                        block_terms=bt, nmax=nmax)
+    torch.cuda.synchronize()
+    times["loglik_mixed"] = time.time() - t0
+    ctx.sbv_sync_status()
+    t0 = time.time()
+    mean, var, var_lat, pnbr = ctx.sbv_predict(X, y, Xt, w["beta_scale"], w["m_pred"], th, 5,
+                                               precision="mixed", want_nbr=True, blocks=b)
+    torch.cuda.synchronize()
+    times["predict_mixed"] = time.time() - t0
+    print({k: round(v, 2) for k, v in times.items()}, "nmax", nmax, "ll", float(ll[0]))
+    assert np.isfinite(ll.item())
+
+    # ---- sampled checks against the oracle
+    Xh = w["X"].astype(np.float64)
+    Z = sbv.scale(w["X"], w["beta_scale"])
+    ptr, pts = b["ptr"].cpu().numpy(), b["pts"].cpu().numpy()
+    blk, rank = b["blk"].cpu().numpy(), b["rank"].cpu().numpy()
+    C = b["centres"].cpu().numpy()
+    nb_h, cn_h, bt_h = nbr.cpu().numpy(), cnt.cpu().numpy(), bt.cpu().numpy()[0]
+    assert ptr[-1] == n and bc <= w["bc"]
+    pslab, _ = sbv.slabs(w["X"], w["beta_scale"], P_SLABS)
+    rng = np.random.default_rng(7)
+    for bi in rng.choice(bc, 8, replace=False):
+        mem = np.sort(pts[ptr[bi]:ptr[bi + 1]])
+        assert np.all(blk[mem] == bi) and np.unique(pslab[mem]).size == 1
+        assert np.array_equal(C[bi], np.cumsum(Z[mem], axis=0)[-1] / len(mem))
+    prank = rank[blk]
+    for bi in rng.choice(bc, 3, replace=False):
+        cand = np.flatnonzero(prank < rank[bi])
+        assert cn_h[bi] == min(m, cand.size)
+        assert knn_is_exact(Z[cand], cand, C[bi], nb_h[bi, :cn_h[bi]])
+        J = nb_h[bi, :cn_h[bi]]
+        want = sbv.block_loglik(Xh, w["y"], J, pts[ptr[bi]:ptr[bi + 1]], th, 5)
+        bs = ptr[bi + 1] - ptr[bi]
+        assert abs(bt_h[bi] - want) <= 1e-5 * bs, (bi, bt_h[bi], want)
+    Zt = sbv.scale(w["Xtest"], w["beta_scale"])
+    allidx = np.arange(n)
+    pn = pnbr.cpu().numpy()
+    mh, vh = mean.cpu().numpy(), var.cpu().numpy()
+    for j in rng.choice(NTEST, 2, replace=False):
+        assert knn_is_exact(Z, allidx, Zt[j], pn[j])
+        om, ov = sbv.predict_given(Xh, w["y"], w["Xtest"][j:j + 1], pn[j], th, 5)
+        assert abs(mh[j] - om) <= 1e-5 and abs(vh[j] - ov) <= 1e-5, (j, mh[j], om, vh[j], ov)
