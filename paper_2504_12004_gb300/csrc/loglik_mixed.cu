@@ -175,13 +175,15 @@ loglik_mixed_kernel(MixedArgs P) {
   // refinement steps: one for the likelihood (its quadratic forms are second
   // order in the solve error); three for prediction, whose variance
   // sigma^2 + tau^2 - Sigma_*J z cancels and is first order in the error of z
-  constexpr int NREF = PRED ? 3 : 4;   // at most
-  // The likelihood stops refining once the estimated remaining error of the
-  // block's quadratic form is below REF_TOL per point: after a step whose
-  // correction changed the form by dq, the error left is about dq^2 / |q|
-  // (the first solve's relative error times dq).  Well-conditioned blocks stop
-  // after one step; ill-conditioned ones (long ranges, small nugget) take more.
-  constexpr double REF_TOL = 1e-7;
+  constexpr int NREF = PRED ? 3 : 6;   // at most
+  // The likelihood stops refining once a step changes the block's quadratic
+  // forms by less than REF_TOL per point of the block (with the refinement
+  // contracting by rho <= 1/2 per step, what is left is at most that change),
+  // or once a step no longer halves the change of the previous one (the
+  // residual's rounding floor is reached).  Blocks whose first solve is
+  // already that accurate stop after one step; ill-conditioned ones (long
+  // ranges, many neighbours, small nugget) refine further.
+  constexpr double REF_TOL = 1e-6;
 
   for (int i = threadIdx.x; i < 256; i += blockDim.x) {
     tab_h[i] = C.tab_h[i];
@@ -607,6 +609,7 @@ loglik_mixed_kernel(MixedArgs P) {
       c2[p] = 0.0f;
     }
     __syncthreads();
+    double dq_prev = INFINITY;   // per item
 #pragma unroll 1
     for (int it = 0; it < NREF; ++it) {
     // ---- 5. residuals in double-float for x = x0 + c1 and x0J + c2; all
@@ -676,25 +679,21 @@ loglik_mixed_kernel(MixedArgs P) {
     }
     __syncthreads();
     bwd_solve2(A, N, r1, r2);
-    double dq = 0.0, qs = 0.0;
+    double dq = 0.0;
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
       c1[p] += r1[p];
       c2[p] += r2[p];
       if (!PRED) {
         const double yp = (double)yv[p].x + (double)yv[p].y;
         dq += yp * (double)r1[p];
-        qs += fabs(yp * ((double)x0[p] + (double)c1[p]));
-        if (p < mb) {
-          dq -= yp * (double)r2[p];
-          qs += fabs(yp * ((double)x0J[p] + (double)c2[p]));
-        }
+        if (p < mb) dq -= yp * (double)r2[p];
       }
     }
     __syncthreads();
     if (!PRED) {
-      const double dqs = cta_sum_mx(dq, red);
-      const double qss = cta_sum_mx(qs, red);
-      if (dqs * dqs <= REF_TOL * (double)bs * qss) break;   // uniform over the CTA
+      const double dqs = fabs(cta_sum_mx(dq, red));   // the same in every thread
+      if (dqs <= REF_TOL * (double)bs || dqs > 0.5 * dq_prev) break;
+      dq_prev = dqs;
     }
     }  // refinement steps
     if (PRED) {
