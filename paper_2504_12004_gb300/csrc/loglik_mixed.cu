@@ -122,6 +122,27 @@ __device__ double cta_sum_mx(double v, double* red) {
   return s;
 }
 
+// Two sums over the CTA at once (red holds at least two doubles per warp).
+__device__ double2 cta_sum2_mx(double a, double b, double* red) {
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    red[2 * (threadIdx.x >> 5)] = a;
+    red[2 * (threadIdx.x >> 5) + 1] = b;
+  }
+  __syncthreads();
+  double sa = 0.0, sb = 0.0;
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+    sa += red[2 * q];
+    sb += red[2 * q + 1];
+  }
+  __syncthreads();
+  return make_double2(sa, sb);
+}
+
 // X split once per call into float pairs (hi, lo), hi + lo = x to ~2^-48 relative.
 __global__ void split_points_kernel(const double* __restrict__ X, int64_t total,
                                     float2* __restrict__ out) {
@@ -151,7 +172,7 @@ loglik_mixed_kernel(MixedArgs P) {
   __shared__ float tab_h[256], tab_l[256];
   __shared__ unsigned int s_item;
   __shared__ int s_fail;
-  __shared__ double red[MX_WARPS];
+  __shared__ double red[2 * MX_WARPS];
   __shared__ float s_org_h[SBV_MAX_DIM], s_org_l[SBV_MAX_DIM];
   __shared__ float s_grid;
   __shared__ uint32_t s_tmem;
@@ -176,14 +197,17 @@ loglik_mixed_kernel(MixedArgs P) {
   // order in the solve error); three for prediction, whose variance
   // sigma^2 + tau^2 - Sigma_*J z cancels and is first order in the error of z
   constexpr int NREF = PRED ? 3 : 6;   // at most
-  // The likelihood stops refining once a step changes the block's quadratic
-  // forms by less than REF_TOL per point of the block (with the refinement
-  // contracting by rho <= 1/2 per step, what is left is at most that change),
-  // or once a step no longer halves the change of the previous one (the
-  // residual's rounding floor is reached).  Blocks whose first solve is
-  // already that accurate stop after one step; ill-conditioned ones (long
-  // ranges, many neighbours, small nugget) refine further.
+  // Likelihood: y^T Sigma^-1 y = y^T x + x^T r + r^T Sigma^-1 r exactly, for
+  // any x and r = y - Sigma x.  Every step forms r at the current x (double
+  // float) and w = L^-1 r (forward solve with the FP32 factor), and takes
+  // q = y^T x + x^T r + |w|^2 for both systems: the error is rho |w|^2, rho
+  // the FP32 factor's contraction, i.e. third order in the error of x.  The
+  // block stops once |w|^2 (both systems) is below REF_TOL per point of the
+  // block, or stops halving (the residual's rounding floor); only otherwise
+  // does the backward solve complete the correction of x for another step.
+  // Well-conditioned blocks finish after one residual and one forward solve.
   constexpr double REF_TOL = 1e-6;
+  __shared__ double s_qvar;   // x^T r of the full system minus that of J
 
   for (int i = threadIdx.x; i < 256; i += blockDim.x) {
     tab_h[i] = C.tab_h[i];
@@ -671,6 +695,16 @@ loglik_mixed_kernel(MixedArgs P) {
       }
       __syncthreads();
     }
+    double t1 = 0.0, t2 = 0.0;
+    if (!PRED) {
+      for (int p = threadIdx.x; p < N; p += blockDim.x) {
+        t1 += ((double)x0[p] + (double)c1[p]) * (double)r1[p];
+        if (p < mb) t2 += ((double)x0J[p] + (double)c2[p]) * (double)r2[p];
+      }
+      const double2 t = cta_sum2_mx(t1, t2, red);   // the same in every thread
+      t1 = t.x;
+      t2 = t.y;
+    }
     // corrections: (L L^T)^{-1} r and (L_JJ L_JJ^T)^{-1} r_J
     fwd_solve2(A, N, r1, r2);
     for (int p = mb + threadIdx.x; p < N; p += blockDim.x) {
@@ -678,23 +712,26 @@ loglik_mixed_kernel(MixedArgs P) {
       if (PRED) r1[p] = 0.0f;
     }
     __syncthreads();
+    if (!PRED) {
+      double u1 = 0.0, u2 = 0.0;
+      for (int p = threadIdx.x; p < N; p += blockDim.x) {
+        u1 += (double)r1[p] * (double)r1[p];
+        u2 += (double)r2[p] * (double)r2[p];
+      }
+      const double2 uu = cta_sum2_mx(u1, u2, red);
+      u1 = uu.x;
+      u2 = uu.y;
+      if (threadIdx.x == 0) s_qvar = (t1 + u1) - (t2 + u2);
+      const double u = u1 + u2;
+      if (u <= REF_TOL * (double)bs || u > 0.5 * dq_prev || it == NREF - 1) break;
+      dq_prev = u;
+    }
     bwd_solve2(A, N, r1, r2);
-    double dq = 0.0;
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
       c1[p] += r1[p];
       c2[p] += r2[p];
-      if (!PRED) {
-        const double yp = (double)yv[p].x + (double)yv[p].y;
-        dq += yp * (double)r1[p];
-        if (p < mb) dq -= yp * (double)r2[p];
-      }
     }
     __syncthreads();
-    if (!PRED) {
-      const double dqs = fabs(cta_sum_mx(dq, red));   // the same in every thread
-      if (dqs <= REF_TOL * (double)bs || dqs > 0.5 * dq_prev) break;
-      dq_prev = dqs;
-    }
     }  // refinement steps
     if (PRED) {
       // mean = Sigma_*J x, var = sigma^2 + tau^2 - Sigma_*J z, sums in FP64
@@ -729,7 +766,7 @@ loglik_mixed_kernel(MixedArgs P) {
         v += 2.0 * ((double)ex * 0.69314718055994530942 + (double)logf(mant));
       }
     }
-    const double s = cta_sum_mx(v, red);
+    const double s = cta_sum_mx(v, red) + s_qvar;
     if (threadIdx.x == 0) {
       const double term = -0.5 * ((double)bs * log2pi + s);
       a.terms[item] = term;
