@@ -58,6 +58,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-side-paths", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--launch", default="graph", choices=["graph", "direct"],
+                   help="time graph replays (default) or direct sbv_loglik calls")
+    p.add_argument("--no-autotune", action="store_true")
     return p.parse_args()
 
 
@@ -298,7 +301,21 @@ def main():
 
     nmax = ctx.max_block_size(ptr, cnt)
 
+    # launch shape from the autotuner, then one evaluation captured as a CUDA
+    # graph (counter reset, persistent block kernel, fixed-order reduction)
+    # and replayed with the parameter row as its only input
+    tuned = None
+    if not args.no_autotune:
+        tuned = ctx.sbv_autotune(X, y, ptr, pts, nbr, cnt, th, nu2=w["nu2"],
+                                 precision=args.precision, nmax=nmax)
+    graph = None
+    if args.launch == "graph":
+        graph = ctx.sbv_loglik_graph_create(X, y, ptr, pts, nbr, cnt, B=1, nu2=w["nu2"],
+                                            precision=args.precision, nmax=nmax)
+
     def evaluate(precision):
+        if graph is not None and precision == args.precision:
+            return graph.launch(th)
         return ctx.sbv_loglik(X, y, ptr, pts, nbr, cnt, th, nu2=w["nu2"], precision=precision,
                               nmax=nmax)
 
@@ -425,7 +442,11 @@ def main():
             "paths": paths,
             "preprocess_s": {"blocking": t_block, "knn": t_knn},
             "algorithmic_flops_per_eval": flops,
-            "gpu_launches": 3 * args.steps,
+            # graph replay: block kernel + reduction per step; direct call:
+            # also the float-pair split of the points
+            "gpu_launches": (2 if graph is not None else 3) * args.steps,
+            "launch": {"mode": args.launch,
+                       "shape": {"threads": tuned[0], "ctas_per_sm": tuned[1]} if tuned else None},
             "clocks": clocks,
             "roofline": roof,
             "cpu_baseline": cpu,

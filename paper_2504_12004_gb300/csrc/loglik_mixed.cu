@@ -364,55 +364,69 @@ loglik_mixed_kernel(MixedArgs P) {
       for (int p = threadIdx.x; p < N; p += blockDim.x) A[tri(N, p)] = yv[p].x;
     }
     __syncthreads();
-    // ---- 3. blocked Cholesky
+    // ---- 3. blocked Cholesky.  CUDA-core variant with look-ahead: while the
+    // other warps apply panel k to the trailing matrix, warp 0 first updates
+    // the next diagonal tile (the first ten 4 x 4 blocks of the trailing
+    // triangle) and factors it, so the tile factorisation is off the critical
+    // path.  The tensor-core variant factors each tile before its panel.
+    //
+    // factor_tile(k0), warp 0 only, lane r holding row r of the tile: the
+    // double-float original (scratch matrix) plus the accumulated FP32 updates
+    // (held negated in A), one exact subtraction, then an FP32 factorisation
+    // in registers; L, its diagonal and inverse diagonal are stored.
+    auto factor_tile = [&](const int kt) {
+      const int nt = min(kt + NB, N) - kt;
+      const int r = lane;
+      float row[NB];
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        float v = 0.0f;
+        if (r < nt && c <= r) {
+          const float2 k = S[(size_t)(kt + c) * N + (kt + r)];
+          const df s = two_sum(k.x, A[tri(kt + r, kt + c)]);
+          v = __fadd_rn(s.h, __fadd_rn(s.l, k.y));
+        }
+        row[c] = v;
+      }
+      bool bad = false;
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        if (c < nt) {
+          const float dcc = __shfl_sync(0xffffffffu, row[c], c);
+          bad |= !(dcc > 0.0f);
+          const float Lcc = sqrtf(fmaxf(dcc, 1e-30f));
+          const float inv = 1.0f / Lcc;
+          if (r == c) row[c] = Lcc;
+          if (r > c) row[c] *= inv;
+#pragma unroll
+          for (int c2 = c + 1; c2 < NB; ++c2) {
+            const float v = __shfl_sync(0xffffffffu, row[c], c2);  // L[c2][c]
+            if (r >= c2 && c2 < nt) row[c2] = fmaf(-row[c], v, row[c2]);
+          }
+        }
+      }
+      if (r < nt) {
+        float Lrr = 0.0f;
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+          if (c <= r) A[tri(kt + r, kt + c)] = row[c];
+          if (c == r) Lrr = row[c];
+        }
+        ldiag[kt + r] = Lrr;
+        idiag[kt + r] = 1.0f / Lrr;
+      }
+      if (bad && lane == 0) s_fail = 1;
+    };
+    if (!TC) {
+      if (warp == 0) factor_tile(0);
+      __syncthreads();
+    }
     for (int k0 = 0; k0 < N; k0 += NB) {
       const int k1 = min(k0 + NB, N), nbk = k1 - k0;
-      if (warp == 0) {
-        // lane r holds row r of the tile: original (double-float, from the
-        // scratch matrix) plus the accumulated FP32 updates (held negated in
-        // A), one exact subtraction, then rounded to FP32
-        const int r = lane;
-        float row[NB];
-#pragma unroll
-        for (int c = 0; c < NB; ++c) {
-          float v = 0.0f;
-          if (r < nbk && c <= r) {
-            const float2 k = S[(size_t)(k0 + c) * N + (k0 + r)];
-            const df s = two_sum(k.x, A[tri(k0 + r, k0 + c)]);
-            v = __fadd_rn(s.h, __fadd_rn(s.l, k.y));
-          }
-          row[c] = v;
-        }
-        bool bad = false;
-#pragma unroll
-        for (int c = 0; c < NB; ++c) {
-          if (c < nbk) {
-            const float dcc = __shfl_sync(0xffffffffu, row[c], c);
-            bad |= !(dcc > 0.0f);
-            const float Lcc = sqrtf(fmaxf(dcc, 1e-30f));
-            const float inv = 1.0f / Lcc;
-            if (r == c) row[c] = Lcc;
-            if (r > c) row[c] *= inv;
-#pragma unroll
-            for (int c2 = c + 1; c2 < NB; ++c2) {
-              const float v = __shfl_sync(0xffffffffu, row[c], c2);  // L[c2][c]
-              if (r >= c2 && c2 < nbk) row[c2] = fmaf(-row[c], v, row[c2]);
-            }
-          }
-        }
-        if (r < nbk) {
-          float Lrr = 0.0f;
-#pragma unroll
-          for (int c = 0; c < NB; ++c) {
-            if (c <= r) A[tri(k0 + r, k0 + c)] = row[c];
-            if (c == r) Lrr = row[c];
-          }
-          ldiag[k0 + r] = Lrr;
-          idiag[k0 + r] = 1.0f / Lrr;
-        }
-        if (bad && lane == 0) s_fail = 1;
+      if (TC) {
+        if (warp == 0) factor_tile(k0);
+        __syncthreads();
       }
-      __syncthreads();
       if (s_fail) break;
       // panel solve: rows k1..N, A(i, k0:k1) <- A(i, k0:k1) L_kk^{-T}; the panel
       // is also stored as the update operand (FP32 column-major, or BF16 pieces)
@@ -467,9 +481,14 @@ loglik_mixed_kernel(MixedArgs P) {
         if (ncols_all > 0) {
           const int RB = (T + 3) >> 2;
           const int nblk = RB * (RB + 1) / 2;
-          int bi = 0, bj = threadIdx.x;
+          // blocks 0..9 (rows and columns k1 .. k1+15: the next diagonal tile)
+          // go to lanes 0..9 of warp 0, the rest to warps 1..
+          const int first = warp == 0 ? lane : 10 + (int)threadIdx.x - 32;
+          const int stride = warp == 0 ? 1 << 30 : (int)blockDim.x - 32;
+          const int lend = warp == 0 ? min(10, nblk) : nblk;
+          int bi = 0, bj = first;
           while (bj > bi) { bj -= bi + 1; ++bi; }
-          for (int l = threadIdx.x; l < nblk; l += blockDim.x) {
+          for (int l = first; l < lend; l += stride) {
             float acc[4][4];
 #pragma unroll
             for (int p = 0; p < 4; ++p)
@@ -496,9 +515,14 @@ loglik_mixed_kernel(MixedArgs P) {
                 if (jj <= ii && jj < N) A[tri(ii, jj)] -= acc[p][q];
               }
             }
-            bj += blockDim.x;
+            if (l + stride >= lend) break;   // before walking (bi, bj) that far
+            bj += stride;
             while (bj > bi) { bj -= bi + 1; ++bi; }
           }
+        }
+        if (warp == 0 && k1 < N) {
+          __syncwarp();
+          factor_tile(k1);
         }
       } else {
         // trailing update on the tensor cores: for each 128-row tile of P and
