@@ -278,7 +278,8 @@ struct PrunedArgs {
   const float* bcen;       // block centres by rank, nb x d
   const float* blo;        // block bounding boxes by rank, nb x d (rounded outwards)
   const float* bhi;
-  float rad_max;           // largest half-extent of a box in the grid dimensions
+  float rad_max;           // largest half-extent of a box in grid dimension g0 ...
+  float rad_max1;          // ... and in g1
   float slack;             // absolute slack of the float32 centre tests
   int g0, g1;              // grid dimensions
   double gmin0, gmin1, cell;
@@ -348,6 +349,7 @@ __global__ void __launch_bounds__(PK_WARPS * 32) knn_pruned_kernel(PrunedArgs a)
   int32_t thr_id = 0x7fffffff;
   float lim = INFINITY;
   const double W = (double)R + (double)a.rad_max + (double)a.slack;
+  const double W1 = (double)R + (double)a.rad_max1 + (double)a.slack;
   auto cell_of = [&](double v, double gmin, int nc) {
     double c = floor((v - gmin) / a.cell);
     return c < 0.0 ? 0 : (c > (double)(nc - 1) ? nc - 1 : (int)c);
@@ -355,8 +357,8 @@ __global__ void __launch_bounds__(PK_WARPS * 32) knn_pruned_kernel(PrunedArgs a)
   // one extra cell on each side absorbs rounding of the cell indices
   const int i0 = max(cell_of(qc[a.g0] - W, a.gmin0, a.nc0) - 1, 0);
   const int i1 = min(cell_of(qc[a.g0] + W, a.gmin0, a.nc0) + 1, a.nc0 - 1);
-  const int j0 = max(cell_of(qc[a.g1] - W, a.gmin1, a.nc1) - 1, 0);
-  const int j1 = min(cell_of(qc[a.g1] + W, a.gmin1, a.nc1) + 1, a.nc1 - 1);
+  const int j0 = max(cell_of(qc[a.g1] - W1, a.gmin1, a.nc1) - 1, 0);
+  const int j1 = min(cell_of(qc[a.g1] + W1, a.gmin1, a.nc1) + 1, a.nc1 - 1);
   for (int ci = i0; ci <= i1; ++ci) {
     for (int cj = j0; cj <= j1; ++cj) {
       const int64_t cs = a.cell_ptr[(int64_t)ci * a.nc1 + cj], ce = a.cell_ptr[(int64_t)ci * a.nc1 + cj + 1];
@@ -440,11 +442,11 @@ __global__ void block_bounds_kernel(const double* __restrict__ Z64, int64_t n, i
                                     const int32_t* __restrict__ blk_of_rank, int64_t nb,
                                     float* __restrict__ bcen, float* __restrict__ blo,
                                     float* __restrict__ bhi, float* __restrict__ bhalf) {
+  // bhalf: nb x d, half-extent of the box around the centre per dimension
   int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   for (; w < nb; w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const double* c = centres + (int64_t)blk_of_rank[w] * d;
-    float half = 0.0f;
     for (int t = 0; t < d; ++t) {
       double lo = INFINITY, hi = -INFINITY;
       for (int64_t p = rptr[w] + lane; p < rptr[w + 1]; p += 32) {
@@ -460,10 +462,9 @@ __global__ void block_bounds_kernel(const double* __restrict__ Z64, int64_t n, i
         blo[w * d + t] = __double2float_rd(lo);
         bhi[w * d + t] = __double2float_ru(hi);
         bcen[w * d + t] = (float)c[t];
-        half = fmaxf(half, __double2float_ru(fmax(c[t] - lo, hi - c[t])));
+        bhalf[w * d + t] = __double2float_ru(fmax(c[t] - lo, hi - c[t]));
       }
     }
-    if (lane == 0) bhalf[w] = half;
   }
 }
 
@@ -605,7 +606,7 @@ static int knn_pruned(sbv_ctx* ctx, KnnArgs base, const int32_t* rank_of_block, 
   const int64_t n = base.n, nq = base.nq;
   const int d = base.d, m = base.m;
   const int sms = ctx->num_sms;
-  size_t bytes = (size_t)nb * 4 + (size_t)nb * d * 4 * 3 + (size_t)nb * 4 + (size_t)nb * 4 * 3 +
+  size_t bytes = (size_t)nb * 4 + (size_t)nb * d * 4 * 4 + (size_t)nb * 4 * 3 +
                  (size_t)(nq + 8) * 8 * 4 + (size_t)nq * 4 * 2 + 4096 + (size_t)64 * 8;
   char* wp = (char*)ws_get(ctx, WS_SORT_D, bytes, &st);
   if (!wp) return st;
@@ -618,7 +619,7 @@ static int knn_pruned(sbv_ctx* ctx, KnnArgs base, const int32_t* rank_of_block, 
   float* bcen = (float*)take((size_t)nb * d * 4);
   float* blo = (float*)take((size_t)nb * d * 4);
   float* bhi = (float*)take((size_t)nb * d * 4);
-  float* brad = (float*)take((size_t)nb * 4);   // largest half-extent of each box
+  float* brad = (float*)take((size_t)nb * d * 4);   // box half-extents per dimension
   int32_t* keys = (int32_t*)take((size_t)nb * 4);
   int32_t* keys_sorted = (int32_t*)take((size_t)nb * 4);
   int32_t* iota = (int32_t*)take((size_t)nb * 4);
@@ -628,7 +629,7 @@ static int knn_pruned(sbv_ctx* ctx, KnnArgs base, const int32_t* rank_of_block, 
   int64_t* spare = (int64_t*)take((size_t)(nq + 8) * 8);
   float* qR = (float*)take((size_t)nq * 4);
   int32_t* brute = (int32_t*)take((size_t)nq * 4);
-  unsigned long long* counters = (unsigned long long*)take(1024);
+  unsigned long long* counters = (unsigned long long*)take(2048);
   unsigned int* mm = (unsigned int*)(counters + 8);  // 64 mins, 64 maxima, radius min and max
   (void)spare;
   block_of_rank_kernel<<<grid_for(nb, 256, sms), 256, 0, s>>>(rank_of_block, nb, blk_of_rank);
@@ -636,21 +637,28 @@ static int knn_pruned(sbv_ctx* ctx, KnnArgs base, const int32_t* rank_of_block, 
                                                                  blk_of_rank, nb, bcen, blo, bhi, brad);
   SBV_LAUNCH_CHECK(ctx, "block_bounds_kernel");
   // extents of the block centres and the largest radius
-  std::vector<unsigned int> init(130);
-  for (int t = 0; t < 130; ++t) init[t] = (t < 64 || t == 128) ? 0xffffffffu : 0u;
-  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(mm, init.data(), 130 * 4, cudaMemcpyHostToDevice, s));
+  // mm: 64 minima and 64 maxima of the centres, then 64 minima and 64 maxima
+  // of the box half-extents, per dimension
+  std::vector<unsigned int> init(256);
+  for (int t = 0; t < 256; ++t) init[t] = (t < 64 || (t >= 128 && t < 192)) ? 0xffffffffu : 0u;
+  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(mm, init.data(), 256 * 4, cudaMemcpyHostToDevice, s));
   minmax_kernel<<<grid_for(nb * d, 256, sms), 256, 0, s>>>(bcen, nb, d, mm, mm + 64);
-  minmax_kernel<<<grid_for(nb, 256, sms), 256, 0, s>>>(brad, nb, 1, mm + 128, mm + 129);
+  minmax_kernel<<<grid_for(nb * d, 256, sms), 256, 0, s>>>(brad, nb, d, mm + 128, mm + 192);
   SBV_LAUNCH_CHECK(ctx, "minmax_kernel");
-  std::vector<unsigned int> hm(130);
-  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(hm.data(), mm, 130 * 4, cudaMemcpyDeviceToHost, s));
+  std::vector<unsigned int> hm(256);
+  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(hm.data(), mm, 256 * 4, cudaMemcpyDeviceToHost, s));
   SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
   std::vector<double> lo(d), ext(d);
   for (int t = 0; t < d; ++t) {
     lo[t] = unmap_float(hm[t]);
     ext[t] = std::max((double)unmap_float(hm[64 + t]) - lo[t], 1e-30);
   }
-  const double rad_max = unmap_float(hm[129]);
+  std::vector<double> half(d);
+  double rad_max = 0.0;
+  for (int t = 0; t < d; ++t) {
+    half[t] = unmap_float(hm[192 + t]);
+    rad_max = std::max(rad_max, half[t]);
+  }
   int g0 = 0, g1 = d > 1 ? 1 : 0;
   for (int t = 0; t < d; ++t)
     if (ext[t] > ext[g0]) g0 = t;
@@ -665,7 +673,7 @@ static int knn_pruned(sbv_ctx* ctx, KnnArgs base, const int32_t* rank_of_block, 
   const double vd = pow(M_PI, 0.5 * d) / tgamma(0.5 * d + 1.0);
   const double vol_over_vd = vol / vd;
   const double r_typ = pow(3.0 * m * vol_over_vd / std::max<double>(n / 2, 1), 1.0 / d);
-  double cell = r_typ + rad_max;
+  double cell = r_typ + std::max(half[g0], half[g1]);
   int nc0 = std::max(1, (int)ceil(ext[g0] / cell)), nc1 = std::max(1, (int)ceil(ext[g1] / cell));
   while ((int64_t)nc0 * nc1 > (1 << 22)) {
     cell *= 2.0;
@@ -720,7 +728,8 @@ static int knn_pruned(sbv_ctx* ctx, KnnArgs base, const int32_t* rank_of_block, 
   a.bcen = bcen;
   a.blo = blo;
   a.bhi = bhi;
-  a.rad_max = (float)rad_max;
+  a.rad_max = (float)half[g0];
+  a.rad_max1 = (float)half[g1];
   double zmax = 0.0;
   for (int t = 0; t < d; ++t) zmax = std::max(zmax, std::max(fabs(lo[t]), fabs(lo[t] + ext[t])));
   a.slack = (float)(1e-5 * (zmax + rad_max + 1.0) * d);
