@@ -175,10 +175,24 @@ __device__ __forceinline__ int colsum_index(int lane) {
   return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
 }
 
-// copy a 128 KB tiled operand from global memory into shared memory
-__device__ __forceinline__ void stage_b(unsigned char* sB, const uint4* g) {
-  uint4* d = reinterpret_cast<uint4*>(sB);
-  for (int i = threadIdx.x; i < B_BYTES / 16; i += blockDim.x) d[i] = __ldg(g + i);
+// Start copying a 128 KB tiled operand into shared memory with the bulk-copy
+// engine (four 32 KB copies on one mbarrier); stage_wait blocks every thread
+// until it has landed.  Thread 0 issues; the caller guarantees that nothing
+// still reads the destination (its previous MMA has completed).
+__device__ __forceinline__ void stage_issue(unsigned char* sB, const uint4* g, uint64_t* bar) {
+  if (threadIdx.x == 0) {
+    umma::mbar_arrive_expect_tx(bar, B_BYTES);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      umma::bulk_g2s(sB + q * (B_BYTES / 4), reinterpret_cast<const unsigned char*>(g) + q * (B_BYTES / 4),
+                     B_BYTES / 4, bar);
+  }
+}
+__device__ __forceinline__ bool stage_wait(uint64_t* bar, uint32_t& phase, int* s_timeout) {
+  if (!umma::mbar_wait(bar, phase, kWait)) *s_timeout = 1;
+  phase ^= 1u;
+  __syncthreads();   // the outcome is the same for every thread
+  return *s_timeout == 0;
 }
 
 // D[tmem] = A (128 x 256) * B (256 x 256)^T from the tiled operands in shared
@@ -213,37 +227,49 @@ __device__ __forceinline__ void tmem_row16(uint32_t taddr, float (&v)[16]) {
   umma::tmem_wait_ld();
 }
 
-__global__ void __launch_bounds__(TILE, 1) mlp_fused_kernel(FusedArgs a) {
+// Two threads per row: warps 0-3 take columns 0..127 of rows 32 (w % 4) ..,
+// warps 4-7 columns 128..255 of the same rows (a warp reads TMEM lanes
+// 32 (w % 4) .. 32 (w % 4) + 31).
+constexpr int MT = 2 * TILE;
+
+__global__ void __launch_bounds__(MT, 1) mlp_fused_kernel(FusedArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;
   unsigned char* sB = smem + A_BYTES;
   float* sX = reinterpret_cast<float*>(sB + B_BYTES);   // TILE x MAXIN
-  float* sred = sX + TILE * MAXIN;                       // 3 x 4 warps x 256
-  __shared__ uint64_t bar;
+  float* sred = sX + TILE * MAXIN;                       // 3 x 4 row groups x 256
+  __shared__ uint64_t bar;    // MMA completion
+  __shared__ uint64_t tbar;   // bulk copies of the weight operands
   __shared__ uint32_t s_tmem;
   __shared__ int s_timeout;
-  __shared__ float s_loss[4];
+  __shared__ float s_loss[8];
+  __shared__ float s_part[2][TILE];   // per-half partial outputs
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int64_t row = (int64_t)blockIdx.x * TILE + t;
+  const int rg = warp & 3, hf = warp >> 2;
+  const int r = rg * 32 + lane;                       // row in the tile
+  const int cb = hf * (WID / 2), ce = cb + WID / 2;   // this thread's columns
+  const int64_t row = (int64_t)blockIdx.x * TILE + r;
   const bool valid = row < a.K;
   const int in = a.in;
   const Off o = offsets(in);
   const PartOff po = part_offsets(in);
-  const float* P = a.p;
+  const float* __restrict__ P = a.p;
 
   if (warp == 0) umma::tmem_alloc(&s_tmem, 512);
   if (t == 0) {
     umma::mbar_init(&bar, 1);
+    umma::mbar_init(&tbar, 1);
     s_timeout = 0;
   }
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tm = s_tmem;
-  const uint32_t lane_base = tm + ((uint32_t)(32 * warp) << 16);
-  uint32_t phase = 0;
+  const uint32_t lane_base = tm + ((uint32_t)(32 * rg) << 16);
+  uint32_t phase = 0, tphase = 0;
   bool ok = true;
+  stage_issue(sB, a.w2, &tbar);   // lands while layer 1 runs
 
   // ---- input row and layer 1 (CUDA cores, FP32) ----
   float x[MAXIN];
@@ -251,114 +277,141 @@ __global__ void __launch_bounds__(TILE, 1) mlp_fused_kernel(FusedArgs a) {
 #pragma unroll
   for (int j = 0; j < MAXIN; ++j) {
     x[j] = (valid && j < in) ? a.X[src * in + j] : 0.0f;
-    sX[t * MAXIN + j] = x[j];
+    if (hf == 0) sX[r * MAXIN + j] = x[j];
   }
   const float tgt = (valid && a.train) ? a.t[src] : 0.0f;
-  stage_b(sB, a.w2);
-  for (int c = 0; c < WID; c += 16) {
+  for (int c = cb; c < ce; c += 16) {
     float h[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int f = c + e;
-      float z = P[o.b1 + f];
-      for (int j = 0; j < in; ++j) z = fmaf(P[o.W1 + (int64_t)f * in + j], x[j], z);
+      float z = __ldg(P + o.b1 + f);
+#pragma unroll
+      for (int j = 0; j < MAXIN; ++j)
+        if (j < in) z = fmaf(__ldg(P + o.W1 + (int64_t)f * in + j), x[j], z);
       h[e] = gelu_f(z);
       if (a.train) a.h1t[(int64_t)f * a.kpad + row] = __float2bfloat16_rn(h[e]);
     }
-    store_row16(sA, t, c, h);
+    store_row16(sA, r, c, h);
   }
   // ---- layer 2: Z2 = H1 W2^T + b2 -> TMEM columns 0..255 ----
-  ok = gemm_128x256(tm, sA, sB, &bar, phase, &s_timeout);
+  ok = stage_wait(&tbar, tphase, &s_timeout);
+  if (ok) ok = gemm_128x256(tm, sA, sB, &bar, phase, &s_timeout);
+  bool pending = false;
   if (ok) {
-    for (int c = 0; c < WID; c += 16) {
+    stage_issue(sB, a.w3, &tbar);   // sB is free: lands during the epilogue
+    pending = true;
+  }
+  if (ok) {
+    for (int c = cb; c < ce; c += 16) {
       float v[16];
       tmem_row16(lane_base + c, v);
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
-        v[e] = gelu_f(v[e] + P[o.b2 + c + e]);
+        v[e] = gelu_f(v[e] + __ldg(P + o.b2 + c + e));
         if (a.train) a.h2t[(int64_t)(c + e) * a.kpad + row] = __float2bfloat16_rn(v[e]);
       }
-      store_row16(sA, t, c, v);
+      store_row16(sA, r, c, v);
     }
   }
   __syncthreads();
-  stage_b(sB, a.w3);
   // ---- layer 3: Z3 = H2 W3^T + b3 -> TMEM columns 256..511 ----
+  if (pending) {
+    ok = stage_wait(&tbar, tphase, &s_timeout) && ok;
+    pending = false;
+  }
   if (ok) ok = gemm_128x256(tm + 256, sA, sB, &bar, phase, &s_timeout);
-  // ---- output and loss ----
-  float sv = P[o.b4];
   if (ok) {
-    for (int c = 0; c < WID; c += 16) {
+    stage_issue(sB, a.w3t, &tbar);
+    pending = true;
+  }
+  // ---- output and loss ----
+  float sp = 0.0f;
+  if (ok) {
+    for (int c = cb; c < ce; c += 16) {
       float v[16];
       tmem_row16(lane_base + 256 + c, v);
 #pragma unroll
-      for (int e = 0; e < 16; ++e) sv = fmaf(gelu_f(v[e] + P[o.b3 + c + e]), P[o.w4 + c + e], sv);
+      for (int e = 0; e < 16; ++e)
+        sp = fmaf(gelu_f(v[e] + __ldg(P + o.b3 + c + e)), __ldg(P + o.w4 + c + e), sp);
     }
   }
+  s_part[hf][r] = sp;
+  __syncthreads();
+  const float sv = (__ldg(P + o.b4) + s_part[0][r]) + s_part[1][r];
   float ds;
   if (a.train) {
-    const float r = sv - tgt;
-    ds = valid ? 2.0f * r * a.inv_K : 0.0f;
-    float l2 = valid ? r * r : 0.0f;
+    const float res = sv - tgt;
+    ds = valid ? 2.0f * res * a.inv_K : 0.0f;
+    float l2 = (valid && hf == 0) ? res * res : 0.0f;
 #pragma unroll
     for (int sh = 16; sh > 0; sh >>= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, sh);
     if (lane == 0) s_loss[warp] = l2;
   } else {
     ds = valid ? 1.0f : 0.0f;
-    if (valid) a.s[row] = sv;
+    if (valid && hf == 0) a.s[row] = sv;
   }
   // ---- dZ3 = ds w4 * GELU'(Z3); partial sums of dw4 and db3 ----
   float* red_w4 = sred;
   float* red_b3 = sred + 4 * WID;
   float* red_b2 = sred + 8 * WID;
-  __syncthreads();   // layer-3 MMA done and every lane past its reads of sB
   if (ok) {
-    for (int c = 0; c < WID; c += 16) {
+    for (int c = cb; c < ce; c += 16) {
       float v[16], g[16], hw[16];
       tmem_row16(lane_base + 256 + c, v);
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
-        const float z = v[e] + P[o.b3 + c + e];
+        const float z = v[e] + __ldg(P + o.b3 + c + e);
         hw[e] = ds * gelu_f(z);
-        g[e] = ds * P[o.w4 + c + e] * gelu_prime_f(z);
+        g[e] = ds * __ldg(P + o.w4 + c + e) * gelu_prime_f(z);
         if (a.train) a.dz3t[(int64_t)(c + e) * a.kpad + row] = __float2bfloat16_rn(g[e]);
       }
-      store_row16(sA, t, c, g);
+      store_row16(sA, r, c, g);
       if (a.train) {
         const int ci = colsum_index(lane);
         const float sw = warp_colsum16(hw, lane);
         const float sb = warp_colsum16(g, lane);
         if ((lane & 1) == 0) {
-          red_w4[warp * WID + c + ci] = sw;
-          red_b3[warp * WID + c + ci] = sb;
+          red_w4[rg * WID + c + ci] = sw;
+          red_b3[rg * WID + c + ci] = sb;
         }
       }
     }
   }
-  stage_b(sB, a.w3t);
   // ---- dH2 = dZ3 W3 -> TMEM columns 256..511; dZ2 = dH2 * GELU'(Z2) ----
+  if (pending) {
+    ok = stage_wait(&tbar, tphase, &s_timeout) && ok;
+    pending = false;
+  }
   if (ok) ok = gemm_128x256(tm + 256, sA, sB, &bar, phase, &s_timeout);
   if (ok) {
-    for (int c = 0; c < WID; c += 16) {
+    stage_issue(sB, a.w2t, &tbar);
+    pending = true;
+  }
+  if (ok) {
+    for (int c = cb; c < ce; c += 16) {
       float dh[16], z[16];
       tmem_row16(lane_base + 256 + c, dh);
       tmem_row16(lane_base + c, z);
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
-        dh[e] *= gelu_prime_f(z[e] + P[o.b2 + c + e]);
+        dh[e] *= gelu_prime_f(z[e] + __ldg(P + o.b2 + c + e));
         if (a.train) a.dz2t[(int64_t)(c + e) * a.kpad + row] = __float2bfloat16_rn(dh[e]);
       }
-      store_row16(sA, t, c, dh);
+      store_row16(sA, r, c, dh);
       if (a.train) {
         const int ci = colsum_index(lane);
         const float sb = warp_colsum16(dh, lane);
-        if ((lane & 1) == 0) red_b2[warp * WID + c + ci] = sb;
+        if ((lane & 1) == 0) red_b2[rg * WID + c + ci] = sb;
       }
     }
   }
   __syncthreads();
-  stage_b(sB, a.w2t);
   // ---- dH1 = dZ2 W2 -> TMEM columns 0..255; dZ1 = dH1 * GELU'(Z1) ----
+  if (pending) {
+    ok = stage_wait(&tbar, tphase, &s_timeout) && ok;
+    pending = false;
+  }
   if (ok) ok = gemm_128x256(tm, sA, sB, &bar, phase, &s_timeout);
   __syncthreads();   // every thread past the MMA wait: sB may now hold dZ1
   float* sdz = reinterpret_cast<float*>(sB);  // 128 x 256 FP32, 16-byte groups XOR-swizzled by row
@@ -366,54 +419,71 @@ __global__ void __launch_bounds__(TILE, 1) mlp_fused_kernel(FusedArgs a) {
 #pragma unroll
   for (int j = 0; j < MAXIN; ++j) gx[j] = 0.0f;
   if (ok) {
-    for (int c = 0; c < WID; c += 16) {
+    for (int c = cb; c < ce; c += 16) {
       float dh[16];
       tmem_row16(lane_base + c, dh);
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
         const int f = c + e;
-        float z = P[o.b1 + f];
-        for (int j = 0; j < in; ++j) z = fmaf(P[o.W1 + (int64_t)f * in + j], x[j], z);
+        float z = __ldg(P + o.b1 + f);
+        float w1[MAXIN];
+#pragma unroll
+        for (int j = 0; j < MAXIN; ++j) {
+          w1[j] = j < in ? __ldg(P + o.W1 + (int64_t)f * in + j) : 0.0f;
+          z = fmaf(w1[j], x[j], z);
+        }
         dh[e] *= gelu_prime_f(z);
         if (!a.train)
-          for (int j = 0; j < in; ++j) gx[j] = fmaf(dh[e], P[o.W1 + (int64_t)f * in + j], gx[j]);
+#pragma unroll
+          for (int j = 0; j < MAXIN; ++j) gx[j] = fmaf(dh[e], w1[j], gx[j]);
       }
       if (a.train) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int grp = ((c >> 2) + q) ^ (t & 7);
-          *reinterpret_cast<float4*>(sdz + t * WID + grp * 4) =
+          const int grp = ((c >> 2) + q) ^ (r & 7);
+          *reinterpret_cast<float4*>(sdz + r * WID + grp * 4) =
               make_float4(dh[4 * q], dh[4 * q + 1], dh[4 * q + 2], dh[4 * q + 3]);
         }
       }
     }
   }
-  if (!a.train && valid && a.dsdx)
-    for (int j = 0; j < in; ++j) a.dsdx[row * in + j] = gx[j];
+  if (!a.train) {
+    // ds/dx = dZ1 W1: the two halves' partial sums meet in shared memory
+    float* sgx = reinterpret_cast<float*>(sB);
+    if (hf == 1)
+#pragma unroll
+      for (int j = 0; j < MAXIN; ++j) sgx[r * MAXIN + j] = gx[j];
+    __syncthreads();
+    if (hf == 0 && valid && a.dsdx)
+#pragma unroll
+      for (int j = 0; j < MAXIN; ++j)
+        if (j < in) a.dsdx[row * in + j] = gx[j] + sgx[r * MAXIN + j];
+  }
   __syncthreads();
   // ---- per-tile partial sums (fixed order) ----
   if (a.train && ok) {
     float* part = a.part + (int64_t)blockIdx.x * po.stride;
-    for (int f = t; f < WID; f += TILE) {
+    for (int f = t; f < WID; f += MT) {
       part[po.dw4 + f] = ((red_w4[f] + red_w4[WID + f]) + red_w4[2 * WID + f]) + red_w4[3 * WID + f];
       part[po.db3 + f] = ((red_b3[f] + red_b3[WID + f]) + red_b3[2 * WID + f]) + red_b3[3 * WID + f];
       part[po.db2 + f] = ((red_b2[f] + red_b2[WID + f]) + red_b2[2 * WID + f]) + red_b2[3 * WID + f];
       float gw[MAXIN], gb = 0.0f;
 #pragma unroll
       for (int j = 0; j < MAXIN; ++j) gw[j] = 0.0f;
-      for (int r = 0; r < TILE; ++r) {
-        const float dz = sdz[r * WID + (((f >> 2) ^ (r & 7)) << 2) + (f & 3)];
+      for (int q = 0; q < TILE; ++q) {
+        const float dz = sdz[q * WID + (((f >> 2) ^ (q & 7)) << 2) + (f & 3)];
         gb += dz;
-        for (int j = 0; j < in; ++j) gw[j] = fmaf(dz, sX[r * MAXIN + j], gw[j]);
+#pragma unroll
+        for (int j = 0; j < MAXIN; ++j) gw[j] = fmaf(dz, sX[q * MAXIN + j], gw[j]);
       }
       part[po.db1 + f] = gb;
-      for (int j = 0; j < in; ++j) part[po.dW1 + f * in + j] = gw[j];
+#pragma unroll
+      for (int j = 0; j < MAXIN; ++j)
+        if (j < in) part[po.dW1 + f * in + j] = gw[j];
     }
-    if (t == 0) {
-      part[po.loss] = ((s_loss[0] + s_loss[1]) + s_loss[2]) + s_loss[3];
-    }
-    // db4 = sum of ds over the tile
-    float d4 = ds;
+    if (t == 0) part[po.loss] = ((s_loss[0] + s_loss[1]) + s_loss[2]) + s_loss[3];
+    // db4 = sum of ds over the tile (each row counted once, by warps 0-3)
+    float d4 = hf == 0 ? ds : 0.0f;
 #pragma unroll
     for (int sh = 16; sh > 0; sh >>= 1) d4 += __shfl_xor_sync(0xffffffffu, d4, sh);
     __syncthreads();
@@ -422,8 +492,9 @@ __global__ void __launch_bounds__(TILE, 1) mlp_fused_kernel(FusedArgs a) {
     if (t == 0) part[po.db4] = ((s_loss[0] + s_loss[1]) + s_loss[2]) + s_loss[3];
   }
   if (s_timeout && t == 0) atomicExch(a.timeout, 1);
-  // a timed-out wait: one more bounded wait for the MMAs still in flight
+  // a timed-out wait: one more bounded wait for the MMAs and copies in flight
   if (s_timeout) umma::mbar_wait(&bar, phase ^ 1u, kWait);
+  if (pending) stage_wait(&tbar, tphase, &s_timeout);
   umma::fence_before_sync();
   __syncthreads();
   if (warp == 0) umma::tmem_dealloc(tm, 512);
@@ -758,7 +829,7 @@ int enqueue_pass(sbv_mlp* h, const float* X, const float* tv, const int32_t* idx
     a.dz3t = base + (size_t)3 * WID * kpad;
     a.part = h->part;
   }
-  mlp_fused_kernel<<<(unsigned)tiles, TILE, fused_smem(), s>>>(a);
+  mlp_fused_kernel<<<(unsigned)tiles, MT, fused_smem(), s>>>(a);
   SBV_LAUNCH_CHECK(ctx, "mlp_fused_kernel");
   if (train) {
     WgradArgs w;
