@@ -59,7 +59,7 @@ __device__ void fwd_solve2(const float* A, int N, float* b1, float* b2) {
       float* b = (lane >> 4) ? b2 : b1;
       float v = 0.0f;
       if (r < nbk) {
-        const float* Li = A + tri(k0 + r, k0);  // row r of the tile inverse
+        const float* Li = A + trp(k0 + r, k0);  // row r of the tile inverse
         for (int c = 0; c <= r; ++c) v = fmaf(Li[c], b[k0 + c], v);
       }
       __syncwarp();
@@ -68,11 +68,22 @@ __device__ void fwd_solve2(const float* A, int N, float* b1, float* b2) {
     __syncthreads();
     for (int i = k1 + threadIdx.x; i < N; i += blockDim.x) {
       float s1 = 0.0f, s2 = 0.0f;
-      const float* Ai = A + tri(i, 0);
-      for (int k = k0; k < k1; ++k) {
-        const float x = Ai[k];
-        s1 = fmaf(x, b1[k], s1);
-        s2 = fmaf(x, b2[k], s2);
+      const float* Ai = A + trp(i, 0);
+      if (nbk == NB) {
+#pragma unroll
+        for (int k = 0; k < NB; k += 4) {
+          const float4 x = *(const float4*)(Ai + k0 + k);
+          const float4 p = *(const float4*)(b1 + k0 + k);
+          const float4 q = *(const float4*)(b2 + k0 + k);
+          s1 = fmaf(x.x, p.x, s1); s1 = fmaf(x.y, p.y, s1); s1 = fmaf(x.z, p.z, s1); s1 = fmaf(x.w, p.w, s1);
+          s2 = fmaf(x.x, q.x, s2); s2 = fmaf(x.y, q.y, s2); s2 = fmaf(x.z, q.z, s2); s2 = fmaf(x.w, q.w, s2);
+        }
+      } else {
+        for (int k = k0; k < k1; ++k) {
+          const float x = Ai[k];
+          s1 = fmaf(x, b1[k], s1);
+          s2 = fmaf(x, b2[k], s2);
+        }
       }
       b1[i] -= s1;
       b2[i] -= s2;
@@ -91,7 +102,7 @@ __device__ void bwd_solve2(const float* A, int N, float* b1, float* b2) {
       float* b = (lane >> 4) ? b2 : b1;
       float v = 0.0f;
       if (r < nbk)
-        for (int c = r; c < nbk; ++c) v = fmaf(A[tri(k0 + c, k0 + r)], b[k0 + c], v);
+        for (int c = r; c < nbk; ++c) v = fmaf(A[trp(k0 + c, k0 + r)], b[k0 + c], v);
       __syncwarp();
       if (r < nbk) b[k0 + r] = v;
     }
@@ -99,7 +110,7 @@ __device__ void bwd_solve2(const float* A, int N, float* b1, float* b2) {
     for (int i = threadIdx.x; i < k0; i += blockDim.x) {
       float s1 = 0.0f, s2 = 0.0f;
       for (int k = k0; k < k1; ++k) {
-        const float x = A[tri(k, i)];
+        const float x = A[trp(k, i)];
         s1 = fmaf(x, b1[k], s1);
         s2 = fmaf(x, b2[k], s2);
       }
@@ -169,7 +180,8 @@ loglik_mixed_kernel(MixedArgs P) {
   unsigned char* opnd = smem + lay.off_u;                 // BF16 panel pieces
   float4* part = (float4*)(smem + lay.off_u);             // residual partial sums
   float* A = GA ? P.gA + (size_t)blockIdx.x * lay.a_floats : (float*)(smem + lay.off_A);
-  __shared__ float tab_h[256], tab_l[256];
+  float* tab_h = (float*)(smem + lay.off_tab);   // covariance phase only
+  float* tab_l = tab_h + 256;
   __shared__ unsigned int s_item;
   __shared__ int s_fail;
   __shared__ double red[2 * MX_WARPS];
@@ -185,12 +197,13 @@ loglik_mixed_kernel(MixedArgs P) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned int total = PRED ? (unsigned int)P.nt : (unsigned int)(a.bc * a.B);
   const double log2pi = 1.8378770664093454836;
+  const int vs = (cap + 4) & ~3;   // vector stride, a multiple of four floats
   float* x0 = vec;
-  float* x0J = vec + (cap + 1);
-  float* r1 = vec + 2 * (cap + 1);
-  float* r2 = vec + 3 * (cap + 1);
-  float* ldiag = vec + 4 * (cap + 1);
-  float* idiag = vec + 5 * (cap + 1);
+  float* x0J = vec + vs;
+  float* r1 = vec + 2 * vs;
+  float* r2 = vec + 3 * vs;
+  float* ldiag = vec + 4 * vs;
+  float* idiag = vec + 5 * vs;
   float* c1 = (float*)(smem + lay.off_c);   // live during refinement only
   float* c2 = c1 + (cap + 1);
   // refinement steps: one for the likelihood (its quadratic forms are second
@@ -208,11 +221,9 @@ loglik_mixed_kernel(MixedArgs P) {
   // Well-conditioned blocks finish after one residual and one forward solve.
   constexpr double REF_TOL = 1e-6;
   __shared__ double s_qvar;   // x^T r of the full system minus that of J
+  __shared__ __align__(16) float s_col[2 * NB];   // column broadcast of the tile factorisation
+  float2* s_tile = (float2*)(smem + lay.off_stile);  // a diagonal tile's originals (factorisation)
 
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
-    tab_h[i] = C.tab_h[i];
-    tab_l[i] = C.tab_l[i];
-  }
   if (threadIdx.x == 0) s_timeout = 0;
   uint32_t tmem_base = 0, mma_phase = 0;
   if (TC) {
@@ -258,6 +269,10 @@ loglik_mixed_kernel(MixedArgs P) {
     const int64_t base = PRED ? 0 : a.ptr[blk];
     // ---- 1. gather and scale in double-float; centre on point 0
     if (threadIdx.x == 0) s_fail = 0;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+      tab_h[i] = C.tab_h[i];
+      tab_l[i] = C.tab_l[i];
+    }
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
       if (PRED && p == mb) {
         yv[p] = make_float2(0.0f, 0.0f);  // the test point's observation is unknown
@@ -355,13 +370,13 @@ loglik_mixed_kernel(MixedArgs P) {
           K = df_mul(s2, df_matern(r, s, a.nu2, C, tab_h, tab_l));
         }
         // diagonal-tile entries start at 0 in A: A accumulates minus the updates
-        A[tri(i, j)] = (i / NB == j / NB) ? 0.0f : K.h;
+        A[trp(i, j)] = (i / NB == j / NB) ? 0.0f : K.h;
         S[(size_t)j * N + i] = make_float2(K.h, K.l);
         S[(size_t)i * N + j] = make_float2(K.h, K.l);
         j += blockDim.x;
         while (j > i) { j -= i + 1; ++i; }
       }
-      for (int p = threadIdx.x; p < N; p += blockDim.x) A[tri(N, p)] = yv[p].x;
+      for (int p = threadIdx.x; p < N; p += blockDim.x) A[trp(N, p)] = yv[p].x;
     }
     __syncthreads();
     // ---- 3. blocked Cholesky.  CUDA-core variant with look-ahead: while the
@@ -374,57 +389,98 @@ loglik_mixed_kernel(MixedArgs P) {
     // double-float original (scratch matrix) plus the accumulated FP32 updates
     // (held negated in A), one exact subtraction, then an FP32 factorisation
     // in registers; L, its diagonal and inverse diagonal are stored.
+    // stage_tile(kt), warp 0: asynchronous copies (cp.async, 8 bytes each) of
+    // tile kt's double-float originals, lower triangle, column-major 16 x 16,
+    // from the scratch matrix into s_tile.  Issued one panel ahead, right
+    // after the previous tile was factored, so that the scratch matrix's DRAM
+    // latency is off the critical path; factor_tile waits for them.
+    auto stage_tile = [&](const int kt) {
+      const int nt = min(kt + NB, N) - kt;
+      __syncwarp();   // the previous tile's reads of s_tile are done
+#pragma unroll
+      for (int e = lane; e < NB * NB; e += 32) {
+        const int c = e >> 4, r = e & 15;
+        if (r < nt && c <= r) {
+          const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s_tile + e);
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst),
+                       "l"(S + (size_t)(kt + c) * N + (kt + r)) : "memory");
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
     auto factor_tile = [&](const int kt) {
       const int nt = min(kt + NB, N) - kt;
       const int r = lane;
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      __syncwarp();
       float row[NB];
 #pragma unroll
       for (int c = 0; c < NB; ++c) {
-        float v = 0.0f;
+        // rows past the tile are padded with the identity, so that no update
+        // below needs a bound
+        float v = c == r ? 1.0f : 0.0f;
         if (r < nt && c <= r) {
-          const float2 k = S[(size_t)(kt + c) * N + (kt + r)];
-          const df s = two_sum(k.x, A[tri(kt + r, kt + c)]);
+          const float2 k = s_tile[c * NB + r];
+          const df s = two_sum(k.x, A[trp(kt + r, kt + c)]);
           v = __fadd_rn(s.h, __fadd_rn(s.l, k.y));
         }
         row[c] = v;
       }
+      // right-looking elimination; column c is broadcast through shared memory
+      // (double-buffered, four floats per load) instead of one shuffle per entry
       bool bad = false;
+      float rinv = 0.0f;   // 1 / L[r][r]
 #pragma unroll
       for (int c = 0; c < NB; ++c) {
-        if (c < nt) {
-          const float dcc = __shfl_sync(0xffffffffu, row[c], c);
-          bad |= !(dcc > 0.0f);
-          const float Lcc = sqrtf(fmaxf(dcc, 1e-30f));
-          const float inv = 1.0f / Lcc;
-          if (r == c) row[c] = Lcc;
-          if (r > c) row[c] *= inv;
+        float* cb = s_col + (c & 1) * NB;
+        if (r < NB) cb[r] = row[c];
+        __syncwarp();
+        const float dcc = cb[c];
+        bad |= !(dcc > 0.0f);
+        // one reciprocal square root gives both the pivot and its inverse
+        // (a few ulp: ~1e-8 per point of the log-determinant, random)
+        const float inv = rsqrtf(fmaxf(dcc, 1e-30f));
+        // a[r][c2] -= L[r][c] L[c2][c] = (a[r][c] / a[c][c]) a[c2][c]
+        const float t = r > c ? row[c] * (inv * inv) : 0.0f;
+        row[c] = r == c ? dcc * inv : row[c] * inv;
+        if (r == c) rinv = inv;
 #pragma unroll
-          for (int c2 = c + 1; c2 < NB; ++c2) {
-            const float v = __shfl_sync(0xffffffffu, row[c], c2);  // L[c2][c]
-            if (r >= c2 && c2 < nt) row[c2] = fmaf(-row[c], v, row[c2]);
-          }
+        for (int j = (c + 1) & ~3; j < NB; j += 4) {
+          const float4 q = *(const float4*)(cb + j);
+          const float qq[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (j + u > c) row[j + u] = fmaf(-t, qq[u], row[j + u]);
         }
       }
       if (r < nt) {
         float Lrr = 0.0f;
 #pragma unroll
         for (int c = 0; c < NB; ++c) {
-          if (c <= r) A[tri(kt + r, kt + c)] = row[c];
+          if (c <= r) A[trp(kt + r, kt + c)] = row[c];
           if (c == r) Lrr = row[c];
         }
         ldiag[kt + r] = Lrr;
-        idiag[kt + r] = 1.0f / Lrr;
+        idiag[kt + r] = rinv;
       }
       if (bad && lane == 0) s_fail = 1;
     };
     if (!TC) {
-      if (warp == 0) factor_tile(0);
+      if (warp == 0) {
+        stage_tile(0);
+        factor_tile(0);
+        if (NB < N) stage_tile(NB);
+      }
       __syncthreads();
     }
     for (int k0 = 0; k0 < N; k0 += NB) {
       const int k1 = min(k0 + NB, N), nbk = k1 - k0;
       if (TC) {
-        if (warp == 0) factor_tile(k0);
+        if (warp == 0) {
+          if (k0 == 0) stage_tile(0);
+          factor_tile(k0);
+          if (k1 < N) stage_tile(k1);
+        }
         __syncthreads();
       }
       if (s_fail) break;
@@ -433,24 +489,44 @@ loglik_mixed_kernel(MixedArgs P) {
       const int T = N + 1 - k1;  // trailing rows k1..N (the last one is y)
       for (int i = k1 + threadIdx.x; i <= N; i += blockDim.x) {
         float v[NB];
-        float* Ai = A + tri(i, 0) + k0;
+        float* Ai = A + trp(i, 0) + k0;   // 16-byte aligned (padded rows)
+        const bool full = nbk == NB;
+        if (full) {
 #pragma unroll
-        for (int c = 0; c < NB; ++c) v[c] = c < nbk ? Ai[c] : 0.0f;
+          for (int c = 0; c < NB; c += 4) {
+            const float4 q = *(const float4*)(Ai + c);
+            v[c] = q.x; v[c + 1] = q.y; v[c + 2] = q.z; v[c + 3] = q.w;
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < NB; ++c) v[c] = c < nbk ? Ai[c] : 0.0f;
+        }
 #pragma unroll
         for (int c = 0; c < NB; ++c) {
           if (c < nbk) {
-            const float* Lc = A + tri(k0 + c, k0);
+            // row c of the tile, four entries per (broadcast) load; the
+            // entries at and past the diagonal are read but not used
+            const float* Lc = A + trp(k0 + c, k0);
             float s = v[c];
 #pragma unroll
-            for (int c2 = 0; c2 < NB; ++c2)
-              if (c2 < c) s = fmaf(-v[c2], Lc[c2], s);
+            for (int c4 = 0; c4 < c; c4 += 4) {
+              const float4 q = *(const float4*)(Lc + c4);
+              const float l4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (c4 + u < c) s = fmaf(-v[c4 + u], l4[u], s);
+            }
             v[c] = s * idiag[k0 + c];
           }
         }
         const int row = i - k1;
+        if (full) {
+#pragma unroll
+          for (int c = 0; c < NB; c += 4) *(float4*)(Ai + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+        }
 #pragma unroll
         for (int c = 0; c < NB; ++c) {
-          if (c < nbk) Ai[c] = v[c];
+          if (!full && c < nbk) Ai[c] = v[c];
           if (TC) {
             const __nv_bfloat16 bh = __float2bfloat16_rn(v[c]);
             const float rr = v[c] - __bfloat162float(bh);           // exact
@@ -505,15 +581,20 @@ loglik_mixed_kernel(MixedArgs P) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(rr[p], cc[q], acc[p][q]);
             }
+            // one aligned float4 read-modify-write per block row; in a
+            // diagonal block the entries past the diagonal land in the row's
+            // padding, which nothing reads
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
               const int ii = k1 + 4 * bi + p;
               if (ii > N) continue;
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const int jj = k1 + 4 * bj + q;
-                if (jj <= ii && jj < N) A[tri(ii, jj)] -= acc[p][q];
-              }
+              float4* a4 = (float4*)(A + trp(ii, k1 + 4 * bj));
+              float4 w = *a4;
+              w.x -= acc[p][0];
+              w.y -= acc[p][1];
+              w.z -= acc[p][2];
+              w.w -= acc[p][3];
+              *a4 = w;
             }
             if (l + stride >= lend) break;   // before walking (bi, bj) that far
             bj += stride;
@@ -523,6 +604,7 @@ loglik_mixed_kernel(MixedArgs P) {
         if (warp == 0 && k1 < N) {
           __syncwarp();
           factor_tile(k1);
+          if (k1 + NB < N) stage_tile(k1 + NB);
         }
       } else {
         // trailing update on the tensor cores: for each 128-row tile of P and
@@ -567,7 +649,7 @@ loglik_mixed_kernel(MixedArgs P) {
 #pragma unroll
                   for (int e = 0; e < 16; ++e) {
                     const int jj = k1 + c0 + cc + e;
-                    if (jj <= ii && jj < N) A[tri(ii, jj)] = (A[tri(ii, jj)] - ds[e]) - dv[e];
+                    if (jj <= ii && jj < N) A[trp(ii, jj)] = (A[trp(ii, jj)] - ds[e]) - dv[e];
                   }
                 }
               }
@@ -585,6 +667,8 @@ loglik_mixed_kernel(MixedArgs P) {
       }
       __syncthreads();
     }
+    // a failed or cut-short factorisation can leave a staged tile in flight
+    asm volatile("cp.async.wait_all;" ::: "memory");
     if (s_fail) {
       if (threadIdx.x == 0) {
         const int code = s_fail == 2 ? SBV_ETIMEOUT : SBV_ENOTSPD;
@@ -609,10 +693,10 @@ loglik_mixed_kernel(MixedArgs P) {
     // the test point's row of L, which lies in the last diagonal tile
     // (-> Sigma_JJ^-1 Sigma_J*); both vanish beyond J.
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
-      const float w = A[tri(N, p)];
+      const float w = A[trp(N, p)];
       if (PRED) {
         x0[p] = p < mb ? w : 0.0f;
-        x0J[p] = p < mb ? A[tri(mb, p)] : 0.0f;
+        x0J[p] = p < mb ? A[trp(mb, p)] : 0.0f;
       } else {
         x0[p] = w;
         x0J[p] = p < mb ? w : 0.0f;
@@ -626,7 +710,7 @@ loglik_mixed_kernel(MixedArgs P) {
       float Lr[NB], Xr[NB];
 #pragma unroll
       for (int c = 0; c < NB; ++c) {
-        Lr[c] = (r < nbk && c <= r) ? A[tri(k0 + r, k0 + c)] : 0.0f;
+        Lr[c] = (r < nbk && c <= r) ? A[trp(k0 + r, k0 + c)] : 0.0f;
         Xr[c] = (c == r) ? 1.0f : 0.0f;
       }
 #pragma unroll
@@ -646,7 +730,7 @@ loglik_mixed_kernel(MixedArgs P) {
       if (r < nbk) {
 #pragma unroll
         for (int c = 0; c < NB; ++c)
-          if (c <= r) A[tri(k0 + r, k0 + c)] = Xr[c];
+          if (c <= r) A[trp(k0 + r, k0 + c)] = Xr[c];
       }
     }
     __syncthreads();
@@ -664,7 +748,20 @@ loglik_mixed_kernel(MixedArgs P) {
     // warps: (32-row group, column chunk) tasks
     {
       const int G = (N + 31) / 32;
-      const int CH = max(1, MX_WARPS / G);
+      // column chunks: the count (within the partial-sum buffer) that
+      // minimises the columns the busiest warp walks
+      int CH = 1;
+      {
+        const int chmax = max(1, min(16, lay.part_cap / max(N, 1)));
+        int best = G * N;
+        for (int ch = 1; ch <= chmax; ++ch) {
+          const int cols = ((G * ch + MX_WARPS - 1) / MX_WARPS) * ((N + ch - 1) / ch);
+          if (cols < best) {
+            best = cols;
+            CH = ch;
+          }
+        }
+      }
       const int chunk = (N + CH - 1) / CH;
       for (int task = warp; task < G * CH; task += MX_WARPS) {
         const int g = task / CH, c = task % CH;
@@ -673,9 +770,19 @@ loglik_mixed_kernel(MixedArgs P) {
         float h1 = 0.0f, l1 = 0.0f, h2 = 0.0f, l2 = 0.0f;
         if (i < N) {
           const bool inJ = i < mb;
-#pragma unroll 4
-          for (int j = j0; j < j1; ++j) {
-            const float2 s = S[(size_t)j * N + i];
+          // sixteen columns of the scratch matrix in flight per lane, then
+          // their products in column order
+          constexpr int RB = 16;
+          for (int jb = j0; jb < j1; jb += RB) {
+          float2 sv[RB];
+#pragma unroll
+          for (int u = 0; u < RB; ++u)
+            sv[u] = jb + u < j1 ? S[(size_t)(jb + u) * N + i] : make_float2(0.0f, 0.0f);
+#pragma unroll
+          for (int u = 0; u < RB; ++u) {
+            const int j = jb + u;
+            if (j >= j1) break;
+            const float2 s = sv[u];
             const float xj = x0[j];
             const float p = __fmul_rn(s.x, xj);
             float pe = __fmaf_rn(s.x, xj, -p);
@@ -694,6 +801,7 @@ loglik_mixed_kernel(MixedArgs P) {
               h2 = q2.h;
               l2 = __fadd_rn(l2, __fadd_rn(q2.l, pe2));
             }
+          }
           }
           part[(size_t)c * N + i] = make_float4(h1, l1, h2, l2);
         }
@@ -859,6 +967,8 @@ static int mixed_occupancy(sbv_ctx* ctx, int threads, bool tc, bool pred, bool g
 // matches (precision, prediction mode, capacity, d), else 256 threads and as
 // many CTAs per SM (<= 2) as shared memory allows.
 // ---------------------------------------------------------------------------
+static int mixed_static_smem(sbv_ctx* ctx, size_t* out);
+
 int mixed_plan(sbv_ctx* ctx, int nmax, int d, int precision, bool pred, int64_t items,
                MixedPlan* o) {
   const bool tc = precision == SBV_PREC_MIXED_BF16;
@@ -866,7 +976,8 @@ int mixed_plan(sbv_ctx* ctx, int nmax, int d, int precision, bool pred, int64_t 
   o->tc = tc;
   o->pred = pred;
   o->lay = mixed_layout(ncap, d, tc);
-  const size_t static_smem = 2 * 256 * 4 + 1024;
+  size_t static_smem = 0;
+  if (int st0 = mixed_static_smem(ctx, &static_smem)) return st0;
   if (o->lay.bytes + static_smem > ctx->smem_optin) o->lay = mixed_layout(ncap, d, tc, true);
   if (o->lay.bytes + static_smem > ctx->smem_optin)
     return fail(ctx, SBV_EUNSUPPORTED,
@@ -935,6 +1046,38 @@ static int allow_smem(sbv_ctx* ctx, int bytes) {
 }
 
 static bool g_mixed_ready[64];
+static size_t g_mixed_static[64];
+
+template <int THREADS, bool TC, bool PRED>
+static size_t static_smem_of() {
+  cudaFuncAttributes a{}, b{};
+  if (cudaFuncGetAttributes(&a, loglik_mixed_kernel<THREADS, TC, PRED, false>) != cudaSuccess ||
+      cudaFuncGetAttributes(&b, loglik_mixed_kernel<THREADS, TC, PRED, true>) != cudaSuccess)
+    return 0;
+  return std::max(a.sharedSizeBytes, b.sharedSizeBytes);
+}
+
+// The largest static shared memory of the variants (the tables, the staged
+// diagonal tile, the reduction buffers), queried once per device.
+static int mixed_static_smem(sbv_ctx* ctx, size_t* out) {
+  const int dev = ctx->device;
+  if (dev < 64 && g_mixed_static[dev]) {
+    *out = g_mixed_static[dev];
+    return SBV_OK;
+  }
+  const size_t v[8] = {static_smem_of<256, false, false>(), static_smem_of<256, true, false>(),
+                       static_smem_of<256, false, true>(),  static_smem_of<256, true, true>(),
+                       static_smem_of<512, false, false>(), static_smem_of<512, true, false>(),
+                       static_smem_of<512, false, true>(),  static_smem_of<512, true, true>()};
+  size_t m = 0;
+  for (size_t x : v) {
+    if (x == 0) return fail(ctx, SBV_ECUDA, "mixed path: cudaFuncGetAttributes failed");
+    m = std::max(m, x);
+  }
+  if (dev < 64) g_mixed_static[dev] = m;
+  *out = m;
+  return SBV_OK;
+}
 
 // Once per device: upload the double-float constants and allow every variant
 // the largest dynamic shared memory, so that later launches (and launches
@@ -943,7 +1086,9 @@ int mixed_prepare(sbv_ctx* ctx) {
   int st = 0;
   if (ctx->device < 64 && g_mixed_ready[ctx->device]) return SBV_OK;
   if ((st = upload_df_consts(ctx))) return st;
-  const int b = (int)ctx->smem_optin - (2 * 256 * 4 + 1024);
+  size_t stat = 0;
+  if ((st = mixed_static_smem(ctx, &stat))) return st;
+  const int b = (int)(ctx->smem_optin - stat);
   if ((st = allow_smem<256, false, false>(ctx, b)) || (st = allow_smem<256, true, false>(ctx, b)) ||
       (st = allow_smem<256, false, true>(ctx, b)) || (st = allow_smem<256, true, true>(ctx, b)) ||
       (st = allow_smem<512, false, false>(ctx, b)) || (st = allow_smem<512, true, false>(ctx, b)) ||
