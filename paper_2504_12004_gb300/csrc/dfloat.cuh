@@ -110,8 +110,10 @@ __device__ __forceinline__ df df_exp_neg(df r, const DfConsts& c, const float* t
   one_m_g = fast_two_sum(one_m_g.h, __fsub_rn(one_m_g.l, g.l));
   df e = df_add(one_m_g, term);
   e = df_mul(e, df{tab_h[k & 255], tab_l[k & 255]});
-  int sh = -(k >> 8);
-  return {ldexpf(e.h, sh), ldexpf(e.l, sh)};
+  // 2^-(k >> 8) is a normal float (k >> 8 <= 122 for r <= 85): an exact
+  // power-of-two multiply, rounded once like ldexpf
+  const float sc = __int_as_float((127 - (k >> 8)) << 23);
+  return {__fmul_rn(e.h, sc), __fmul_rn(e.l, sc)};
 }
 
 // Matern correlation M_nu(r) for nu = nu2/2 (closed forms), r and s = r^2 in double-float.

@@ -332,11 +332,15 @@ loglik_mixed_kernel(MixedArgs P) {
     }
     __syncthreads();
     {
+      // heads become integer grid coordinates (|k| < 2^22), so that squared
+      // head differences sum exactly in 64-bit integers
       const float g = s_grid, ig = 1.0f / g;  // powers of two: exact scaling
+      int* vk = (int*)vh;
       for (int e = threadIdx.x; e < N * d; e += blockDim.x) {
         const float h = vh[e];
-        const float hq = rintf(h * ig) * g;   // on the grid, exact
-        vh[e] = hq;
+        const float kq = rintf(h * ig);
+        const float hq = kq * g;              // on the grid, exact
+        vk[e] = (int)kq;
         vl[e] = __fadd_rn(__fsub_rn(h, hq), vl[e]);  // h - hq is exact
       }
     }
@@ -346,6 +350,8 @@ loglik_mixed_kernel(MixedArgs P) {
       const df s2 = {th.s2_h, th.s2_l};
       const df diag = {th.diag_h, th.diag_l};
       const int npair = N * (N + 1) / 2;
+      const int* vk = (const int*)vh;
+      const float g = s_grid, g2x = 2.0f * g, gg = g * g;
       int i = 0, j = threadIdx.x;
       while (j > i) { j -= i + 1; ++i; }
       for (int l = threadIdx.x; l < npair; l += blockDim.x) {
@@ -353,19 +359,21 @@ loglik_mixed_kernel(MixedArgs P) {
         if (i == j) {
           K = diag;
         } else {
-          float sh = 0.0f, sl = 0.0f;
+          // |x_i - x_j|^2 = g^2 sum dk^2 (exact, int64) + sum (2 dh dl + dl^2)
+          long long acc = 0;
+          float pe = 0.0f;
           for (int t = 0; t < d; ++t) {
-            const float dh = __fsub_rn(vh[t * N + i], vh[t * N + j]);  // exact
+            const int dk = vk[t * N + i] - vk[t * N + j];   // |dk| < 2^23
+            acc += (long long)dk * dk;
             const float dl = __fsub_rn(vl[t * N + i], vl[t * N + j]);
-            const float p = __fmul_rn(dh, dh);
-            float pe = __fmaf_rn(dh, dh, -p);
-            pe = __fmaf_rn(2.0f * dh, dl, pe);
-            pe = __fmaf_rn(dl, dl, pe);
-            const df q = two_sum(sh, p);
-            sh = q.h;
-            sl = __fadd_rn(sl, __fadd_rn(q.l, pe));
+            const float dh2 = __fmul_rn((float)dk, g2x);   // 2 dh, exact
+            pe = __fmaf_rn(dl, dl, __fmaf_rn(dh2, dl, pe));
           }
-          const df s = fast_two_sum(sh, sl);
+          // acc -> head + remainder (exact but for the last rounding, 2^-48
+          // relative), scaled by the power of two g^2
+          const float ah = __ll2float_rn(acc);
+          const float al = __ll2float_rn(acc - __float2ll_rz(ah));
+          const df s = two_sum(__fmul_rn(ah, gg), __fadd_rn(__fmul_rn(al, gg), pe));
           const df r = df_sqrt(s);
           K = df_mul(s2, df_matern(r, s, a.nu2, C, tab_h, tab_l));
         }
@@ -464,6 +472,48 @@ loglik_mixed_kernel(MixedArgs P) {
         idiag[kt + r] = rinv;
       }
       if (bad && lane == 0) s_fail = 1;
+    };
+    // invert_tile(k0), one warp, lane r = row r: the tile's L is replaced in
+    // place by L^{-1}, row by row (forward substitution).  Row c is final
+    // once rows 0..c-1 are applied; lane c scales and stores it (16-byte
+    // aligned rows, zeros past the diagonal land in the row's padding) and
+    // the rows below read it back as broadcast float4 loads.  Only the
+    // triangle q <= c is touched.
+    auto invert_tile = [&](const int k0) {
+      const int nbk = min(NB, N - k0);
+      const int r = lane;
+      float Lr[NB], Xr[NB];
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        Lr[c] = (r < nbk && c <= r) ? A[trp(k0 + r, k0 + c)] : 0.0f;
+        Xr[c] = (c == r) ? 1.0f : 0.0f;
+      }
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        if (c < nbk) {
+          float* Xc = A + trp(k0 + c, k0);
+          if (r == c) {
+            const float ic = idiag[k0 + c];
+#pragma unroll
+            for (int q = 0; q <= c; ++q) Xr[q] *= ic;
+#pragma unroll
+            for (int q4 = 0; q4 <= c; q4 += 4)
+              *(float4*)(Xc + q4) = make_float4(Xr[q4], Xr[q4 + 1], Xr[q4 + 2], Xr[q4 + 3]);
+          }
+          __syncwarp();
+          if (r > c) {
+#pragma unroll
+            for (int q4 = 0; q4 <= c; q4 += 4) {
+              const float4 x = *(const float4*)(Xc + q4);
+              const float x4[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (q4 + u <= c) Xr[q4 + u] = fmaf(-Lr[c], x4[u], Xr[q4 + u]);
+            }
+          }
+        }
+      }
+      __syncwarp();
     };
     if (!TC) {
       if (warp == 0) {
@@ -703,37 +753,8 @@ loglik_mixed_kernel(MixedArgs P) {
       }
     }
     __syncthreads();
-    // ---- 4. diagonal tiles -> their inverses (one warp per tile, lane = row)
-    for (int k0 = warp * NB; k0 < N; k0 += MX_WARPS * NB) {
-      const int nbk = min(NB, N - k0);
-      const int r = lane;
-      float Lr[NB], Xr[NB];
-#pragma unroll
-      for (int c = 0; c < NB; ++c) {
-        Lr[c] = (r < nbk && c <= r) ? A[trp(k0 + r, k0 + c)] : 0.0f;
-        Xr[c] = (c == r) ? 1.0f : 0.0f;
-      }
-#pragma unroll
-      for (int c = 0; c < NB; ++c) {
-        if (c < nbk) {
-          if (r == c) {
-#pragma unroll
-            for (int q = 0; q < NB; ++q) Xr[q] *= idiag[k0 + c];
-          }
-#pragma unroll
-          for (int q = 0; q < NB; ++q) {
-            const float xc = __shfl_sync(0xffffffffu, Xr[q], c);
-            if (r > c) Xr[q] = fmaf(-Lr[c], xc, Xr[q]);
-          }
-        }
-      }
-      if (r < nbk) {
-#pragma unroll
-        for (int c = 0; c < NB; ++c)
-          if (c <= r) A[trp(k0 + r, k0 + c)] = Xr[c];
-      }
-    }
-    __syncthreads();
+    // ---- 4. diagonal tiles -> their inverses (one warp per tile)
+    for (int k0 = warp * NB; k0 < N; k0 += MX_WARPS * NB) invert_tile(k0);
     __syncthreads();
     bwd_solve2(A, N, x0, x0J);
     for (int p = threadIdx.x; p < N; p += blockDim.x) {
