@@ -40,7 +40,9 @@ L2_BYTES = 129 * 1024 * 1024
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # FP64 peak: 1.25 TFLOP/s nominal for GB300 (a DFMA probe measured 1.19-1.20)
 FP64_PEAK_TFLOPS = 1.25
-KERNEL_SRC = os.path.join(ROOT, "paper_2504_12004_gb300", "csrc", "loglik_mixed.cu")
+# the sources of the mixed block kernel (the recorded traffic is valid for these)
+KERNEL_SRC = [os.path.join(ROOT, "paper_2504_12004_gb300", "csrc", f)
+              for f in ("loglik_mixed.cu", "mixed.cuh", "dfloat.cuh", "block_common.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "loglik_mixed_sine10d_traffic.txt")
 
 
@@ -160,9 +162,12 @@ def kernel_pairs(ptr: np.ndarray, cnt: np.ndarray) -> float:
     return float(np.sum(N * (N + 1) / 2))
 
 
-def source_hash(path: str) -> str:
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def source_hash(paths) -> str:
+    h = hashlib.sha256()
+    for path in paths:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def recorded_traffic(workload: str):

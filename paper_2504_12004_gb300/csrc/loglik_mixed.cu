@@ -332,15 +332,11 @@ loglik_mixed_kernel(MixedArgs P) {
     }
     __syncthreads();
     {
-      // heads become integer grid coordinates (|k| < 2^22), so that squared
-      // head differences sum exactly in 64-bit integers
       const float g = s_grid, ig = 1.0f / g;  // powers of two: exact scaling
-      int* vk = (int*)vh;
       for (int e = threadIdx.x; e < N * d; e += blockDim.x) {
         const float h = vh[e];
-        const float kq = rintf(h * ig);
-        const float hq = kq * g;              // on the grid, exact
-        vk[e] = (int)kq;
+        const float hq = rintf(h * ig) * g;   // on the grid, exact
+        vh[e] = hq;
         vl[e] = __fadd_rn(__fsub_rn(h, hq), vl[e]);  // h - hq is exact
       }
     }
@@ -350,8 +346,6 @@ loglik_mixed_kernel(MixedArgs P) {
       const df s2 = {th.s2_h, th.s2_l};
       const df diag = {th.diag_h, th.diag_l};
       const int npair = N * (N + 1) / 2;
-      const int* vk = (const int*)vh;
-      const float g = s_grid, g2x = 2.0f * g, gg = g * g;
       int i = 0, j = threadIdx.x;
       while (j > i) { j -= i + 1; ++i; }
       for (int l = threadIdx.x; l < npair; l += blockDim.x) {
@@ -359,21 +353,19 @@ loglik_mixed_kernel(MixedArgs P) {
         if (i == j) {
           K = diag;
         } else {
-          // |x_i - x_j|^2 = g^2 sum dk^2 (exact, int64) + sum (2 dh dl + dl^2)
-          long long acc = 0;
-          float pe = 0.0f;
+          float sh = 0.0f, sl = 0.0f;
           for (int t = 0; t < d; ++t) {
-            const int dk = vk[t * N + i] - vk[t * N + j];   // |dk| < 2^23
-            acc += (long long)dk * dk;
+            const float dh = __fsub_rn(vh[t * N + i], vh[t * N + j]);  // exact
             const float dl = __fsub_rn(vl[t * N + i], vl[t * N + j]);
-            const float dh2 = __fmul_rn((float)dk, g2x);   // 2 dh, exact
-            pe = __fmaf_rn(dl, dl, __fmaf_rn(dh2, dl, pe));
+            const float p = __fmul_rn(dh, dh);
+            float pe = __fmaf_rn(dh, dh, -p);
+            pe = __fmaf_rn(2.0f * dh, dl, pe);
+            pe = __fmaf_rn(dl, dl, pe);
+            const df q = two_sum(sh, p);
+            sh = q.h;
+            sl = __fadd_rn(sl, __fadd_rn(q.l, pe));
           }
-          // acc -> head + remainder (exact but for the last rounding, 2^-48
-          // relative), scaled by the power of two g^2
-          const float ah = __ll2float_rn(acc);
-          const float al = __ll2float_rn(acc - __float2ll_rz(ah));
-          const df s = two_sum(__fmul_rn(ah, gg), __fadd_rn(__fmul_rn(al, gg), pe));
+          const df s = fast_two_sum(sh, sl);
           const df r = df_sqrt(s);
           K = df_mul(s2, df_matern(r, s, a.nu2, C, tab_h, tab_l));
         }
