@@ -174,7 +174,11 @@ int sbv_set_knn_mode(sbv_ctx* ctx, int32_t mode);
  *
  *   X, dtype, n, d     device points (unscaled; the kernel ranges come from theta)
  *   y                  device, n doubles, observations
- *   ptr, pts           device, block CSR from sbv_blocking (bc blocks)
+ *   ptr, pts           device, block CSR from sbv_blocking (bc blocks); the
+ *                      offsets in ptr are absolute indices into pts, so a
+ *                      contiguous range of blocks [lo, hi) is evaluated by
+ *                      passing ptr + lo, nbr + lo * m, cnt + lo and bc = hi - lo
+ *                      (one rank's share of an evaluation: Alg. 1 Step 5)
  *   nbr, cnt           device, neighbours from sbv_knn (row stride m)
  *   nmax               largest m_i + bs_i over the blocks, or 0: the call then
  *                      computes it (one small kernel and a device-to-host read
