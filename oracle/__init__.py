@@ -16,6 +16,9 @@ Modules
             with an emulation of the GPU's BF16 operand rounding.
   mle    -- maximum-likelihood estimation over log theta (library optimiser),
             with the scale-family closed form used as a pin.
+  grad   -- d l / d theta of the block terms (Gaussian log-density derivative
+            of the block conditional, dense inverses and traces), pinned by
+            central differences of sbv.block_loglik and a closed form.
 
 Parity status: every function is pinned by a test in tests/test_oracle_*.py
 except the blocking trajectory itself (RAC anchors, Lloyd iterations, block
