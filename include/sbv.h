@@ -216,6 +216,37 @@ int sbv_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y,
                void* stream);
 
 /*
+ * sbv_loglik_grad -- the FP64 log-likelihood of sbv_loglik together with its
+ * gradient with respect to theta = (sigma^2, tau^2, beta_1..beta_d), for B
+ * parameter rows (the "gradient quantities" handed to the optimiser, Sec. 6).
+ *
+ * Arguments as sbv_loglik (FP64 arithmetic; no precision argument), plus
+ *   grad               device, B x (2+d) doubles out: d l(theta_b) / d theta_k
+ *                      (natural parameters, not their logarithms)
+ *   block_grads        device, B x bc x (2+d) doubles out (or NULL):
+ *                      d l_{b,i} / d theta_k
+ * For block i, with S = J_i u B_i and either Gaussian system (S, and J_i),
+ * d log N(y; 0, Sigma)/d theta_k = 1/2 x^T dSigma_k x - 1/2 tr(Sigma^-1 dSigma_k),
+ * x = Sigma^-1 y; l_{b,i} is the S density minus the J_i one.  Derivatives of
+ * the covariance: dK/dsigma^2 = M_nu(r), dK/dtau^2 = [same point],
+ * dK/dbeta_t = sigma^2 h_nu(r) u_t^2 / beta_t with u_t = (x_at - x_bt)/beta_t and
+ * h_nu = -M_nu'(r)/r (nu = 1/2: e^-r/r, 0 at r = 0; 3/2: e^-r; 5/2: (1+r)e^-r/3;
+ * 7/2: (3+3r+r^2)e^-r/15).  The block terms (ll, block_terms) are the same
+ * numbers sbv_loglik returns in FP64, bit for bit.  Sums over blocks are
+ * fixed-order trees (repeatable).  Each item costs about three times the FP64
+ * likelihood (the B rows of L^-1 by one backward substitution with bs + 2
+ * right-hand sides, then one pass over the pairs).
+ * Errors: as sbv_loglik (SBV_EINVAL, SBV_EUNSUPPORTED, SBV_ENOMEM,
+ * SBV_ECUDA); a block that is not positive definite gets NaN term and
+ * gradient and status SBV_ENOTSPD.
+ */
+int sbv_loglik_grad(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n,
+                    int32_t d, const int64_t* ptr, const int32_t* pts, const int32_t* nbr,
+                    const int32_t* cnt, int64_t bc, int32_t m, int32_t nmax,
+                    const double* theta, int32_t B, int32_t nu2, double* ll, double* grad,
+                    double* block_terms, double* block_grads, int32_t* status, void* stream);
+
+/*
  * sbv_sync_status -- wait for `stream`, then report whether any sbv_loglik or
  * sbv_predict kernel since the previous call met a non-positive-definite
  * matrix (SBV_ENOTSPD, message names the first block/test point) or a CUDA

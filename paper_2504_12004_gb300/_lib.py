@@ -74,6 +74,8 @@ SIGNATURES = {
                           _P, _P, _P]),
     "sbv_loglik": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64, _I32,
                              _I32, _P, _I32, _I32, _I32, _P, _P, _P, _P]),
+    "sbv_loglik_grad": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64, _I32,
+                                  _I32, _P, _I32, _I32, _P, _P, _P, _P, _P, _P]),
     "sbv_sync_status": (C.c_int, [_P, _P]),
     "sbv_set_knn_mode": (C.c_int, [_P, _I32]),
     "sbv_predict": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _I64, _P, _I32, _P,
@@ -265,6 +267,30 @@ class Context:
                                  _ptr(status), _stream(stream))
         self._check(rc)
         return ll
+
+    def sbv_loglik_grad(self, X, y, ptr, pts, nbr, cnt, theta, nu2: int = 5, ll=None, grad=None,
+                        block_terms=None, block_grads=None, status=None, stream=None, nmax: int = 0):
+        """Enqueue the FP64 log-likelihood and its gradient in theta for every row;
+        returns the device tensors (ll (B), grad (B x (2+d)))."""
+        X = _dev(X, None, "X")
+        n, d = X.shape
+        bc = cnt.numel()
+        m = nbr.shape[1] if nbr.dim() == 2 else 0
+        th = _host_f64(theta, "theta").reshape(-1, 2 + d)
+        B = th.shape[0]
+        if ll is None:
+            ll = torch.empty(B, dtype=torch.float64, device=X.device)
+        if grad is None:
+            grad = torch.empty(B, 2 + d, dtype=torch.float64, device=X.device)
+        nbr_c = _dev(nbr.contiguous() if nbr.stride(0) != m else nbr, torch.int32, "nbr")
+        rc = self.lib.sbv_loglik_grad(self.h, _ptr(X), _xdtype(X), _ptr(_dev(y, torch.float64, "y")),
+                                      n, d, _ptr(_dev(ptr, torch.int64, "ptr")),
+                                      _ptr(_dev(pts, torch.int32, "pts")), _ptr(nbr_c),
+                                      _ptr(_dev(cnt, torch.int32, "cnt")), bc, m, int(nmax), _ptr(th),
+                                      B, nu2, _ptr(ll), _ptr(grad), _ptr(block_terms),
+                                      _ptr(block_grads), _ptr(status), _stream(stream))
+        self._check(rc)
+        return ll, grad
 
     def sbv_autotune(self, X, y, ptr, pts, nbr, cnt, theta, nu2: int = 5, precision="mixed",
                      nmax: int = 0, stream=None):

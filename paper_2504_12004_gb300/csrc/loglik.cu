@@ -420,6 +420,302 @@ int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t 
 }
 
 // ---------------------------------------------------------------------------
+// Gradient of the block terms with respect to theta = (sigma^2, tau^2,
+// beta_1..beta_d), FP64 (the "gradient quantities" of Sec. 6).  For either
+// Gaussian system (joint S = J u B, and J), with x = Sigma^{-1} y,
+//   d log N(y; 0, Sigma) / d theta_k = 1/2 x^T dSigma_k x - 1/2 tr(Sigma^{-1} dSigma_k),
+// and l_i is the joint log-density minus the J one.  From the item's factor L:
+//   * x = L^{-T} w and x_J = L_JJ^{-T} w_J (= L^{-T} (w_J, 0) restricted to J),
+//   * Sigma^{-1} - [Sigma_JJ^{-1}, 0; 0, 0] = Z_B^T Z_B, Z_B the B rows of L^{-1},
+// all from one backward substitution with L^T over bs + 2 right-hand sides
+// (unit vectors e_t for t in B, w, (w_J, 0)).  Then one pass over the pairs
+// (i >= j) adds  c_ij dSigma_ij,k  with
+//   c_ij = (2 - [i = j]) (1/2 (x_i x_j - xJ_i xJ_j) - 1/2 (Z_B^T Z_B)_ij),
+//   dSigma/dsigma^2 = M(r), dSigma/dtau^2 = [i = j],
+//   dSigma/dbeta_t = sigma^2 h(r) u_t^2 / beta_t,  h = -M'(r) / r,
+// u_t the scaled coordinate difference, r = |u|.
+// ---------------------------------------------------------------------------
+constexpr int GR_CHUNK = 16;   // gradient components accumulated per pass over the pairs
+
+struct GradArgs {
+  double* gterms;      // B x bc x (2 + d): d l_{b,i} / d theta_k
+  double* zt;          // per CTA: N x (bs + 2) right-hand sides, row-major
+  size_t zt_stride;    // doubles per CTA slice (ncap x (ncap + 2))
+};
+
+// -M'(r) / r for the closed-form Matern correlations (0 at r = 0 for nu = 1/2,
+// where every u_t is 0 as well).
+__device__ __forceinline__ double h_nu64(double r, int nu2) {
+  const double e = exp(-r);
+  switch (nu2) {
+    case 1: return r > 0.0 ? e / r : 0.0;
+    case 3: return e;
+    case 5: return (1.0 + r) * e * (1.0 / 3.0);
+    default: return fma(r, r + 3.0, 3.0) * e * (1.0 / 15.0);
+  }
+}
+
+__global__ void __launch_bounds__(LL_THREADS)
+loglik_grad_fp64_kernel(LoglikArgs a, GradArgs g) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ double s_scalar;
+  __shared__ int s_flag;
+  __shared__ unsigned int s_item;
+  __shared__ double red[LL_THREADS / 32];
+  __shared__ double gred[LL_THREADS / 32][GR_CHUNK];
+  const int d = a.d, p = d + 2;
+  const int ustride = a.ncap + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double* u = sm;                               // d x (ncap+1)
+  double* yv = u + (size_t)d * ustride;         // ncap+1
+  double* A = a.gmat ? a.gmat + (size_t)blockIdx.x * a.gmat_stride : yv + ustride;
+  double* Zt = g.zt + (size_t)blockIdx.x * g.zt_stride;
+  const unsigned int total = (unsigned int)(a.bc * a.B);
+  const double log2pi = 1.8378770664093454836;
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const unsigned int item = s_item;
+    if (item >= total) break;
+    const int th_i = (int)(item / a.bc);
+    const int64_t blk = (int64_t)(item % a.bc);
+    const ThetaDev& th = a.theta[th_i];
+    const int bs = (int)(a.ptr[blk + 1] - a.ptr[blk]);
+    const int mb = a.cnt[blk];
+    const int N = mb + bs;
+    double* gout = g.gterms + (size_t)item * p;
+    if (N > a.ncap) {
+      if (threadIdx.x == 0) {
+        a.terms[item] = nan;
+        if (a.status) a.status[item] = SBV_EUNSUPPORTED;
+        record_failure(a.dstat, SBV_EUNSUPPORTED, (int)blk, th_i);
+      }
+      for (int k = threadIdx.x; k < p; k += blockDim.x) gout[k] = nan;
+      __syncthreads();
+      continue;
+    }
+    gather_item(a, blk, mb, N, th, u, ustride, yv);
+    __syncthreads();
+    build_cov(u, ustride, d, N, th, a.nu2, yv, A);
+    if (threadIdx.x == 0) s_flag = 0;
+    __syncthreads();
+    const bool ok = chol_columns(A, N, N, &s_scalar, &s_flag);
+    double v = 0.0;
+    if (ok) {
+      for (int t = mb + threadIdx.x; t < N; t += blockDim.x) {
+        const double w = A[tri(N, t)];
+        v += 2.0 * log(A[tri(t, t)]) + w * w;
+      }
+    }
+    const double s = cta_sum(v, red);
+    if (threadIdx.x == 0) {
+      if (ok) {
+        a.terms[item] = -0.5 * ((double)bs * log2pi + s);
+        if (a.status) a.status[item] = 0;
+      } else {
+        a.terms[item] = nan;
+        if (a.status) a.status[item] = SBV_ENOTSPD;
+        record_failure(a.dstat, SBV_ENOTSPD, (int)blk, th_i);
+      }
+    }
+    if (!ok) {
+      for (int k = threadIdx.x; k < p; k += blockDim.x) gout[k] = nan;
+      __syncthreads();
+      continue;
+    }
+    // right-hand sides: columns q < bs the unit vectors e_{mb+q}, column bs
+    // w = L^{-1} y (row N of A), column bs+1 (w_J, 0)
+    const int nq = bs + 2;
+    for (int e = threadIdx.x; e < N * nq; e += blockDim.x) {
+      const int k = e / nq, q = e - k * nq;
+      double r0;
+      if (q < bs) r0 = (k == mb + q) ? 1.0 : 0.0;
+      else if (q == bs || k < mb) r0 = A[tri(N, k)];
+      else r0 = 0.0;
+      Zt[e] = r0;
+    }
+    __syncthreads();
+    // backward substitution with L^T for all right-hand sides: row c is final
+    // once rows c+1..N-1 are subtracted; then it is removed from rows 0..c-1
+    for (int c = N - 1; c >= 0; --c) {
+      const double inv = 1.0 / A[tri(c, c)];
+      for (int q = threadIdx.x; q < nq; q += blockDim.x) Zt[(size_t)c * nq + q] *= inv;
+      __syncthreads();
+      for (int e = threadIdx.x; e < c * nq; e += blockDim.x) {
+        const int k = e / nq, q = e - k * nq;
+        Zt[e] = fma(-A[tri(c, k)], Zt[(size_t)c * nq + q], Zt[e]);
+      }
+      __syncthreads();
+    }
+    // pass over the pairs, GR_CHUNK gradient components at a time
+    const int npair = N * (N + 1) / 2;
+    for (int k0 = 0; k0 < p; k0 += GR_CHUNK) {
+      double acc[GR_CHUNK];
+#pragma unroll
+      for (int c = 0; c < GR_CHUNK; ++c) acc[c] = 0.0;
+      int i = 0, j = threadIdx.x;
+      while (j > i) { j -= i + 1; ++i; }
+      for (int l = threadIdx.x; l < npair; l += blockDim.x) {
+        double r2 = 0.0;
+        for (int t = 0; t < d; ++t) {
+          const double df = u[t * ustride + i] - u[t * ustride + j];
+          r2 = fma(df, df, r2);
+        }
+        const double r = sqrt(r2);
+        const double* zi = Zt + (size_t)i * nq;
+        const double* zj = Zt + (size_t)j * nq;
+        double D = 0.0;
+        for (int q = 0; q < bs; ++q) D = fma(zi[q], zj[q], D);
+        double wgt = 0.5 * (zi[bs] * zj[bs] - zi[bs + 1] * zj[bs + 1]) - 0.5 * D;
+        if (i != j) wgt *= 2.0;
+        const double Mv = matern64(r, a.nu2);
+        const double hv = th.sigma2 * h_nu64(r, a.nu2);
+#pragma unroll
+        for (int c = 0; c < GR_CHUNK; ++c) {
+          const int k = k0 + c;
+          double dk = 0.0;
+          if (k == 0) {
+            dk = Mv;
+          } else if (k == 1) {
+            dk = (i == j) ? 1.0 : 0.0;
+          } else if (k < p) {
+            const int t = k - 2;
+            const double df = u[t * ustride + i] - u[t * ustride + j];
+            dk = hv * df * df * th.inv_beta[t];
+          }
+          acc[c] = fma(wgt, dk, acc[c]);
+        }
+        j += blockDim.x;
+        while (j > i) { j -= i + 1; ++i; }
+      }
+      // fixed-order CTA reduction of the chunk
+#pragma unroll
+      for (int c = 0; c < GR_CHUNK; ++c) {
+        double x = acc[c];
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) gred[warp][c] = x;
+      }
+      __syncthreads();
+      if (threadIdx.x < GR_CHUNK && k0 + (int)threadIdx.x < p) {
+        double x = 0.0;
+        for (int w = 0; w < nw; ++w) x += gred[w][threadIdx.x];
+        gout[k0 + threadIdx.x] = x;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// grad[b, k] = sum_i gterms[b, i, k] in a fixed order (as reduce_terms_kernel).
+__global__ void reduce_grad_kernel(const double* __restrict__ gterms, int64_t bc, int p,
+                                   double* __restrict__ grad) {
+  __shared__ double red[32];
+  const int b = blockIdx.x / p, k = blockIdx.x - b * p;
+  const double* t = gterms + (size_t)b * bc * p + k;
+  double v = 0.0;
+  for (int64_t i = threadIdx.x; i < bc; i += blockDim.x) v += t[(size_t)i * p];
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) grad[blockIdx.x] = w;
+  }
+}
+
+static bool g_grad_ready[64];
+
+int run_loglik_grad(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n, int d,
+                    const int64_t* ptr, const int32_t* pts, const int32_t* nbr,
+                    const int32_t* cnt, int64_t bc, int m, int nmax_hint, const double* h_theta,
+                    int B, int nu2, double* ll, double* grad, double* terms, double* gterms,
+                    int32_t* status, cudaStream_t s) {
+  int st = 0;
+  const int p = d + 2;
+  if ((uint64_t)bc * (uint64_t)B >= 0xffffffffull)
+    return fail(ctx, SBV_EUNSUPPORTED, "bc*B too large");
+  int nmax = nmax_hint;
+  if (nmax <= 0 && (st = structure_max_n(ctx, ptr, cnt, bc, &nmax, s))) return st;
+  if (nmax > SBV_MAX_BLOCK_N)
+    return fail(ctx, SBV_EUNSUPPORTED, "a block has m_i + bs_i = %d > %d", nmax, SBV_MAX_BLOCK_N);
+  ThetaDev* dth = nullptr;
+  if ((st = upload_theta(ctx, h_theta, B, d, &dth, s))) return st;
+  if (!terms) {
+    terms = (double*)ws_get(ctx, WS_TERMS, (size_t)B * bc * sizeof(double), &st);
+    if (!terms) return st;
+  }
+  if (!gterms) {
+    gterms = (double*)ws_get(ctx, WS_GRAD, (size_t)B * bc * p * sizeof(double), &st);
+    if (!gterms) return st;
+  }
+  unsigned int* counter = (unsigned int*)ws_get(ctx, WS_SMALL, 64, &st);
+  if (!counter) return st;
+  counter += 4;
+  SBV_CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
+  if (!(ctx->device < 64 && g_grad_ready[ctx->device])) {
+    SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_grad_fp64_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)ctx->smem_optin - 4096));
+    if (ctx->device < 64) g_grad_ready[ctx->device] = true;
+  }
+  // the FP64 plan, with room for this kernel's larger static shared memory
+  const size_t ub = (size_t)(d + 1) * (nmax + 1) * sizeof(double);
+  const size_t mat = (size_t)(nmax + 1) * (nmax + 2) / 2 * sizeof(double);
+  size_t smem = ub + mat, gstride = 0;
+  if (smem + 4096 > ctx->smem_optin) {
+    smem = ub;
+    if (ub + 4096 > ctx->smem_optin)
+      return fail(ctx, SBV_EUNSUPPORTED, "d=%d with N=%d exceeds shared memory", d, nmax);
+    gstride = (mat / sizeof(double) + 31) & ~(size_t)31;
+  }
+  int64_t grid = (int64_t)ctx->num_sms * std::max(1, std::min(2, (int)((228 * 1024) / (smem + 4096))));
+  if (grid > bc * (int64_t)B) grid = std::max<int64_t>(bc * (int64_t)B, 1);
+  LoglikArgs a;
+  a.X = X;
+  a.dtype = dtype;
+  a.y = y;
+  a.n = n;
+  a.d = d;
+  a.ptr = ptr;
+  a.pts = pts;
+  a.nbr = nbr;
+  a.cnt = cnt;
+  a.bc = bc;
+  a.m = m;
+  a.theta = dth;
+  a.B = B;
+  a.nu2 = nu2;
+  a.ncap = nmax;
+  a.terms = terms;
+  a.status = status;
+  a.dstat = ctx->d_status;
+  a.counter = counter;
+  a.gmat = nullptr;
+  a.gmat_stride = 0;
+  if (gstride) {
+    double* gm = (double*)ws_get(ctx, WS_MATRIX, gstride * grid * sizeof(double), &st);
+    if (!gm) return st;
+    a.gmat = gm;
+    a.gmat_stride = gstride;
+  }
+  GradArgs ga;
+  ga.gterms = gterms;
+  ga.zt_stride = ((size_t)nmax * (nmax + 2) + 31) & ~(size_t)31;
+  ga.zt = (double*)ws_get(ctx, WS_GRADZ, ga.zt_stride * grid * sizeof(double), &st);
+  if (!ga.zt) return st;
+  loglik_grad_fp64_kernel<<<(int)grid, LL_THREADS, smem, s>>>(a, ga);
+  SBV_LAUNCH_CHECK(ctx, "loglik_grad_fp64_kernel");
+  reduce_terms_kernel<<<B, 1024, 0, s>>>(terms, bc, ll);
+  SBV_LAUNCH_CHECK(ctx, "reduce_terms_kernel");
+  reduce_grad_kernel<<<B * p, 1024, 0, s>>>(gterms, bc, p, grad);
+  SBV_LAUNCH_CHECK(ctx, "reduce_grad_kernel");
+  return SBV_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Prediction: one test point per item, conditioned on its m nearest training
 // points; the joint matrix is [J; *] with the bordered row (y_J, 0).
 // ---------------------------------------------------------------------------

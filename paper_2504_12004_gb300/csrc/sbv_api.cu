@@ -212,6 +212,25 @@ extern "C" int sbv_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* 
                     precision, ll, block_terms, status, (cudaStream_t)stream);
 }
 
+extern "C" int sbv_loglik_grad(sbv_ctx* ctx, const void* X, int dtype, const double* y,
+                               int64_t n, int32_t d, const int64_t* ptr, const int32_t* pts,
+                               const int32_t* nbr, const int32_t* cnt, int64_t bc, int32_t m,
+                               int32_t nmax, const double* theta, int32_t B, int32_t nu2,
+                               double* ll, double* grad, double* block_terms,
+                               double* block_grads, int32_t* status, void* stream) {
+  int st = check_common(ctx, X, dtype, n, d);
+  if (st) return st;
+  if (!y || !ptr || !pts || !cnt || !ll || !grad || (m > 0 && !nbr))
+    return fail(ctx, SBV_EINVAL, "null pointer argument");
+  if (bc < 1 || bc > n) return fail(ctx, SBV_EINVAL, "bc=%lld outside [1, n]", (long long)bc);
+  if (m < 0) return fail(ctx, SBV_EINVAL, "m=%d must be >= 0", m);
+  if ((st = check_theta(ctx, theta, B, d))) return st;
+  if (!nu_ok(nu2)) return fail(ctx, SBV_EINVAL, "nu2=%d not in {1,3,5,7}", nu2);
+  if (nmax < 0) return fail(ctx, SBV_EINVAL, "nmax=%d must be >= 0", nmax);
+  return run_loglik_grad(ctx, X, dtype, y, n, d, ptr, pts, nbr, cnt, bc, m, nmax, theta, B, nu2,
+                         ll, grad, block_terms, block_grads, status, (cudaStream_t)stream);
+}
+
 extern "C" int sbv_sync_status(sbv_ctx* ctx, void* stream) {
   if (!ctx) return SBV_EINVAL;
   cudaSetDevice(ctx->device);

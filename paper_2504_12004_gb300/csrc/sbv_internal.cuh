@@ -37,29 +37,7 @@ struct TunedShape {
   int threads, per_sm;
 };
 
-}  // namespace sbv
-
-struct sbv_ctx {
-  int device = 0;
-  int num_sms = 0;
-  size_t smem_optin = 0;
-  std::string err;
-  sbv::DevStatus* d_status = nullptr;  // device record
-  sbv::DevBuf ws[16];                  // named workspace slots
-  sbv::LaunchShape force;              // set while the autotuner times a shape
-  std::vector<sbv::TunedShape> tuned;  // autotuning records
-  int knn_mode = 0;                    // 0 automatic, 1 brute force, 2 pruned search
-  // pinned host ring for parameter rows: slot k is reused only after the
-  // event recorded behind its previous copy has completed
-  static const int kRing = 8;
-  unsigned char* h_ring = nullptr;
-  size_t ring_slot = 0;
-  cudaEvent_t ring_ev[kRing] = {};
-  int ring_next = 0;
-};
-
-namespace sbv {
-
+// Named device workspace slots of a context (grow-only buffers).
 enum WsSlot {
   WS_Z = 0,       // scaled coordinates
   WS_SORT_A,      // sort keys / values
@@ -77,8 +55,33 @@ enum WsSlot {
   WS_XSPLIT,      // points split into float pairs for the mixed path
   WS_TUNE,        // results of the autotuner's timing runs
   WS_PRED,        // prediction neighbour lists when the caller passes NULL
+  WS_GRAD,        // per-block gradients when the caller passes NULL
+  WS_GRADZ,       // per-CTA right-hand sides of the gradient kernel
   WS_COUNT
 };
+
+}  // namespace sbv
+
+struct sbv_ctx {
+  int device = 0;
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  std::string err;
+  sbv::DevStatus* d_status = nullptr;  // device record
+  sbv::DevBuf ws[sbv::WS_COUNT];       // named workspace slots
+  sbv::LaunchShape force;              // set while the autotuner times a shape
+  std::vector<sbv::TunedShape> tuned;  // autotuning records
+  int knn_mode = 0;                    // 0 automatic, 1 brute force, 2 pruned search
+  // pinned host ring for parameter rows: slot k is reused only after the
+  // event recorded behind its previous copy has completed
+  static const int kRing = 8;
+  unsigned char* h_ring = nullptr;
+  size_t ring_slot = 0;
+  cudaEvent_t ring_ev[kRing] = {};
+  int ring_next = 0;
+};
+
+namespace sbv {
 
 int fail(sbv_ctx* ctx, int code, const char* fmt, ...);
 int cuda_fail(sbv_ctx* ctx, cudaError_t e, const char* where);
@@ -121,6 +124,11 @@ int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t 
                const int32_t* cnt, int64_t bc, int m, int nmax, const double* h_theta,
                int B, int nu2, int precision, double* ll, double* terms, int32_t* status,
                cudaStream_t s);
+int run_loglik_grad(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n, int d,
+                    const int64_t* ptr, const int32_t* pts, const int32_t* nbr,
+                    const int32_t* cnt, int64_t bc, int m, int nmax_hint, const double* h_theta,
+                    int B, int nu2, double* ll, double* grad, double* terms, double* gterms,
+                    int32_t* status, cudaStream_t s);
 int run_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n,
                 int d, const void* Xt, int64_t nt, const int32_t* nbr, int m,
                 const double* h_theta, int nu2, int precision, double* mean,
