@@ -447,7 +447,9 @@ int sbv_mlp_predict(sbv_mlp* mlp, const float* X, int64_t K, float* s, float* ds
  * batched call for a line search over `line_points` step lengths
  * 1, 1/2, 1/4, ... along the quasi-Newton direction (capped to `max_step` in
  * the max norm) and one batched call for the central-difference gradient
- * (2 (2 + d) rows) at the accepted point.  It stops when an accepted step
+ * (2 (2 + d) rows) at the accepted point, or, with gradient = 1, one call of
+ * sbv_loglik_grad (FP64 value and analytic gradient, chain rule to log
+ * theta) at the accepted point.  It stops when an accepted step
  * gains less than ftol |l|, when no step length improves l along a fresh
  * (reset) direction, or before a call would exceed max_evals rows.
  * A parameter row whose block matrices are not positive definite counts as
@@ -464,6 +466,7 @@ typedef struct {
   int32_t line_points;   /* step lengths per line-search call, 1..64 (8) */
   int32_t precision;     /* SBV_PREC_* (SBV_PREC_MIXED) */
   int32_t nu2;           /* 2 nu in {1, 3, 5, 7} (5) */
+  int32_t gradient;      /* 0 central differences, 1 analytic (sbv_loglik_grad, FP64) (0) */
 } sbv_mle_opts;
 
 typedef struct {
@@ -472,6 +475,8 @@ typedef struct {
   int32_t calls;         /* batched likelihood calls */
   int32_t iterations;    /* accepted steps */
   int32_t converged;     /* 1 gain < ftol, 2 stationary, 0 budget exhausted */
+  int32_t grad_evals;    /* analytic gradients evaluated (each also one row of evals;
+                            about 2.4 FP64 likelihood rows of work) */
 } sbv_mle_result;
 
 /* theta0, theta_out: host, 2 + d.  opts may be NULL (defaults above).  If

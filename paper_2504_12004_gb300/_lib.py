@@ -29,13 +29,13 @@ class MleOpts(C.Structure):
     """sbv_mle_opts"""
     _fields_ = [("max_evals", C.c_int32), ("fd_step", C.c_double), ("ftol", C.c_double),
                 ("max_step", C.c_double), ("line_points", C.c_int32), ("precision", C.c_int32),
-                ("nu2", C.c_int32)]
+                ("nu2", C.c_int32), ("gradient", C.c_int32)]
 
 
 class MleResult(C.Structure):
     """sbv_mle_result"""
     _fields_ = [("ll", C.c_double), ("evals", C.c_int32), ("calls", C.c_int32),
-                ("iterations", C.c_int32), ("converged", C.c_int32)]
+                ("iterations", C.c_int32), ("converged", C.c_int32), ("grad_evals", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -49,9 +49,11 @@ class SurrogateOpts(C.Structure):
 
 
 def mle_opts(max_evals=4000, fd_step=1e-3, ftol=1e-10, max_step=1.0, line_points=8,
-             precision="mixed", nu2=5) -> MleOpts:
+             precision="mixed", nu2=5, gradient="differences") -> MleOpts:
+    """gradient: "differences" (central, 2 (2 + d) rows) or "analytic" (sbv_loglik_grad, FP64)."""
+    g = {"differences": 0, "analytic": 1}[gradient] if isinstance(gradient, str) else int(gradient)
     return MleOpts(max_evals, fd_step, ftol, max_step, line_points,
-                   PRECISIONS[precision] if isinstance(precision, str) else int(precision), nu2)
+                   PRECISIONS[precision] if isinstance(precision, str) else int(precision), nu2, g)
 
 
 def surrogate_opts(exact_starts=4, train_steps=4000, batch=512, lr=1e-3, ascent_starts=256,

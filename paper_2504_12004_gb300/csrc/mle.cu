@@ -70,12 +70,15 @@ struct Evaluator {
   double* d_ll = nullptr;
   int cap = 0;
   int64_t evals = 0;
+  int64_t grad_evals = 0;
   int calls = 0;
+  double* d_g = nullptr;      // analytic gradient of one row
   std::vector<Vec> hist_u;    // every evaluated row (log theta) ...
   Vec hist_l;                 // ... and its log-likelihood (-inf if it failed)
 
   ~Evaluator() {
     if (d_ll) cudaFree(d_ll);
+    if (d_g) cudaFree(d_g);
   }
   Vec clamp(const Vec& u) const {
     Vec v(u);
@@ -126,6 +129,57 @@ struct Evaluator {
     calls += 1;
     return SBV_OK;
   }
+  // FP64 value and analytic gradient in log theta (d l / d log theta_k =
+  // theta_k d l / d theta_k) of one row; the row joins the history
+  int eval_grad(Vec& u, double& f, Vec& g) {
+    sbv_ctx* ctx = pb.ctx;
+    if (cap < 1) {
+      if (d_ll) cudaFree(d_ll);
+      d_ll = nullptr;
+      if (cudaMalloc(&d_ll, sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, SBV_ENOMEM, "likelihood buffer");
+      }
+      cap = 1;
+    }
+    if (!d_g) {
+      if (cudaMalloc(&d_g, (size_t)p * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        d_g = nullptr;
+        return fail(ctx, SBV_ENOMEM, "gradient buffer");
+      }
+    }
+    u = clamp(u);
+    Vec th(p), gt(p);
+    for (int j = 0; j < p; ++j) th[j] = exp(u[j]);
+    int st = run_loglik_grad(ctx, pb.X, pb.dtype, pb.y, pb.n, pb.d, pb.ptr, pb.pts, pb.nbr,
+                             pb.cnt, pb.bc, pb.m, pb.nmax, th.data(), 1, pb.nu2, d_ll, d_g,
+                             nullptr, nullptr, nullptr, pb.s);
+    if (st) return st;
+    DevStatus ds;
+    SBV_CUDA_TRY(ctx, cudaMemcpyAsync(&f, d_ll, sizeof(double), cudaMemcpyDeviceToHost, pb.s));
+    SBV_CUDA_TRY(ctx, cudaMemcpyAsync(gt.data(), d_g, (size_t)p * sizeof(double),
+                                      cudaMemcpyDeviceToHost, pb.s));
+    SBV_CUDA_TRY(ctx, cudaMemcpyAsync(&ds, ctx->d_status, sizeof(ds), cudaMemcpyDeviceToHost, pb.s));
+    SBV_CUDA_TRY(ctx, cudaStreamSynchronize(pb.s));
+    if (ds.code != 0) {
+      SBV_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(DevStatus), pb.s));
+      if (ds.code != SBV_ENOTSPD)
+        return fail(ctx, ds.code, "gradient kernel reported code %d", ds.code);
+    }
+    g.assign(p, 0.0);
+    if (!isfinite(f)) {
+      f = -INFINITY;
+    } else {
+      for (int j = 0; j < p; ++j) g[j] = isfinite(gt[j]) ? th[j] * gt[j] : 0.0;
+    }
+    hist_u.push_back(u);
+    hist_l.push_back(f);
+    evals += 1;
+    grad_evals += 1;
+    calls += 1;
+    return SBV_OK;
+  }
 };
 
 sbv_mle_opts default_opts() {
@@ -138,6 +192,7 @@ sbv_mle_opts default_opts() {
   o.line_points = 8;
   o.precision = SBV_PREC_MIXED;
   o.nu2 = 5;
+  o.gradient = 0;
   return o;
 }
 
@@ -146,6 +201,8 @@ int check_opts(sbv_ctx* ctx, const sbv_mle_opts& o) {
       !(o.max_step > 0.0) || o.line_points < 1 || o.line_points > 64)
     return fail(ctx, SBV_EINVAL, "bad MLE options");
   if (o.nu2 != 1 && o.nu2 != 3 && o.nu2 != 5 && o.nu2 != 7) return fail(ctx, SBV_EINVAL, "bad nu2");
+  if (o.gradient != 0 && o.gradient != 1)
+    return fail(ctx, SBV_EINVAL, "gradient=%d not 0 or 1", o.gradient);
   if (o.precision != SBV_PREC_FP64 && o.precision != SBV_PREC_MIXED &&
       o.precision != SBV_PREC_MIXED_BF16)
     return fail(ctx, SBV_EINVAL, "precision=%d unknown", o.precision);
@@ -180,14 +237,21 @@ int bfgs(Evaluator& E, const Vec& u0, const sbv_mle_opts& o, Vec& u_out, sbv_mle
   const int64_t ev0 = E.evals;
   const size_t h0 = E.hist_l.size();
   const int c0 = E.calls;
+  const int64_t gv0 = E.grad_evals;
   const double h = o.fd_step;
+  const bool analytic = o.gradient == 1;
   Vec u = E.clamp(u0), g, gn;
-  std::vector<Vec> U{u};
   Vec F;
-  int st = E.eval(U, F);
-  if (st) return st;
-  double f = F[0];
-  if ((st = fd_gradient(E, u, h, g))) return st;
+  double f = 0.0;
+  int st = 0;
+  if (analytic) {
+    if ((st = E.eval_grad(u, f, g))) return st;
+  } else {
+    std::vector<Vec> U{u};
+    if ((st = E.eval(U, F))) return st;
+    f = F[0];
+    if ((st = fd_gradient(E, u, h, g))) return st;
+  }
   std::vector<double> H((size_t)p * p, 0.0);
   auto reset = [&]() {
     std::fill(H.begin(), H.end(), 0.0);
@@ -197,7 +261,8 @@ int bfgs(Evaluator& E, const Vec& u0, const sbv_mle_opts& o, Vec& u_out, sbv_mle
   bool fresh = true;
   int iters = 0, conv = 0;
   const int L = o.line_points;
-  while (E.evals - ev0 + L + 2 * p <= o.max_evals) {
+  const int per_iter = L + (analytic ? 1 : 2 * p);
+  while (E.evals - ev0 + per_iter <= o.max_evals) {
     Vec dir(p, 0.0);
     double mx = 0.0;
     for (int i = 0; i < p; ++i) {
@@ -231,9 +296,14 @@ int bfgs(Evaluator& E, const Vec& u0, const sbv_mle_opts& o, Vec& u_out, sbv_mle
       continue;
     }
     ++iters;
-    const Vec un = C[kb];   // clamped by the evaluator
-    const double fn = F[kb];
-    if ((st = fd_gradient(E, un, h, gn))) return st;
+    Vec un = C[kb];   // clamped by the evaluator
+    double fn = F[kb];
+    if (analytic) {
+      // the FP64 value at the accepted point replaces the line search's one
+      if ((st = E.eval_grad(un, fn, gn))) return st;
+    } else if ((st = fd_gradient(E, un, h, gn))) {
+      return st;
+    }
     Vec s(p), yv(p);
     double ys = 0.0;
     for (int j = 0; j < p; ++j) {
@@ -277,6 +347,7 @@ int bfgs(Evaluator& E, const Vec& u0, const sbv_mle_opts& o, Vec& u_out, sbv_mle
   r.calls = E.calls - c0;
   r.iterations = iters;
   r.converged = conv;
+  r.grad_evals = (int32_t)(E.grad_evals - gv0);
   return SBV_OK;
 }
 
