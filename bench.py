@@ -387,6 +387,30 @@ def main():
         for p in paths.values():
             p["delta_l_per_n_vs_fp64"] = abs(p["ll"] - ref) / w["n"]
         paths["speedup_vs_fp64"] = paths["fp64"]["ms_per_call"] / call_ms
+    if not args.no_side_paths:
+        # FP64 value and analytic gradient in theta (sbv_loglik_grad), same
+        # structure and theta; L2 flushed before every timed call
+        try:
+            for _ in range(2):
+                gl, gg = ctx.sbv_loglik_grad(X, y, ptr, pts, nbr, cnt, th, nu2=w["nu2"], nmax=nmax)
+            torch.cuda.synchronize()
+            g_ms = []
+            for i in range(3):
+                flush.fill_(float(i))
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                gl, gg = ctx.sbv_loglik_grad(X, y, ptr, pts, nbr, cnt, th, nu2=w["nu2"], nmax=nmax)
+                a1.record(stream)
+                torch.cuda.synchronize()
+                g_ms.append(a0.elapsed_time(a1))
+            g_call = statistics.median(g_ms)
+            entry = {"evals_per_s": 1000.0 / g_call, "ms_per_call": g_call, "ll": float(gl[0].item()),
+                     "gradient_components": int(gg.shape[1])}
+            if "fp64" in paths:
+                entry["ll_equals_fp64_path"] = entry["ll"] == paths["fp64"]["ll"]
+            paths["fp64_value_and_gradient"] = entry
+        except Exception as e:  # a side measurement never costs the headline line
+            paths["fp64_value_and_gradient"] = {"error": str(e)[:200]}
 
     # ---------------- end to end: host buffers in, host scalar out, copies timed
     pin = lambda t: t.cpu().pin_memory()
