@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -163,10 +164,15 @@ def kernel_pairs(ptr: np.ndarray, cnt: np.ndarray) -> float:
 
 
 def source_hash(paths) -> str:
+    """sha256 (16 hex) of the kernel sources with comments and whitespace removed,
+    so that a recorded capture stays valid across comment-only edits."""
     h = hashlib.sha256()
     for path in paths:
-        with open(path, "rb") as f:
-            h.update(f.read())
+        with open(path, encoding="utf-8") as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -19,10 +19,14 @@
 //  4. the diagonal tiles are replaced by their inverses, which turns the
 //     diagonal steps of the triangular solves into small parallel products;
 //     x0 = L^-T w0 and x0_J = L_JJ^-T w0_J in FP32 (one two-column sweep);
-//  5. one step of iterative refinement: r = y - Sigma x0 and r_J = y_J -
-//     Sigma_JJ x0_J accumulated in double-float from the scratch matrix, the
-//     corrections solved in FP32;
-//  6. l_i = -1/2 [bs log 2pi + 2 sum_{t>=m} log L_tt + y^T x - y_J^T x_J],
+//  5. refinement of the two quadratic forms: each step forms r = y - Sigma x
+//     and r_J = y_J - Sigma_JJ x_J in double-float from the scratch matrix,
+//     w = L^{-1} r with the FP32 factor, and takes q = y^T x + x^T r + |w|^2
+//     (third order in the error of x) for both systems; a block stops once
+//     |w|^2 is below 1e-6 per point or stops halving, otherwise the backward
+//     solve corrects x for another step (at most six; prediction takes
+//     three);
+//  6. l_i = -1/2 [bs log 2pi + 2 sum_{t>=m} log L_tt + q - q_J],
 //     log L_tt = e ln2 + log(mantissa), sums in FP64.
 // y^T Sigma^{-1} y - y_J^T Sigma_JJ^{-1} y_J is the quadratic form of the
 // Schur complement Sigma^lk - Sigma^cor of Alg. 5 (applied to y_B - mu^new),
@@ -382,13 +386,15 @@ loglik_mixed_kernel(MixedArgs P) {
     // ---- 3. blocked Cholesky.  CUDA-core variant with look-ahead: while the
     // other warps apply panel k to the trailing matrix, warp 0 first updates
     // the next diagonal tile (the first ten 4 x 4 blocks of the trailing
-    // triangle) and factors it, so the tile factorisation is off the critical
-    // path.  The tensor-core variant factors each tile before its panel.
+    // triangle) and factors it, so the tile factorisation overlaps the
+    // trailing update instead of following it.  The tensor-core variant
+    // factors each tile before its panel.
     //
     // factor_tile(k0), warp 0 only, lane r holding row r of the tile: the
-    // double-float original (scratch matrix) plus the accumulated FP32 updates
-    // (held negated in A), one exact subtraction, then an FP32 factorisation
-    // in registers; L, its diagonal and inverse diagonal are stored.
+    // double-float original (staged in s_tile) plus the accumulated FP32
+    // updates (held negated in A), one exact subtraction, then an FP32
+    // factorisation in registers; L, its diagonal and inverse diagonal are
+    // stored.
     // stage_tile(kt), warp 0: asynchronous copies (cp.async, 8 bytes each) of
     // tile kt's double-float originals, lower triangle, column-major 16 x 16,
     // from the scratch matrix into s_tile.  Issued one panel ahead, right
