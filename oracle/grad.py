@@ -30,19 +30,27 @@ so dK/dbeta_t = sigma^2 h_nu(r) u_t^2 / beta_t with h_nu(r) = -M_nu'(r) / r:
     nu = 7/2:  h = (3 + 3 r + r^2) exp(-r) / 15
 
 (from M' of the closed forms: -e^-r; -r e^-r; -r (1 + r) e^-r / 3;
--r (3 + 3r + r^2) e^-r / 15).  Dense inverses and traces, one block at a time;
+-r (3 + 3r + r^2) e^-r / 15), and for any other nu = nu2/2 (nu >= 1)
+h = 2^(1-nu)/Gamma(nu) r^(nu-1) K_(nu-1)(r) from the Bessel-function
+derivative d/dr [r^nu K_nu(r)] = -r^nu K_(nu-1)(r).  Dense inverses and traces, one block at a time;
 pinned by central differences of oracle.sbv.block_loglik, by the closed form
 of dl/dsigma^2 at tau^2 = 0, and by additivity over blocks.
 """
 from __future__ import annotations
 
 import numpy as np
+from scipy import special
 
 from . import sbv
 
 
 def h_nu(r: np.ndarray, nu2: int) -> np.ndarray:
-    """-M_nu'(r) / r for nu = nu2 / 2 (0 where r = 0 for nu = 1/2)."""
+    """-M_nu'(r) / r for nu = nu2 / 2 (0 where r = 0 for nu = 1/2).
+
+    Other 2 <= nu2 <= 40: from d/dr [r^nu K_nu(r)] = -r^nu K_(nu-1)(r),
+    -M'(r)/r = 2^(1-nu)/Gamma(nu) r^(nu-1) K_(nu-1)(r) (scipy's K), with its
+    r -> 0 limit 1/(2 (nu - 1)) for nu > 1 and 0 at r = 0 for nu = 1 (where
+    it multiplies u_t^2 = 0)."""
     e = np.exp(-r)
     if nu2 == 1:
         with np.errstate(divide="ignore", invalid="ignore"):
@@ -53,7 +61,15 @@ def h_nu(r: np.ndarray, nu2: int) -> np.ndarray:
         return (1.0 + r) * e / 3.0
     if nu2 == 7:
         return (3.0 + 3.0 * r + r * r) * e / 15.0
-    raise ValueError("nu2 must be 1, 3, 5 or 7")
+    if 2 <= nu2 <= 40:
+        nu = nu2 / 2.0
+        r = np.asarray(r, dtype=np.float64)
+        out = np.full_like(r, 0.5 / (nu - 1.0) if nu > 1.0 else 0.0)
+        pos = r > 0
+        rp = r[pos]
+        out[pos] = 2.0 ** (1.0 - nu) / special.gamma(nu) * rp ** (nu - 1.0) * special.kv(abs(nu - 1.0), rp)
+        return out
+    raise ValueError("nu2 must be an integer in [1, 40]")
 
 
 def cov_derivatives(X, idx, theta, nu2: int) -> list[np.ndarray]:

@@ -15,6 +15,7 @@ from __future__ import annotations
 import math
 
 import numpy as np
+from scipy import special
 from scipy.linalg import solve_triangular
 
 from .prng import SplitMix64, full_shuffle, partial_shuffle_prefix
@@ -229,7 +230,9 @@ def knn(Z, blk, rank, centres, m: int, blocks=None):
 # Scaled Matern kernel (Eq. scale, Eq. maternkernel)
 # --------------------------------------------------------------------------
 def matern(r: np.ndarray, nu2: int) -> np.ndarray:
-    """2^(1-nu)/Gamma(nu) r^nu K_nu(r) for nu = nu2/2 in {1/2, 3/2, 5/2, 7/2}, closed forms.
+    """2^(1-nu)/Gamma(nu) r^nu K_nu(r) for nu = nu2/2: closed forms for
+    nu2 in {1, 3, 5, 7}, the Bessel-function definition (scipy's K_nu) for any
+    other 2 <= nu2 <= 40, with M(0) = 1.
 
     Reading: the argument is the scaled distance r itself, with no sqrt(2 nu)
     factor, exactly as Eq. maternkernel is printed.
@@ -243,7 +246,19 @@ def matern(r: np.ndarray, nu2: int) -> np.ndarray:
         return (1.0 + r + r * r / 3.0) * e
     if nu2 == 7:
         return (1.0 + r + 2.0 * r * r / 5.0 + r ** 3 / 15.0) * e
-    raise ValueError("nu2 must be 1, 3, 5 or 7")
+    if 2 <= nu2 <= 40:
+        return matern_bessel(r, nu2 / 2.0)
+    raise ValueError("nu2 must be an integer in [1, 40]")
+
+
+def matern_bessel(r, nu: float) -> np.ndarray:
+    """Eq. maternkernel written out with the Bessel function K_nu (scipy), M(0) = 1."""
+    r = np.asarray(r, dtype=np.float64)
+    out = np.ones_like(r)
+    pos = r > 0
+    rp = r[pos]
+    out[pos] = 2.0 ** (1.0 - nu) / special.gamma(nu) * rp ** nu * special.kv(nu, rp)
+    return out
 
 
 def cov(Xa: np.ndarray, Xb: np.ndarray, theta, nu2: int, same: np.ndarray | None = None) -> np.ndarray:

@@ -33,7 +33,7 @@ def fd_block(X, y, J, B, theta, nu2, k, rel=1e-5):
     return (sbv.block_loglik(X, y, J, B, tp, nu2) - sbv.block_loglik(X, y, J, B, tm, nu2)) / (2 * h)
 
 
-@pytest.mark.parametrize("nu2", [1, 3, 5, 7])
+@pytest.mark.parametrize("nu2", [1, 2, 3, 4, 5, 7, 9])
 def test_central_differences(nu2):
     X, y, b, nbr, cnt = problem()
     theta = np.array([1.3, 0.02, 0.25, 0.4, 0.6])
@@ -83,8 +83,13 @@ def test_block_gradients_add_up_to_the_total():
 
 def test_h_nu_is_minus_derivative_over_r():
     r = np.linspace(0.05, 6.0, 50)
-    for nu2 in (1, 3, 5, 7):
+    for nu2 in (1, 2, 3, 4, 5, 7, 9, 20):
         e = 1e-6
         dM = (sbv.matern(r + e, nu2) - sbv.matern(r - e, nu2)) / (2 * e)
-        assert np.allclose(og.h_nu(r, nu2), -dM / r, rtol=1e-7)
+        assert np.allclose(og.h_nu(r, nu2), -dM / r, rtol=1e-7), nu2
     assert og.h_nu(np.array([0.0]), 1)[0] == 0.0
+    # the r -> 0 limit 1 / (2 (nu - 1)) of the Bessel form (nu = 2, 4.5)
+    for nu2 in (4, 9):
+        nu = nu2 / 2
+        assert og.h_nu(np.array([1e-7]), nu2)[0] == pytest.approx(0.5 / (nu - 1), rel=1e-6)
+        assert og.h_nu(np.array([0.0]), nu2)[0] == 0.5 / (nu - 1)

@@ -296,3 +296,28 @@ def test_prediction_interpolates_without_nugget():
     mean, var, _, _ = sbv.predict(X, y, Xt, np.array([1.0, 1.0]), 10, th, 5)
     assert np.allclose(mean, y[[3, 17]], atol=1e-6)
     assert np.all(np.abs(var) < 1e-6)
+
+
+def test_matern_bessel_form_general_nu():
+    """Eq. maternkernel through the Bessel function K_nu (any nu = nu2/2):
+    equal to the closed forms at the half-integers, to a direct quadrature of
+    the defining integral K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt at
+    integer nu, 1 at r = 0 and decreasing in r."""
+    from scipy import integrate
+    r = np.array([1e-6, 0.05, 0.3, 1.0, 2.5, 7.0])
+    for nu2 in (1, 3, 5, 7):
+        assert np.allclose(sbv.matern_bessel(r, nu2 / 2), sbv.matern(r, nu2), rtol=1e-12, atol=0)
+    for nu2 in (2, 4):
+        nu = nu2 / 2
+        for x in r[1:]:
+            # beyond t_max the integrand is below exp(-800 + nu t_max) ~ 0
+            t_max = math.acosh(800.0 / x)
+            K, _ = integrate.quad(lambda t: math.exp(-x * math.cosh(t)) * math.cosh(nu * t), 0, t_max,
+                                  epsabs=0, epsrel=1e-13, limit=400)
+            want = 2 ** (1 - nu) / math.gamma(nu) * x ** nu * K
+            assert sbv.matern(np.array([x]), nu2)[0] == pytest.approx(want, rel=1e-10)
+    for nu2 in (2, 4, 9, 20):
+        m = sbv.matern(np.concatenate([[0.0], r]), nu2)
+        assert m[0] == 1.0 and np.all(np.diff(m) < 0) and m[1] == pytest.approx(1.0, abs=1e-9)
+    with pytest.raises(ValueError):
+        sbv.matern(r, 41)
