@@ -25,10 +25,11 @@
  *   - Parameter rows theta are (sigma^2, tau^2, beta_1 .. beta_d): process
  *     variance, nugget and per-dimension ranges of the scaled Matern kernel
  *     K(a,b) = sigma^2 M_nu(r) + tau^2 [a is b], r^2 = sum_t ((x_at-x_bt)/beta_t)^2
- *     (Eq. scale, Eq. maternkernel), M_nu the closed-form Matern correlation
- *     for nu = nu2/2, nu2 in {1,3,5,7}, evaluated at r itself (no sqrt(2 nu)
- *     factor, as the equation is printed).  The nugget is added only where a
- *     and b are the same data point.
+ *     (Eq. scale, Eq. maternkernel), M_nu the Matern correlation for
+ *     nu = nu2/2 (closed forms for nu2 in {1,3,5,7}; the FP64 paths also take
+ *     any other nu2 up to SBV_MAX_NU2 through K_nu), evaluated at r itself
+ *     (no sqrt(2 nu) factor, as the equation is printed).  The nugget is
+ *     added only where a and b are the same data point.
  *   - Indices in outputs are original point indices (0-based).
  *   - There is no CPU fallback: every computation runs in CUDA kernels.
  */
@@ -63,6 +64,7 @@ extern "C" {
 
 /* compiled limits */
 #define SBV_MAX_DIM      64     /* d */
+#define SBV_MAX_NU2      40     /* largest 2 nu of the FP64 paths (nu <= 20) */
 #define SBV_MAX_BLOCK_N  1024   /* m_i + bs_i of one block */
 
 typedef struct sbv_ctx sbv_ctx;
@@ -186,7 +188,11 @@ int sbv_set_knn_mode(sbv_ctx* ctx, int32_t mode);
  *                      largest size is safe: the blocks above it get status
  *                      SBV_EUNSUPPORTED and a NaN term.
  *   theta              host, B x (2+d) doubles, rows (sigma^2, tau^2, beta_1..beta_d)
- *   nu2                2*nu in {1, 3, 5, 7}
+ *   nu2                2*nu: {1, 3, 5, 7} (closed forms) in every precision;
+ *                      with SBV_PREC_FP64 also any other 2..SBV_MAX_NU2, where
+ *                      M_nu = 2^(1-nu)/Gamma(nu) r^nu K_nu(r) with K_nu by an
+ *                      exponentially convergent quadrature of its integral
+ *                      representation (relative error below 1e-12)
  *   precision          SBV_PREC_FP64, SBV_PREC_MIXED or SBV_PREC_MIXED_BF16
  *   ll                 device, B doubles  out: l(theta_b) = sum_i l_{b,i}
  *   block_terms        device, B x bc doubles out (or NULL): l_{b,i}

@@ -16,12 +16,20 @@
 #include <algorithm>
 #include <vector>
 
+#include "bessel.cuh"
 #include "block_common.cuh"
 #include "sbv_internal.cuh"
 
 namespace sbv {
 
 constexpr int LL_THREADS = 256;
+
+// Matern correlation of the FP64 paths: the closed forms for nu2 in
+// {1, 3, 5, 7}, the Bessel-function form (bessel.cuh) for any other nu2.
+__device__ __forceinline__ double matern_fp64(double r, int nu2) {
+  if (nu2 == 1 || nu2 == 3 || nu2 == 5 || nu2 == 7) return matern64(r, nu2);
+  return matern_general(r, 0.5 * nu2);
+}
 
 // Gather the N points of an item into u[t][p] = x_p,t / beta_t and yv[p].
 // Point p < mb is neighbour p of the block, p >= mb is member p - mb.
@@ -53,7 +61,7 @@ __device__ void build_cov(const double* u, int ustride, int d, int N, const Thet
       double df = u[t * ustride + i] - u[t * ustride + j];
       s = fma(df, df, s);
     }
-    double K = th.sigma2 * matern64(sqrt(s), nu2);
+    double K = th.sigma2 * matern_fp64(sqrt(s), nu2);
     if (i == j) K += th.tau2;
     A[l] = K;
     j += blockDim.x;
@@ -443,15 +451,16 @@ struct GradArgs {
   size_t zt_stride;    // doubles per CTA slice (ncap x (ncap + 2))
 };
 
-// -M'(r) / r for the closed-form Matern correlations (0 at r = 0 for nu = 1/2,
-// where every u_t is 0 as well).
+// -M'(r) / r: closed forms for nu2 in {1, 3, 5, 7} (0 at r = 0 for nu = 1/2,
+// where every u_t is 0 as well), the Bessel-function form for any other nu2.
 __device__ __forceinline__ double h_nu64(double r, int nu2) {
   const double e = exp(-r);
   switch (nu2) {
     case 1: return r > 0.0 ? e / r : 0.0;
     case 3: return e;
     case 5: return (1.0 + r) * e * (1.0 / 3.0);
-    default: return fma(r, r + 3.0, 3.0) * e * (1.0 / 15.0);
+    case 7: return fma(r, r + 3.0, 3.0) * e * (1.0 / 15.0);
+    default: return matern_general_h(r, 0.5 * nu2);
   }
 }
 
@@ -570,7 +579,7 @@ loglik_grad_fp64_kernel(LoglikArgs a, GradArgs g) {
         for (int q = 0; q < bs; ++q) D = fma(zi[q], zj[q], D);
         double wgt = 0.5 * (zi[bs] * zj[bs] - zi[bs + 1] * zj[bs + 1]) - 0.5 * D;
         if (i != j) wgt *= 2.0;
-        const double Mv = matern64(r, a.nu2);
+        const double Mv = matern_fp64(r, a.nu2);
         const double hv = th.sigma2 * h_nu64(r, a.nu2);
 #pragma unroll
         for (int c = 0; c < GR_CHUNK; ++c) {

@@ -200,7 +200,10 @@ int check_opts(sbv_ctx* ctx, const sbv_mle_opts& o) {
   if (o.max_evals < 1 || !(o.fd_step > 0.0 && o.fd_step < 1.0) || !(o.ftol >= 0.0) ||
       !(o.max_step > 0.0) || o.line_points < 1 || o.line_points > 64)
     return fail(ctx, SBV_EINVAL, "bad MLE options");
-  if (o.nu2 != 1 && o.nu2 != 3 && o.nu2 != 5 && o.nu2 != 7) return fail(ctx, SBV_EINVAL, "bad nu2");
+  const bool closed = o.nu2 == 1 || o.nu2 == 3 || o.nu2 == 5 || o.nu2 == 7;
+  if (!(closed || (o.precision == SBV_PREC_FP64 && o.nu2 >= 1 && o.nu2 <= SBV_MAX_NU2)))
+    return fail(ctx, SBV_EINVAL, "nu2=%d: FP64 takes 1..%d, the mixed precisions {1,3,5,7}",
+                o.nu2, SBV_MAX_NU2);
   if (o.gradient != 0 && o.gradient != 1)
     return fail(ctx, SBV_EINVAL, "gradient=%d not 0 or 1", o.gradient);
   if (o.precision != SBV_PREC_FP64 && o.precision != SBV_PREC_MIXED &&

@@ -132,7 +132,12 @@ static int check_theta(sbv_ctx* ctx, const double* theta, int B, int d) {
   return SBV_OK;
 }
 
+// 2 nu: the mixed precisions evaluate the four closed forms in double-float;
+// the FP64 paths also take any other nu = nu2 / 2 <= 20 through K_nu
 static bool nu_ok(int nu2) { return nu2 == 1 || nu2 == 3 || nu2 == 5 || nu2 == 7; }
+static bool nu_ok_prec(int nu2, int precision) {
+  return precision == SBV_PREC_FP64 ? (nu2 >= 1 && nu2 <= SBV_MAX_NU2) : nu_ok(nu2);
+}
 
 extern "C" int sbv_blocking_partitioned(sbv_ctx* ctx, const void* X, int dtype, int64_t n,
                                         int32_t d, const double* beta_scale, int64_t bc,
@@ -203,10 +208,12 @@ extern "C" int sbv_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* 
   if (bc < 1 || bc > n) return fail(ctx, SBV_EINVAL, "bc=%lld outside [1, n]", (long long)bc);
   if (m < 0) return fail(ctx, SBV_EINVAL, "m=%d must be >= 0", m);
   if ((st = check_theta(ctx, theta, B, d))) return st;
-  if (!nu_ok(nu2)) return fail(ctx, SBV_EINVAL, "nu2=%d not in {1,3,5,7}", nu2);
   if (precision != SBV_PREC_FP64 && precision != SBV_PREC_MIXED &&
       precision != SBV_PREC_MIXED_BF16)
     return fail(ctx, SBV_EINVAL, "precision=%d unknown", precision);
+  if (!nu_ok_prec(nu2, precision))
+    return fail(ctx, SBV_EINVAL, "nu2=%d: FP64 takes 1..%d, the mixed precisions {1,3,5,7}", nu2,
+                SBV_MAX_NU2);
   if (nmax < 0) return fail(ctx, SBV_EINVAL, "nmax=%d must be >= 0", nmax);
   return run_loglik(ctx, X, dtype, y, n, d, ptr, pts, nbr, cnt, bc, m, nmax, theta, B, nu2,
                     precision, ll, block_terms, status, (cudaStream_t)stream);
@@ -225,7 +232,8 @@ extern "C" int sbv_loglik_grad(sbv_ctx* ctx, const void* X, int dtype, const dou
   if (bc < 1 || bc > n) return fail(ctx, SBV_EINVAL, "bc=%lld outside [1, n]", (long long)bc);
   if (m < 0) return fail(ctx, SBV_EINVAL, "m=%d must be >= 0", m);
   if ((st = check_theta(ctx, theta, B, d))) return st;
-  if (!nu_ok(nu2)) return fail(ctx, SBV_EINVAL, "nu2=%d not in {1,3,5,7}", nu2);
+  if (!nu_ok_prec(nu2, SBV_PREC_FP64))
+    return fail(ctx, SBV_EINVAL, "nu2=%d outside 1..%d", nu2, SBV_MAX_NU2);
   if (nmax < 0) return fail(ctx, SBV_EINVAL, "nmax=%d must be >= 0", nmax);
   return run_loglik_grad(ctx, X, dtype, y, n, d, ptr, pts, nbr, cnt, bc, m, nmax, theta, B, nu2,
                          ll, grad, block_terms, block_grads, status, (cudaStream_t)stream);
@@ -265,10 +273,12 @@ static int predict_common(sbv_ctx* ctx, const void* X, int dtype, const double* 
   if (m_pred > SBV_MAX_BLOCK_N - 1)
     return fail(ctx, SBV_EUNSUPPORTED, "m_pred=%d above %d", m_pred, SBV_MAX_BLOCK_N - 1);
   if ((st = check_theta(ctx, theta, 1, d))) return st;
-  if (!nu_ok(nu2)) return fail(ctx, SBV_EINVAL, "nu2=%d not in {1,3,5,7}", nu2);
   if (precision != SBV_PREC_FP64 && precision != SBV_PREC_MIXED &&
       precision != SBV_PREC_MIXED_BF16)
     return fail(ctx, SBV_EINVAL, "precision=%d unknown", precision);
+  if (!nu_ok_prec(nu2, precision))
+    return fail(ctx, SBV_EINVAL, "nu2=%d: FP64 takes 1..%d, the mixed precisions {1,3,5,7}", nu2,
+                SBV_MAX_NU2);
   if (ptr && (!pts || !rank || !centres || bc < 1 || bc > n))
     return fail(ctx, SBV_EINVAL, "incomplete block structure");
   cudaStream_t s = (cudaStream_t)stream;

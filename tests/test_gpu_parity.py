@@ -330,8 +330,14 @@ def test_invalid_arguments_are_rejected(ctx, gp5d, gp5d_oracle):
     with pytest.raises(SBVError) as e:
         gpu_loglik(ctx, gp5d["X"], gp5d["y"], b, bad, 5, "fp64")
     assert e.value.code == 1
+    # 2 nu: FP64 takes 1..40 (Bessel form beyond the closed forms), the mixed
+    # precisions only the closed forms {1, 3, 5, 7}
     with pytest.raises(SBVError):
-        gpu_loglik(ctx, gp5d["X"], gp5d["y"], b, gp5d["theta"][0], 4, "fp64")
+        gpu_loglik(ctx, gp5d["X"], gp5d["y"], b, gp5d["theta"][0], 41, "fp64")
+    with pytest.raises(SBVError):
+        gpu_loglik(ctx, gp5d["X"], gp5d["y"], b, gp5d["theta"][0], 0, "fp64")
+    with pytest.raises(SBVError):
+        gpu_loglik(ctx, gp5d["X"], gp5d["y"], b, gp5d["theta"][0], 4, "mixed")
     with pytest.raises(SBVError):
         ctx.sbv_blocking(cuda(gp5d["X"]), gp5d["beta_scale"], 0, 1, 1)
     with pytest.raises(SBVError):
