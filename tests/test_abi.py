@@ -48,6 +48,20 @@ def test_null_context_is_rejected_without_device(lib):
     rc = lib.sbv_blocking(None, None, 0, 0, 0, None, 0, 0, 0, None, None, None, None, None, None,
                           None)
     assert rc == 1
+    rc = lib.sbv_loglik_grad(None, None, 0, None, 0, 0, None, None, None, None, 0, 0, 0, None, 0,
+                             0, None, None, None, None, None, None)
+    assert rc == 1
+
+
+def test_mle_structs_match_the_c_layout():
+    """ctypes mirrors of sbv_mle_opts / sbv_mle_result: natural alignment gives
+    the C layout (int32, 4 bytes padding, 3 doubles, 4 int32) and (double, 5 int32)."""
+    import ctypes
+    from paper_2504_12004_gb300 import _lib
+    assert ctypes.sizeof(_lib.MleOpts) == 48 and _lib.MleOpts.gradient.offset == 44
+    assert ctypes.sizeof(_lib.MleResult) == 32 and _lib.MleResult.grad_evals.offset == 24
+    o = _lib.mle_opts(gradient="analytic", precision="fp64")
+    assert o.gradient == 1 and o.precision == 0
 
 
 def test_product_path_does_not_import_oracle():
