@@ -37,10 +37,11 @@ sys.path.insert(0, ROOT)
 METRIC = "SBV loglik evals/s & TFLOP/s on 1 GB300, mixed vs FP64 at |dl|/n <= 1e-6"
 UNIT = "evals/s"
 L2_BYTES = 129 * 1024 * 1024
-# FP32 CUDA-core peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# FP64 peak: 1.25 TFLOP/s nominal for GB300 (a DFMA probe measured 1.19-1.20)
-FP64_PEAK_TFLOPS = 1.25
+# nominal dense tensor rates of GB300 (context): the TF32 peak is taken as the
+# measured BF16 rate times this nominal ratio
+TF32_PER_BF16 = 1.1 / 2.25
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_BF16_TFLOPS = 1900.0   # used only when the measured-peaks file is absent
 # the sources of the mixed block kernel (the recorded traffic is valid for these)
 KERNEL_SRC = [os.path.join(ROOT, "paper_2504_12004_gb300", "csrc", f)
               for f in ("loglik_mixed.cu", "mixed.cuh", "dfloat.cuh", "block_common.cuh")]
@@ -60,7 +61,7 @@ def parse():
     p.add_argument("--kmeans-iters", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-side-paths", action="store_true")
-    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--oracle-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--launch", default="graph", choices=["graph", "direct"],
                    help="time graph replays (default) or direct sbv_loglik calls")
     p.add_argument("--no-autotune", action="store_true")
@@ -158,6 +159,28 @@ def algorithmic_flops(ptr: np.ndarray, cnt: np.ndarray) -> float:
     return float(np.sum(N ** 3 / 3.0 + N ** 2))
 
 
+def algorithmic_bytes(ptr: np.ndarray, cnt: np.ndarray, d: int, xbytes: int) -> float:
+    """Bytes one evaluation must move: per block the N_i gathered points (d
+    coordinates and y), the m_i neighbour ids and bs_i member ids, its slice of
+    ptr and cnt, and its FP64 term written."""
+    bs = np.diff(ptr).astype(np.float64)
+    N = bs + cnt.astype(np.float64)
+    return float(np.sum(N * (d * xbytes + 8) + 4 * N + 8 + 4 + 8))
+
+
+def measured_peaks():
+    """BF16 tensor peaks from the measured-peaks file (burst and sustained), else the fallback."""
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return {"bf16_burst": float(p["bf16_tflops"]),
+                "bf16_sustained": float(p.get("bf16_tflops_sustained", p["bf16_tflops"])),
+                "hbm_gbs": float(p.get("hbm_gbs", 0.0)), "source": "measured"}
+    except Exception:
+        return {"bf16_burst": FALLBACK_BF16_TFLOPS, "bf16_sustained": FALLBACK_BF16_TFLOPS,
+                "hbm_gbs": 6800.0, "source": "fallback"}
+
+
 def kernel_pairs(ptr: np.ndarray, cnt: np.ndarray) -> float:
     N = np.diff(ptr).astype(np.float64) + cnt.astype(np.float64)
     return float(np.sum(N * (N + 1) / 2))
@@ -193,50 +216,114 @@ def recorded_traffic(workload: str):
 
 
 # ----------------------------------------------------------------------------- CPU baseline
-CPU_SNIPPET = r"""
-import json, sys, time
-import numpy as np
-sys.path.insert(0, {root!r})
-from synth.inputs import workload
-from oracle import sbv
-w = workload({name!r})
-n, bc, m = w["n"], w["bc"], w["m"]
-bs = n // bc
-# the oracle's per-block arithmetic depends only on the block's size and neighbour
-# count: a smaller point set with the same bs and m gives full-size blocks to time
-nb = {nblocks}
-nsub = min(n, nb * bs)
-X = w["X"][:nsub]; y = w["y"][:nsub]
-b = sbv.blocking(X, w["beta_scale"], nsub // bs, 0, 5)
-nbr, cnt = sbv.knn(b["Z"], b["blk"], b["rank"], b["centres"], m)
-rows = np.nonzero(cnt == min(m, int(cnt.max())))[0]
-th = w["theta"][0]
-done = 0
-t0 = time.perf_counter()
-while time.perf_counter() - t0 < {seconds}:
-    sbv.loglik_terms(X, y, b["ptr"], b["pts"], nbr, cnt, th, w["nu2"], blocks=rows)
-    done += rows.size
-dt = time.perf_counter() - t0
-print(json.dumps(dict(seconds=dt, blocks=int(done), distinct=int(rows.size), bc=bc, bs=bs, m=m)))
-"""
+def cpu_model() -> str:
+    """Host CPU model as lscpu (or /proc/cpuinfo) names it."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
 
 
-def cpu_baseline(name: str, seconds: float, nblocks: int = 400):
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+_ORACLE = {}
+
+
+def _oracle_init(X, y, ptr, pts, nbr, cnt, th, nu2):
+    # each worker process of the pool holds the sample structure once
+    from oracle import sbv  # the oracle, in worker processes of the CPU baseline only
+    _ORACLE.update(sbv=sbv, X=X, y=y, ptr=ptr, pts=pts, nbr=nbr, cnt=cnt, th=th, nu2=nu2)
+
+
+def _oracle_terms(rows):
+    o = _ORACLE
+    t = o["sbv"].loglik_terms(o["X"], o["y"], o["ptr"], o["pts"], o["nbr"], o["cnt"], o["th"],
+                              o["nu2"], blocks=rows)
+    return float(np.sum(t))
+
+
+def oracle_worker(name: str, steps: int, warmup: int, nblocks: int = 400):
+    """Time the FP64 oracle over all host cores: one step = bc block terms.
+
+    The oracle's per-block arithmetic depends only on the block's size and its
+    neighbour count, so the blocks come from a sample of the workload (a point
+    set holding `nblocks` blocks of the workload's mean size, blocked by the
+    oracle, with the workload's m); each step evaluates bc block terms, cycling
+    over the sample's blocks that have the full m neighbours, split over a
+    process pool (spawned: no CUDA state is inherited) with one process per
+    core.  Prints one JSON line with the wall time of every step."""
+    import multiprocessing as mp
+    from synth.inputs import workload
+    from oracle import sbv  # the oracle, in the CPU baseline leg only
+    w = workload(name)
+    n, bc, m = w["n"], w["bc"], w["m"]
+    bs = max(1, n // bc)
+    nsub = min(n, nblocks * bs)
+    X = np.ascontiguousarray(w["X"][:nsub])
+    y = np.ascontiguousarray(w["y"][:nsub])
+    b = sbv.blocking(X, w["beta_scale"], nsub // bs, 0, 5)
+    nbr, cnt = sbv.knn(b["Z"], b["blk"], b["rank"], b["centres"], m)
+    full = np.nonzero(cnt == min(m, int(cnt.max())))[0]
+    rows = np.resize(full, bc)                      # bc block terms per step
+    cores = host_cores()
+    chunks = np.array_split(rows, cores * 4)
+    ctx = mp.get_context("spawn")
+    times = []
+    with ctx.Pool(cores, initializer=_oracle_init,
+                  initargs=(X, y, b["ptr"], b["pts"], nbr, cnt, w["theta"][0], w["nu2"])) as pool:
+        pool.map(_oracle_terms, [r[:1] for r in chunks[:cores]])   # workers up
+        for i in range(warmup + steps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_terms, chunks, chunksize=1)
+            if i >= warmup:
+                times.append(time.perf_counter() - t0)
+    print(json.dumps(dict(times=times, cores=cores, model=cpu_model(), bc=bc, bs=bs, m=m,
+                          distinct=int(full.size), sample_points=int(nsub))))
+
+
+def run_oracle(name: str, steps: int, warmup: int):
+    """Run oracle_worker in a fresh process without CUDA; returns its record."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    code = CPU_SNIPPET.format(root=ROOT, name=name, nblocks=nblocks, seconds=seconds)
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       timeout=1200)
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", "--workload", name,
+           "--steps", str(steps), "--warmup", str(warmup)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=3600)
     if r.returncode != 0:
         return {"error": r.stderr[-400:]}
-    res = json.loads(r.stdout.strip().splitlines()[-1])
-    per_block = res["seconds"] / res["blocks"]
-    evals_per_s = 1.0 / (per_block * res["bc"])
-    return {"value": evals_per_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{res['blocks']} block terms ({res['distinct']} distinct full-size blocks, "
-                      f"bs~{res['bs']}, m={res['m']}) of the {name} workload shape in "
-                      f"{res['seconds']:.1f} s of single-thread FP64 oracle time, extrapolated "
-                      f"linearly to bc={res['bc']}"}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_sample_text(res, name):
+    return (f"per step {res['bc']} FP64 oracle block terms (one evaluation's worth: bs~{res['bs']}, "
+            f"m={res['m']}), cycled over the {res['distinct']} full-size blocks of a "
+            f"{res['sample_points']}-point sample of the {name} workload, on {res['cores']} "
+            f"processes ({res['model']})")
+
+
+def cpu_baseline(name: str):
+    res = run_oracle(name, 1, 0)
+    if "error" in res:
+        return {"error": res["error"]}
+    t = statistics.median(res["times"])
+    return {"value": 1.0 / t, "unit": UNIT, "cores": res["cores"], "kind": "oracle",
+            "cpu_model": res["model"], "sample": oracle_sample_text(res, name)}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -246,25 +333,21 @@ def run_reference(args):
         return
     from synth.inputs import WORKLOADS
     w = WORKLOADS[args.workload]
-    per_step = []
-    secs = max(2.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
-    for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(args.workload, secs)
-        if "error" in cb:
-            print(json.dumps({"impl": "reference", "unavailable": cb["error"][-200:]}))
-            return
-        if i >= args.warmup:
-            per_step.append(cb)
-    v = statistics.median([c["value"] for c in per_step])
+    res = run_oracle(args.workload, args.steps, args.warmup)
+    if "error" in res:
+        print(json.dumps({"impl": "reference", "unavailable": res["error"][-200:]}))
+        return
+    t = statistics.median(res["times"])
+    v = 1.0 / t
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "n": w["n"], "d": w["d"], "bc": w["bc"],
-                   "m": w["m"], "nu": w["nu2"] / 2, "theta_per_eval": 1},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": per_step[-1]["sample"]},
+                   "m": w["m"], "nu": w["nu2"] / 2, "theta_per_eval": 1, "precision": "fp64"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": res["cores"], "kind": "oracle",
+                         "cpu_model": res["model"], "sample": oracle_sample_text(res, args.workload)},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -273,6 +356,9 @@ def run_reference(args):
 # ----------------------------------------------------------------------------- our arm
 def main():
     args = parse()
+    if args.oracle_worker:
+        oracle_worker(args.workload, args.steps, args.warmup)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -440,23 +526,40 @@ def main():
            "d2h_bytes_per_step": 8}
 
     # ---------------- roofline of the dominant kernel (the block log-likelihood)
+    # achieved = sum_i (N_i^3/3 + N_i^2) per launch / CUDA-event time per
+    # launch (graph replay: block kernel + the 10 us reduction)
     achieved_tflops = flops / (call_ms / 1000.0) / 1e12
+    peaks = measured_peaks()
+    fp64_peak = ctx.sbv_peak_probe("fp64")
+    fp32_peak = ctx.sbv_peak_probe("fp32")
+    xbytes = X.element_size()
+    abytes = algorithmic_bytes(ptr_h, cnt_h, w["d"], xbytes)
     if precision == "fp64":
-        roof = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "nominal FP64 rate of GB300 (DFMA probe measured 1.19)"}
+        roof = {"bound": "alu", "achieved": achieved_tflops, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": achieved_tflops / fp64_peak, "traffic": None,
+                "peak_source": "of measured: FP64 DFMA rate from sbv_peak_probe in this run"}
     else:
-        roof = {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved_tflops / FP32_PEAK_TFLOPS,
-                "traffic": recorded_traffic(args.workload) if precision == "mixed" else None,
-                "peak_source": "FP32 CUDA-core rate from 152 SMs x 128 lanes x 2 x 2.07 GHz",
+        tf32 = peaks["bf16_burst"] * TF32_PER_BF16
+        traffic = recorded_traffic(args.workload) if precision == "mixed" else None
+        roof = {"bound": "tensor", "achieved": achieved_tflops, "peak": tf32,
+                "unit": "TFLOP/s", "frac": achieved_tflops / tf32, "traffic": traffic,
+                "peak_source": "of %s: BF16 burst %.1f TFLOP/s x nominal TF32/BF16 ratio 1.1/2.25 "
+                               "(the Cholesky stage's dense contraction class)"
+                               % (peaks["source"], peaks["bf16_burst"]),
+                "algorithmic_bytes": abytes,
+                "traffic_over_algorithmic": (traffic / abytes) if traffic else None,
+                "achieved_gbs": abytes / (call_ms / 1000.0) / 1e9,
+                "hbm_frac": abytes / (call_ms / 1000.0) / 1e9 / peaks["hbm_gbs"] if peaks["hbm_gbs"] else None,
+                "simt_fp32": {"peak": fp32_peak, "frac": achieved_tflops / fp32_peak,
+                              "peak_source": "of measured: FP32 FFMA rate from sbv_peak_probe"},
+                "fp64_probe_tflops": fp64_peak,
                 "note": "achieved counts the Cholesky flops sum N^3/3 + N^2 only; the "
                         "double-float covariance (%.3g kernel evaluations per call) is the "
                         "larger share of the issued instructions" % pairs}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.workload, args.cpu_seconds)
+        cpu = cpu_baseline(args.workload)
 
     if rank == 0:
         line = {

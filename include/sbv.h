@@ -343,6 +343,17 @@ int sbv_autotune(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_
                  const double* theta, int32_t B, int32_t nu2, int32_t precision,
                  int32_t* threads, int32_t* ctas_per_sm, void* stream);
 
+/*
+ * sbv_peak_probe -- measured FMA rate of the CUDA cores, for roofline
+ * denominators.  The paper has no counterpart (it reports the GFLOP/s of its
+ * FP64 batched kernels, Sec. 8.1, without a peak).  kind 0 times FP64 DFMA,
+ * kind 1 FP32 FFMA: 8 independent chains per thread, 8 CTAs of 256 threads
+ * per SM, 2 flops per FMA; one warm-up launch, then the best of three timed
+ * launches (CUDA events on a private stream, which the call synchronises).
+ * *tflops (host) receives TFLOP/s.  Errors: SBV_EINVAL, SBV_ECUDA.
+ */
+int sbv_peak_probe(sbv_ctx* ctx, int32_t kind, double* tflops);
+
 /* Limits of the fixed scratch array of sbv_loglik_fp64_noalloc (about 8.1 MB
  * per GPU that loads the library, held until the process exits). */
 #define SBV_NOALLOC_MAX_THETA 64          /* parameter rows per call */

@@ -93,6 +93,7 @@ SIGNATURES = {
     "sbv_loglik_graph_destroy": (None, [_P]),
     "sbv_autotune": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64, _I32, _I32,
                                _P, _I32, _I32, _I32, C.POINTER(_I32), C.POINTER(_I32), _P]),
+    "sbv_peak_probe": (C.c_int, [_P, _I32, C.POINTER(_D)]),
     "sbv_mlp_num_params": (_I64, [_I32]),
     "sbv_mlp_create": (C.c_int, [_P, _I32, _U64, C.POINTER(_P)]),
     "sbv_mlp_destroy": (None, [_P]),
@@ -309,6 +310,12 @@ class Context:
                                    C.byref(t), C.byref(c), _stream(stream))
         self._check(rc)
         return t.value, c.value
+
+    def sbv_peak_probe(self, kind: str = "fp64") -> float:
+        """Measured FMA rate of the CUDA cores in TFLOP/s (kind "fp64" or "fp32")."""
+        v = C.c_double(0.0)
+        self._check(self.lib.sbv_peak_probe(self.h, {"fp64": 0, "fp32": 1}[kind], C.byref(v)))
+        return v.value
 
     def sbv_loglik_graph_create(self, X, y, ptr, pts, nbr, cnt, B: int, nu2: int = 5,
                                 precision="mixed", nmax: int = 0, block_terms=None, status=None):

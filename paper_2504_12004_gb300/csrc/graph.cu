@@ -39,7 +39,12 @@ int check_loglik_args(sbv_ctx* ctx, const void* X, int dtype, const double* y, i
   if (n < 1 || d < 1 || d > SBV_MAX_DIM || bc < 1 || bc > n || m < 0)
     return fail(ctx, SBV_EINVAL, "bad sizes");
   if (B < 1) return fail(ctx, SBV_EINVAL, "B=%d must be >= 1", B);
-  if (nu2 != 1 && nu2 != 3 && nu2 != 5 && nu2 != 7) return fail(ctx, SBV_EINVAL, "bad nu2");
+  // as sbv_loglik: the captured FP64 kernel takes any nu2 in 1..SBV_MAX_NU2,
+  // the mixed kernels the closed forms
+  const bool closed = nu2 == 1 || nu2 == 3 || nu2 == 5 || nu2 == 7;
+  if (precision == SBV_PREC_FP64 ? (nu2 < 1 || nu2 > SBV_MAX_NU2) : !closed)
+    return fail(ctx, SBV_EINVAL, "nu2=%d: FP64 takes 1..%d, the mixed precisions {1,3,5,7}", nu2,
+                SBV_MAX_NU2);
   if (precision != SBV_PREC_FP64 && precision != SBV_PREC_MIXED &&
       precision != SBV_PREC_MIXED_BF16)
     return fail(ctx, SBV_EINVAL, "precision=%d unknown", precision);

@@ -76,7 +76,8 @@ extern "C" int sbv_loglik_fp64_noalloc(const void* X, int dtype, const double* y
   if (!X || !y || !ptr || !pts || !cnt || !ll || !theta || (m > 0 && !nbr)) return SBV_EINVAL;
   if (dtype != SBV_F64 && dtype != SBV_F32) return SBV_EINVAL;
   if (n < 1 || d < 1 || d > SBV_MAX_DIM || bc < 1 || bc > n || m < 0 || nmax < 0) return SBV_EINVAL;
-  if (nu2 != 1 && nu2 != 3 && nu2 != 5 && nu2 != 7) return SBV_EINVAL;
+  // the FP64 kernel evaluates the closed forms and, for any other nu2, K_nu
+  if (nu2 < 1 || nu2 > SBV_MAX_NU2) return SBV_EINVAL;
   if (B < 1 || B > SBV_NOALLOC_MAX_THETA) return SBV_EUNSUPPORTED;
   if (!block_terms && (uint64_t)bc * (uint64_t)B > (uint64_t)SBV_NOALLOC_MAX_TERMS)
     return SBV_EUNSUPPORTED;
@@ -159,8 +160,12 @@ extern "C" int sbv_loglik_fp64_noalloc(const void* X, int dtype, const double* y
   if (per_sm > 4) per_sm = 4;
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > bc * (int64_t)B) grid = bc * (int64_t)B;
+  // the same limit sbv_loglik's FP64 path sets (the largest opt-in minus the
+  // static shared memory), never this call's smaller size: the attribute is
+  // per kernel and per process, and later sbv_loglik launches with larger
+  // blocks rely on it
   if (cudaFuncSetAttribute(loglik_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
+                           optin - 1024) != cudaSuccess)
     return SBV_ECUDA;
   loglik_fp64_kernel<<<(int)grid, NA_THREADS, smem, s>>>(a);
   if (cudaGetLastError() != cudaSuccess) return SBV_ECUDA;

@@ -48,6 +48,8 @@ def test_null_context_is_rejected_without_device(lib):
     rc = lib.sbv_blocking(None, None, 0, 0, 0, None, 0, 0, 0, None, None, None, None, None, None,
                           None)
     assert rc == 1
+    v = C.c_double(0.0)
+    assert lib.sbv_peak_probe(None, 0, C.byref(v)) == 1
     rc = lib.sbv_loglik_grad(None, None, 0, None, 0, 0, None, None, None, None, 0, 0, 0, None, 0,
                              0, None, None, None, None, None, None)
     assert rc == 1

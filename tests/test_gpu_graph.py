@@ -58,6 +58,28 @@ def test_graph_replay_equals_loglik(setup, precision):
         assert torch.equal(out, ref), (precision, k, (out - ref).abs().max().item())
 
 
+def test_graph_general_smoothness_fp64(setup):
+    # the captured FP64 kernel takes any nu = nu2/2 (Eq. maternkernel through
+    # K_nu) exactly as sbv_loglik does; the mixed precisions keep the closed forms
+    from paper_2504_12004_gb300 import SBVError
+    s = setup
+    ctx, b = s["ctx"], s["b"]
+    th = s["th"][0]
+    ref = ctx.sbv_loglik(s["X"], s["y"], b["ptr"], b["pts"], s["nbr"], s["cnt"], th, nu2=4,
+                         precision="fp64").clone()
+    g = ctx.sbv_loglik_graph_create(s["X"], s["y"], b["ptr"], b["pts"], s["nbr"], s["cnt"],
+                                    B=th.shape[0], nu2=4, precision="fp64")
+    try:
+        out = g.launch(th).clone()
+        torch.cuda.synchronize()
+    finally:
+        g.close()
+    assert torch.equal(out, ref)
+    with pytest.raises(SBVError):
+        ctx.sbv_loglik_graph_create(s["X"], s["y"], b["ptr"], b["pts"], s["nbr"], s["cnt"],
+                                    B=th.shape[0], nu2=4, precision="mixed")
+
+
 def test_graph_rejects_bad_rows(setup):
     from paper_2504_12004_gb300 import SBVError
     s = setup

@@ -63,6 +63,71 @@ def test_noalloc_matches_loglik_on_two_calls():
         assert np.max(np.abs(o - r)) / n <= TOL_FP64, (o, r)
 
 
+def _structure(ctx, n, bc, m, seed):
+    from synth.inputs import workload
+    w = workload("sine10d", n=n, bc=bc, m=m)
+    X = torch.from_numpy(w["X"]).cuda()
+    y = torch.from_numpy(w["y"]).cuda()
+    b = ctx.sbv_blocking(X, w["beta_scale"], w["bc"], 3, seed)
+    nbr, cnt = ctx.sbv_knn(X, w["beta_scale"], b["ptr"], b["pts"], b["rank"], b["centres"], w["m"])
+    return w, X, y, b, nbr.contiguous(), cnt
+
+
+def _noalloc(lib, X, y, b, nbr, cnt, th, nu2):
+    th = np.ascontiguousarray(th, dtype=np.float64)
+    ll = torch.empty(th.shape[0], dtype=torch.float64, device="cuda")
+    n, d = X.shape
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = lib.sbv_loglik_fp64_noalloc(
+        _p(X), 0, _p(y), n, d, _p(b["ptr"]), _p(b["pts"]), _p(nbr), _p(cnt), cnt.numel(),
+        nbr.shape[1], 0, th.ctypes.data_as(C.c_void_p), th.shape[0], nu2, _p(ll), None, None,
+        stream)
+    return rc, ll
+
+
+def test_noalloc_general_smoothness():
+    # nu = 2 (nu2 = 4) goes through the Bessel form of the FP64 kernel, as in sbv_loglik
+    from paper_2504_12004_gb300 import build, Context, _lib
+
+    build.build()
+    lib = _lib.load()
+    ctx = Context(0)
+    w, X, y, b, nbr, cnt = _structure(ctx, 8000, 160, 30, 5)
+    th = w["theta"]
+    ref = ctx.sbv_loglik(X, y, b["ptr"], b["pts"], nbr, cnt, th, nu2=4, precision="fp64")
+    rc, ll = _noalloc(lib, X, y, b, nbr, cnt, th, 4)
+    torch.cuda.synchronize()
+    assert rc == 0
+    assert np.max(np.abs(ll.cpu().numpy() - ref.cpu().numpy())) / X.shape[0] <= TOL_FP64
+
+
+def test_loglik_after_noalloc_with_larger_blocks():
+    # a small no-alloc call must leave sbv_loglik's FP64 kernel able to take
+    # blocks that need more shared memory later in the same process
+    from paper_2504_12004_gb300 import build, Context, _lib
+
+    build.build()
+    lib = _lib.load()
+    ctx = Context(0)
+    w1, X1, y1, b1, nbr1, cnt1 = _structure(ctx, 4000, 400, 8, 3)
+    # sbv_loglik first (its one-time set-up of the kernel), then the small
+    # no-alloc call, then sbv_loglik with blocks of ~170 points
+    ctx.sbv_loglik(X1, y1, b1["ptr"], b1["pts"], nbr1, cnt1, w1["theta"], nu2=5, precision="fp64")
+    rc, _ = _noalloc(lib, X1, y1, b1, nbr1, cnt1, w1["theta"], 5)
+    torch.cuda.synchronize()
+    assert rc == 0
+    w2, X2, y2, b2, nbr2, cnt2 = _structure(ctx, 20000, 400, 120, 4)
+    got = ctx.sbv_loglik(X2, y2, b2["ptr"], b2["pts"], nbr2, cnt2, w2["theta"], nu2=5,
+                         precision="fp64")
+    rc, ll = _noalloc(lib, X2, y2, b2, nbr2, cnt2, w2["theta"], 5)
+    torch.cuda.synchronize()
+    assert rc == 0
+    ctx.sbv_sync_status()
+    g, o = got.cpu().numpy(), ll.cpu().numpy()
+    assert np.all(np.isfinite(g))
+    assert np.max(np.abs(g - o)) / X2.shape[0] <= TOL_FP64
+
+
 def test_noalloc_rejects_sizes_beyond_its_limits():
     from paper_2504_12004_gb300 import build, _lib
 
