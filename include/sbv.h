@@ -57,10 +57,10 @@ extern "C" {
 
 /* arithmetic of the per-block factorisation */
 #define SBV_PREC_FP64       0  /* everything in FP64 */
-#define SBV_PREC_MIXED      1  /* FP32 factorisation (CUDA cores); FP64-accurate covariance,
-                                  diagonal-tile subtraction, log-det and one refinement step */
-#define SBV_PREC_MIXED_BF16 2  /* as SBV_PREC_MIXED with the trailing updates on the tensor
-                                  cores (tcgen05, split BF16 operands, FP32 accumulators) */
+#define SBV_PREC_MIXED      1  /* FP32 factor of Sigma_JJ; double-float covariance, residual
+                                  and Schur complement (third-order corrected); double-float
+                                  LDL^T of the bs x bs conditional system */
+#define SBV_PREC_MIXED_BF16 2  /* as SBV_PREC_MIXED (the same kernel in this version) */
 
 /* compiled limits */
 #define SBV_MAX_DIM      64     /* d */
@@ -205,10 +205,19 @@ int sbv_set_knn_mode(sbv_ctx* ctx, int32_t mode);
  * and L its Cholesky factor, w = L^{-1} [y_J; y_B] and
  *   l_{b,i} = -1/2 [ bs_i log(2 pi) + 2 sum_{t in B} log L_tt + sum_{t in B} w_t^2 ],
  * which equals the POTRF/TRSM/GEMM/Schur/POTRF/TRSV chain of Alg. 5 (with
- * Sigma^lk in the Schur step).  The sum over blocks is a fixed-order tree, so
- * repeated calls give bit-identical results.  The call only enqueues work on
- * `stream` and returns; failures inside kernels are reported through
- * `status`, NaN totals, and sbv_sync_status().
+ * Sigma^lk in the Schur step).  The mixed precisions follow that chain: an
+ * FP32 factor of Sigma_JJ gives approximate kriging weights X, one
+ * double-float residual R = Sigma_JB - Sigma_JJ X corrects the conditional
+ * covariance and mean to third order in the error of X,
+ *   Sigma^new = Sigma_BB - Sigma_BJ X - X^T R - (L^{-1} R)^T (L^{-1} R),
+ * and a double-float LDL^T of Sigma^new gives the log-determinant and the
+ * quadratic form.  A block whose FP32 or double-float pivot is not positive,
+ * or whose conditional system exceeds the kernel's capacity, is recomputed
+ * by the FP64 kernel in the same call (counted by sbv_fp64_reruns).  The sum
+ * over blocks is a fixed-order tree, so repeated calls give bit-identical
+ * results.  The call only enqueues work on `stream` and returns; failures
+ * inside kernels are reported through `status`, NaN totals, and
+ * sbv_sync_status().
  * Errors (argument checks, before any work): SBV_EINVAL (null pointers,
  * B < 1, sigma^2 <= 0, tau^2 < 0, beta <= 0, bad nu2 or precision),
  * SBV_EUNSUPPORTED (a block with m_i + bs_i > SBV_MAX_BLOCK_N), SBV_ENOMEM,
@@ -259,6 +268,16 @@ int sbv_loglik_grad(sbv_ctx* ctx, const void* X, int dtype, const double* y, int
  * error (SBV_ECUDA).  Clears the record.
  */
 int sbv_sync_status(sbv_ctx* ctx, void* stream);
+
+/*
+ * sbv_fp64_reruns -- wait for `stream`, then write to *count (host) how many
+ * (theta, block) items or test points the mixed-precision kernels handed to
+ * the FP64 kernels since the last sbv_sync_status (which clears the count):
+ * items with a non-positive FP32 or double-float pivot, or whose conditional
+ * system exceeds the mixed kernel's capacity.  Their results are the FP64
+ * path's.  Errors: SBV_EINVAL (null ctx or count), SBV_ECUDA.
+ */
+int sbv_fp64_reruns(sbv_ctx* ctx, void* stream, int64_t* count);
 
 /*
  * sbv_predict -- Block Vecchia prediction with one test point per block

@@ -79,6 +79,7 @@ SIGNATURES = {
     "sbv_loglik_grad": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64, _I32,
                                   _I32, _P, _I32, _I32, _P, _P, _P, _P, _P, _P]),
     "sbv_sync_status": (C.c_int, [_P, _P]),
+    "sbv_fp64_reruns": (C.c_int, [_P, _P, C.POINTER(_I64)]),
     "sbv_set_knn_mode": (C.c_int, [_P, _I32]),
     "sbv_predict": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _I64, _P, _I32, _P,
                               _I32, _I32, _P, _P, _P, _P, _P]),
@@ -377,6 +378,12 @@ class Context:
 
     def sbv_sync_status(self, stream=None):
         self._check(self.lib.sbv_sync_status(self.h, _stream(stream)))
+
+    def sbv_fp64_reruns(self, stream=None) -> int:
+        """Items the mixed kernels handed to the FP64 kernels since the last sbv_sync_status."""
+        c = C.c_int64(0)
+        self._check(self.lib.sbv_fp64_reruns(self.h, _stream(stream), C.byref(c)))
+        return c.value
 
     def sbv_predict(self, X, y, Xtest, beta_scale, m_pred: int, theta, nu2: int = 5,
                     precision="fp64", want_nbr=False, stream=None, blocks=None):

@@ -65,6 +65,10 @@ struct LoglikArgs {
   unsigned int* counter;   // work counter
   double* gmat;            // global scratch (one matrix per CTA) or NULL
   size_t gmat_stride;      // doubles per CTA slice
+  // list mode (FP64 kernels only): when `list` is not NULL the items are
+  // list[0 .. *list_n - 1] (filled by a previous kernel on the stream)
+  const unsigned int* list;
+  const unsigned int* list_n;
 };
 
 template <typename T>
@@ -81,6 +85,11 @@ struct Fp64Plan {
 int fp64_plan(sbv_ctx* ctx, int nmax, int d, int64_t items, Fp64Plan* o);
 int fp64_enqueue(sbv_ctx* ctx, const LoglikArgs& a, const Fp64Plan& o, cudaStream_t s);
 int fp64_prepare(sbv_ctx* ctx);
+// FP64 kernel over the items a mixed kernel handed over (list mode); the
+// global matrices come from gmat_owned, or the context workspace when NULL
+int fp64_fallback_enqueue(sbv_ctx* ctx, const LoglikArgs& a, int nmax, const unsigned int* list,
+                          const unsigned int* list_n, unsigned int* counter, cudaStream_t s,
+                          double* gmat_owned = nullptr);
 int run_max_n(sbv_ctx* ctx, const int64_t* ptr, const int32_t* cnt, int64_t bc, int* out,
               cudaStream_t s);
 int reduce_enqueue(sbv_ctx* ctx, const double* terms, int64_t bc, int B, double* ll,

@@ -81,6 +81,29 @@ __device__ __forceinline__ df df_sqrt(df s) {
   return fast_two_sum(rh, rl);
 }
 
+// acc -= s * x for a double-float s (float pair) and a float x: the product
+// s.h x is split exactly into p + e (FMA), s.l x is added to e; acc.l is left
+// unnormalised (the caller renormalises once at the end of a dot product).
+__device__ __forceinline__ void df_fnma_acc(df& acc, float2 s, float x) {
+  const float p = __fmul_rn(s.x, x);
+  float e = __fmaf_rn(s.x, x, -p);
+  e = __fmaf_rn(s.y, x, e);
+  const df t = two_sum(acc.h, -p);
+  acc.h = t.h;
+  acc.l = __fadd_rn(acc.l, __fsub_rn(t.l, e));
+}
+
+// 1 / x for a positive double-float: the float reciprocal plus one Newton
+// correction from the exact residual 1 - x r (about 46 significant bits).
+__device__ __forceinline__ df df_recip(df x) {
+  const float r = __frcp_rn(x.h);
+  const float p = __fmul_rn(x.h, r);
+  const float pe = __fmaf_rn(x.h, r, -p);
+  // 1 - x r = (1 - p) - pe - x.l r, with 1 - p exact (p is within an ulp of 1)
+  const float e = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, p), pe), __fmul_rn(x.l, r));
+  return fast_two_sum(r, __fmul_rn(r, e));
+}
+
 // Constants of the double-float exponential, filled from host FP64 values:
 // 1/ln2, ln2, 1/3, 2/5, 1/15 and the table 2^(-i/256), i = 0..255.
 struct DfConsts {

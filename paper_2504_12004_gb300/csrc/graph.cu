@@ -23,7 +23,7 @@ struct sbv_graph {
   ThetaDev* d_theta = nullptr;      // parameter rows read by the captured kernel
   ThetaDev* h_theta = nullptr;      // pinned staging of the rows
   cudaEvent_t staged = nullptr;     // recorded after the copy out of h_theta
-  void* owned[6] = {};              // device buffers owned by the graph
+  void* owned[8] = {};              // device buffers owned by the graph
 };
 
 namespace {
@@ -158,19 +158,29 @@ extern "C" int sbv_loglik_graph_create(sbv_ctx* ctx, const void* X, int dtype, c
   MixedArgs P;
   MixedPlan mp;
   Fp64Plan fp;
+  double* fb_gmat = nullptr;
   if (mixed) {
     memset(&P, 0, sizeof(P));
     P.a = a;
-    if ((st = mixed_plan(ctx, nmax, d, precision, false, items, &mp))) return bail(st);
+    if ((st = mixed_plan(ctx, nmax, m, d, precision, false, items, &mp))) return bail(st);
     if (dtype == SBV_F64) {  // X is fixed: split it once, outside the graph
       if ((st = own(g, 3, (size_t)n * d * sizeof(float2), &p))) return bail(st);
       if ((st = mixed_split(ctx, X, dtype, n * d, (float2*)p, cap))) return bail(st);
       P.Xs = (const float2*)p;
     }
     if ((st = own(g, 4, mp.scratch_bytes(), &p))) return bail(st);
-    P.scratch = (float2*)p;
-    P.gA = mp.lay.ga ? (float*)((unsigned char*)p + mp.ga_offset()) : nullptr;
-    if ((st = mixed_prepare(ctx))) return bail(st);
+    P.gbase = (float*)p;
+    // hand-over list and the FP64 kernel's global matrices (when its blocks
+    // do not fit shared memory)
+    if ((st = own(g, 6, (size_t)items * sizeof(unsigned int), &p))) return bail(st);
+    P.fb_list = (unsigned int*)p;
+    P.fb_count = counter + 1;
+    if ((st = fp64_plan(ctx, nmax, d, items, &fp))) return bail(st);
+    if (fp.gmat_stride) {
+      if ((st = own(g, 7, fp.gmat_stride * fp.grid * sizeof(double), &p))) return bail(st);
+      fb_gmat = (double*)p;
+    }
+    if ((st = mixed_prepare(ctx)) || (st = fp64_prepare(ctx))) return bail(st);
   } else {
     if ((st = fp64_plan(ctx, nmax, d, items, &fp))) return bail(st);
     if (fp.gmat_stride) {
@@ -184,8 +194,11 @@ extern "C" int sbv_loglik_graph_create(sbv_ctx* ctx, const void* X, int dtype, c
   // capture: reset the work counter, the block kernel, the deterministic sum
   SBV_CUDA_TRY(ctx, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
   int cst = SBV_OK;
-  if (cudaMemsetAsync(counter, 0, sizeof(unsigned int), cap) != cudaSuccess) cst = SBV_ECUDA;
+  // work counter, hand-over count, FP64 work counter
+  if (cudaMemsetAsync(counter, 0, 3 * sizeof(unsigned int), cap) != cudaSuccess) cst = SBV_ECUDA;
   if (!cst) cst = mixed ? mixed_enqueue(ctx, P, mp, cap) : fp64_enqueue(ctx, a, fp, cap);
+  if (!cst && mixed)
+    cst = fp64_fallback_enqueue(ctx, a, nmax, P.fb_list, counter + 1, counter + 2, cap, fb_gmat);
   if (!cst) cst = reduce_enqueue(ctx, terms, bc, B, ll, cap);
   cudaError_t e = cudaStreamEndCapture(cap, &g->graph);
   if (cst) return bail(cst);

@@ -140,14 +140,18 @@ loglik_fp64_kernel(LoglikArgs a) {
   double* u = sm;                               // d x (ncap+1)
   double* yv = u + (size_t)d * ustride;         // ncap+1
   double* A = a.gmat ? a.gmat + (size_t)blockIdx.x * a.gmat_stride : yv + ustride;
-  const unsigned int total = (unsigned int)(a.bc * a.B);
+  // all items, or (list mode) the items a previous kernel handed over
+  const unsigned int total = a.list ? *a.list_n : (unsigned int)(a.bc * a.B);
   const double log2pi = 1.8378770664093454836;
 
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
+    if (threadIdx.x == 0) {
+      const unsigned int k = atomicAdd(a.counter, 1u);
+      s_item = k < total ? (a.list ? a.list[k] : k) : 0xffffffffu;
+    }
     __syncthreads();
     const unsigned int item = s_item;
-    if (item >= total) break;
+    if (item == 0xffffffffu) break;
     const int th_i = (int)(item / a.bc);
     const int64_t blk = (int64_t)(item % a.bc);
     const ThetaDev& th = a.theta[th_i];
@@ -289,10 +293,10 @@ static int structure_max_n(sbv_ctx* ctx, const int64_t* ptr, const int32_t* cnt,
 }
 
 int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a, int nmax, int precision,
-                        cudaStream_t s);
+                        unsigned int* fb_list, unsigned int* fb_count, cudaStream_t s);
 int launch_predict_mixed(sbv_ctx* ctx, const LoglikArgs& a0, const void* Xt, int64_t nt,
                          double* mean, double* var, double* var_latent, int precision,
-                         cudaStream_t s);
+                         unsigned int* fb_list, unsigned int* fb_count, cudaStream_t s);
 
 int run_max_n(sbv_ctx* ctx, const int64_t* ptr, const int32_t* cnt, int64_t bc, int* out,
               cudaStream_t s) {
@@ -364,6 +368,31 @@ int reduce_enqueue(sbv_ctx* ctx, const double* terms, int64_t bc, int B, double*
   return SBV_OK;
 }
 
+// FP64 kernel in list mode over the items the mixed kernel handed over
+// (list[0 .. *list_n - 1]); a persistent grid whose CTAs leave at once when
+// the list is empty.
+int fp64_fallback_enqueue(sbv_ctx* ctx, const LoglikArgs& a0, int nmax, const unsigned int* list,
+                          const unsigned int* list_n, unsigned int* counter, cudaStream_t s,
+                          double* gmat_owned) {
+  int st = 0;
+  LoglikArgs a = a0;
+  a.list = list;
+  a.list_n = list_n;
+  a.counter = counter;
+  Fp64Plan o;
+  if ((st = fp64_plan(ctx, nmax, a.d, a.bc * (int64_t)a.B, &o))) return st;
+  if (o.gmat_stride) {
+    double* g = gmat_owned;
+    if (!g) {
+      g = (double*)ws_get(ctx, WS_GMAT64, o.gmat_stride * o.grid * sizeof(double), &st);
+      if (!g) return st;
+    }
+    a.gmat = g;
+    a.gmat_stride = o.gmat_stride;
+  }
+  return fp64_enqueue(ctx, a, o, s);
+}
+
 int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n, int d,
                const int64_t* ptr, const int32_t* pts, const int32_t* nbr, const int32_t* cnt,
                int64_t bc, int m, int nmax_hint, const double* h_theta, int B, int nu2,
@@ -383,10 +412,12 @@ int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t 
   }
   unsigned int* counter = (unsigned int*)ws_get(ctx, WS_SMALL, 64, &st);
   if (!counter) return st;
-  counter += 4;  // first words hold the max-N scratch
-  SBV_CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
+  counter += 4;  // first words hold the max-N scratch; then the work counter,
+                 // the hand-over count and the FP64 kernel's work counter
+  SBV_CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, 3 * sizeof(unsigned int), s));
 
   LoglikArgs a;
+  memset(&a, 0, sizeof(a));
   a.X = X;
   a.dtype = dtype;
   a.y = y;
@@ -410,7 +441,12 @@ int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t 
   a.gmat_stride = 0;
 
   if (precision == SBV_PREC_MIXED || precision == SBV_PREC_MIXED_BF16) {
-    if ((st = launch_loglik_mixed(ctx, a, nmax, precision, s))) return st;
+    unsigned int* list =
+        (unsigned int*)ws_get(ctx, WS_RERUN, (size_t)B * bc * sizeof(unsigned int), &st);
+    if (!list) return st;
+    if ((st = launch_loglik_mixed(ctx, a, nmax, precision, list, counter + 1, s))) return st;
+    // the items handed over (pivots, capacity) go through the FP64 kernel
+    if ((st = fp64_fallback_enqueue(ctx, a, nmax, list, counter + 1, counter + 2, s))) return st;
   } else {
     Fp64Plan o;
     if ((st = fp64_plan(ctx, nmax, d, bc * (int64_t)B, &o))) return st;
@@ -683,6 +719,7 @@ int run_loglik_grad(sbv_ctx* ctx, const void* X, int dtype, const double* y, int
   int64_t grid = (int64_t)ctx->num_sms * std::max(1, std::min(2, (int)((228 * 1024) / (smem + 4096))));
   if (grid > bc * (int64_t)B) grid = std::max<int64_t>(bc * (int64_t)B, 1);
   LoglikArgs a;
+  memset(&a, 0, sizeof(a));
   a.X = X;
   a.dtype = dtype;
   a.y = y;
@@ -746,6 +783,8 @@ struct PredictArgs {
   unsigned int* counter;
   double* gmat;
   size_t gmat_stride;
+  const unsigned int* list;     // list mode: the test points handed over, or NULL
+  const unsigned int* list_n;
 };
 
 __global__ void __launch_bounds__(LL_THREADS)
@@ -761,11 +800,15 @@ predict_fp64_kernel(PredictArgs a) {
   double* yv = u + (size_t)d * ustride;
   double* A = a.gmat ? a.gmat + (size_t)blockIdx.x * a.gmat_stride : yv + ustride;
   const ThetaDev& th = a.theta[0];
+  const unsigned int total = a.list ? *a.list_n : (unsigned int)a.nt;
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
+    if (threadIdx.x == 0) {
+      const unsigned int k = atomicAdd(a.counter, 1u);
+      s_item = k < total ? (a.list ? a.list[k] : k) : 0xffffffffu;
+    }
     __syncthreads();
     const unsigned int item = s_item;
-    if (item >= a.nt) break;
+    if (item == 0xffffffffu) break;
     for (int e = threadIdx.x; e < N * d; e += blockDim.x) {
       int p = e / d, t = e - p * d;
       double x;
@@ -817,8 +860,11 @@ int run_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t
   unsigned int* counter = (unsigned int*)ws_get(ctx, WS_SMALL, 64, &st);
   if (!counter) return st;
   counter += 4;
-  SBV_CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
+  SBV_CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, 3 * sizeof(unsigned int), s));
+  unsigned int* list = nullptr;
   if (precision != SBV_PREC_FP64) {
+    list = (unsigned int*)ws_get(ctx, WS_RERUN, (size_t)nt * sizeof(unsigned int), &st);
+    if (!list) return st;
     LoglikArgs la;
     memset(&la, 0, sizeof(la));
     la.X = X;
@@ -835,9 +881,12 @@ int run_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t
     la.ncap = m + 1;
     la.dstat = ctx->d_status;
     la.counter = counter;
-    return launch_predict_mixed(ctx, la, Xt, nt, mean, var, var_latent, precision, s);
+    if ((st = launch_predict_mixed(ctx, la, Xt, nt, mean, var, var_latent, precision, list,
+                                   counter + 1, s)))
+      return st;
   }
   PredictArgs a;
+  memset(&a, 0, sizeof(a));
   a.X = X;
   a.Xt = Xt;
   a.dtype = dtype;
@@ -855,6 +904,11 @@ int run_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t
   a.counter = counter;
   a.gmat = nullptr;
   a.gmat_stride = 0;
+  if (list) {  // FP64 pass over the test points the mixed kernel handed over
+    a.list = list;
+    a.list_n = counter + 1;
+    a.counter = counter + 2;
+  }
   const int N = m + 1;
   const size_t ub = (size_t)(d + 1) * (N + 1) * sizeof(double);
   const size_t mat = (size_t)(N + 1) * (N + 2) / 2 * sizeof(double);
@@ -869,7 +923,7 @@ int run_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t
       return fail(ctx, SBV_EUNSUPPORTED, "d=%d with m_pred=%d exceeds shared memory", d, m);
     grid = ctx->num_sms * 2;
     size_t stride = (mat / sizeof(double) + 31) & ~(size_t)31;
-    double* g = (double*)ws_get(ctx, WS_MATRIX, stride * grid * sizeof(double), &st);
+    double* g = (double*)ws_get(ctx, WS_GMAT64, stride * grid * sizeof(double), &st);
     if (!g) return st;
     a.gmat = g;
     a.gmat_stride = stride;

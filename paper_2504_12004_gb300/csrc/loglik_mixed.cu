@@ -1,129 +1,56 @@
-// Mixed-precision block log-likelihood (Alg. 5 per block).
+// Mixed-precision block log-likelihood and prediction: Alg. 5 per block with
+// an FP32 factor of the neighbour covariance and a third-order corrected
+// Schur complement.
 //
-// Per (theta, block) item, one CTA:
-//  1. gather the N = m_i + bs_i points as double-float coordinates (split
-//     once per call from FP64 X), scale by 1/beta in double-float, centre on
-//     the first point and re-split on a common power-of-two grid so that every
+// Per (theta, block) item, one CTA.  J = the block's mb neighbours, B = its
+// bs points, B' = B plus the observations as a bordered right-hand side.
+//  1. gather the N = mb + bs points as double-float coordinates (split once
+//     per call from FP64 X), scale by 1/beta in double-float, centre on the
+//     first point and re-split on a common power-of-two grid so that every
 //     difference of the float heads is exact;
-//  2. evaluate the joint covariance in double-float (dfloat.cuh): the float
-//     head of each off-diagonal-tile entry feeds the FP32 factorisation; the
-//     full double-float matrix goes to a per-CTA scratch slice (L2-resident)
-//     for the diagonal tiles and the refinement residual;
-//  3. blocked right-looking Cholesky (16-column panels): each diagonal tile is
-//     formed as (double-float original) - (FP32-accumulated updates) with one
-//     exact subtraction, rounded, and factored in FP32 registers by one warp;
-//     FP32 panel solve; trailing update either FP32 on the CUDA cores
-//     (SBV_PREC_MIXED) or split-BF16 on the tensor cores with TMEM
-//     accumulators (SBV_PREC_MIXED_BF16); y is bordered as row N so the
-//     factorisation also yields w0 = L^{-1} y;
-//  4. the diagonal tiles are replaced by their inverses, which turns the
-//     diagonal steps of the triangular solves into small parallel products;
-//     x0 = L^-T w0 and x0_J = L_JJ^-T w0_J in FP32 (one two-column sweep);
-//  5. refinement of the two quadratic forms: each step forms r = y - Sigma x
-//     and r_J = y_J - Sigma_JJ x_J in double-float from the scratch matrix,
-//     w = L^{-1} r with the FP32 factor, and takes q = y^T x + x^T r + |w|^2
-//     (third order in the error of x) for both systems; a block stops once
-//     |w|^2 is below 1e-6 per point or stops halving, otherwise the backward
-//     solve corrects x for another step (at most six; prediction takes
-//     three);
-//  6. l_i = -1/2 [bs log 2pi + 2 sum_{t>=m} log L_tt + q - q_J],
-//     log L_tt = e ln2 + log(mantissa), sums in FP64.
-// y^T Sigma^{-1} y - y_J^T Sigma_JJ^{-1} y_J is the quadratic form of the
-// Schur complement Sigma^lk - Sigma^cor of Alg. 5 (applied to y_B - mu^new),
-// and the trailing log-determinant is its log-determinant.
+//  2. evaluate the joint covariance in double-float (dfloat.cuh): the full
+//     matrix goes to a per-CTA global slice, the float heads of Sigma_JJ to
+//     the packed triangle A and those of Sigma_{J,B'} = [Sigma_JB, y_J] to
+//     the right-hand-side block X (one row per member of B');
+//  3. POTRF of Sigma_JJ in FP32 (Alg. 5, l.7), blocked right-looking with
+//     16-column panels; each diagonal tile is formed as (double-float
+//     original) - (FP32 updates) and factored by one warp, looked ahead
+//     during the trailing update; the rows of X ride along as extra rows, so
+//     they leave as L^{-1} Sigma_{J,B'} (the TRSM and TRSV of Alg. 5, l.8-9);
+//  4. the diagonal tiles are replaced by their inverses;
+//  5. backward substitution: X <- Sigma~_JJ^{-1} Sigma_{J,B'} (FP32), i.e.
+//     the kriging weights of B and x_J = Sigma~^{-1} y_J;
+//  6. residual R = Sigma_{J,B'} - Sigma_JJ X in double-float from the global
+//     copy of Sigma (one extended-precision pass);
+//  7. the conditional system of Alg. 5 (GEMM, GEMV and the Schur
+//     subtraction, l.10-13) by the exact identity
+//        S' = Sigma_{B'B'} - Sigma_{B'J} X - X^T R - R^T Sigma_JJ^{-1} R,
+//     whose last term, taken with the FP32 factor as (L^{-1} R)^T (L^{-1} R),
+//     is the only approximation: the error is third order in the error of
+//     X.  S' holds Sigma^new (bs x bs) and, in its bordered row, y_B - mu^new;
+//  8. LDL^T of Sigma^new in double-float (one column per step), bordered
+//     by y_B - mu^new (POTRF and TRSV of Alg. 5, l.15-16); the log-
+//     determinant and the quadratic form (l.17-19) are summed in FP64:
+//        l_i = -1/2 [bs log 2pi + sum_t log d_t + sum_t z_t^2 / d_t].
+// Prediction is the same pipeline with B = {test point} and no y_B: the
+// mean is mu^new and the variance Sigma^new (Sec. 5.5).
+// An item whose FP32 or double-float pivot is not positive, or whose
+// conditional system does not fit the X region, is appended to a list that
+// the FP64 kernel processes right after this one (same stream).
 #include <math.h>
 #include <string.h>
 
 #include <algorithm>
 #include <vector>
 
-#include <cuda_bf16.h>
-
 #include "block_common.cuh"
 #include "dfloat.cuh"
 #include "mixed.cuh"
 #include "sbv_internal.cuh"
-#include "umma.cuh"
 
 namespace sbv {
 
 static __constant__ DfConsts c_df;
-
-// ---------------------------------------------------------------------------
-// Triangular solves with the factor packed in A, whose diagonal tiles hold
-// the inverses of the diagonal blocks.  Two right-hand sides (lanes 0-15 and
-// 16-31 of warp 0 in the diagonal steps).
-// ---------------------------------------------------------------------------
-__device__ void fwd_solve2(const float* A, int N, float* b1, float* b2) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k0 = 0; k0 < N; k0 += NB) {
-    const int k1 = min(k0 + NB, N), nbk = k1 - k0;
-    if (warp == 0) {
-      const int r = lane & 15;
-      float* b = (lane >> 4) ? b2 : b1;
-      float v = 0.0f;
-      if (r < nbk) {
-        const float* Li = A + trp(k0 + r, k0);  // row r of the tile inverse
-        for (int c = 0; c <= r; ++c) v = fmaf(Li[c], b[k0 + c], v);
-      }
-      __syncwarp();
-      if (r < nbk) b[k0 + r] = v;
-    }
-    __syncthreads();
-    for (int i = k1 + threadIdx.x; i < N; i += blockDim.x) {
-      float s1 = 0.0f, s2 = 0.0f;
-      const float* Ai = A + trp(i, 0);
-      if (nbk == NB) {
-#pragma unroll
-        for (int k = 0; k < NB; k += 4) {
-          const float4 x = *(const float4*)(Ai + k0 + k);
-          const float4 p = *(const float4*)(b1 + k0 + k);
-          const float4 q = *(const float4*)(b2 + k0 + k);
-          s1 = fmaf(x.x, p.x, s1); s1 = fmaf(x.y, p.y, s1); s1 = fmaf(x.z, p.z, s1); s1 = fmaf(x.w, p.w, s1);
-          s2 = fmaf(x.x, q.x, s2); s2 = fmaf(x.y, q.y, s2); s2 = fmaf(x.z, q.z, s2); s2 = fmaf(x.w, q.w, s2);
-        }
-      } else {
-        for (int k = k0; k < k1; ++k) {
-          const float x = Ai[k];
-          s1 = fmaf(x, b1[k], s1);
-          s2 = fmaf(x, b2[k], s2);
-        }
-      }
-      b1[i] -= s1;
-      b2[i] -= s2;
-    }
-    __syncthreads();
-  }
-}
-
-__device__ void bwd_solve2(const float* A, int N, float* b1, float* b2) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntile = (N + NB - 1) / NB;
-  for (int kt = ntile - 1; kt >= 0; --kt) {
-    const int k0 = kt * NB, k1 = min(k0 + NB, N), nbk = k1 - k0;
-    if (warp == 0) {
-      const int r = lane & 15;
-      float* b = (lane >> 4) ? b2 : b1;
-      float v = 0.0f;
-      if (r < nbk)
-        for (int c = r; c < nbk; ++c) v = fmaf(A[trp(k0 + c, k0 + r)], b[k0 + c], v);
-      __syncwarp();
-      if (r < nbk) b[k0 + r] = v;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < k0; i += blockDim.x) {
-      float s1 = 0.0f, s2 = 0.0f;
-      for (int k = k0; k < k1; ++k) {
-        const float x = A[trp(k, i)];
-        s1 = fmaf(x, b1[k], s1);
-        s2 = fmaf(x, b2[k], s2);
-      }
-      b1[i] -= s1;
-      b2[i] -= s2;
-    }
-    __syncthreads();
-  }
-}
 
 // FP64 CTA sum, same value returned on every thread.
 __device__ double cta_sum_mx(double v, double* red) {
@@ -137,27 +64,6 @@ __device__ double cta_sum_mx(double v, double* red) {
   return s;
 }
 
-// Two sums over the CTA at once (red holds at least two doubles per warp).
-__device__ double2 cta_sum2_mx(double a, double b, double* red) {
-  for (int o = 16; o; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-  }
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) {
-    red[2 * (threadIdx.x >> 5)] = a;
-    red[2 * (threadIdx.x >> 5) + 1] = b;
-  }
-  __syncthreads();
-  double sa = 0.0, sb = 0.0;
-  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-    sa += red[2 * q];
-    sb += red[2 * q + 1];
-  }
-  __syncthreads();
-  return make_double2(sa, sb);
-}
-
 // X split once per call into float pairs (hi, lo), hi + lo = x to ~2^-48 relative.
 __global__ void split_points_kernel(const double* __restrict__ X, int64_t total,
                                     float2* __restrict__ out) {
@@ -169,80 +75,42 @@ __global__ void split_points_kernel(const double* __restrict__ X, int64_t total,
   }
 }
 
-template <int THREADS, bool TC, bool PRED, bool GA>
+template <int THREADS, bool PRED, bool GA>
 __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
 loglik_mixed_kernel(MixedArgs P) {
-  constexpr int MX_WARPS = THREADS / 32;
+  constexpr int NW = THREADS / 32;
   extern __shared__ __align__(128) unsigned char smem[];
   const LoglikArgs& a = P.a;
   const MixedLayout& lay = P.lay;
   float2* yv = (float2*)(smem + lay.off_y);
-  float* vec = (float*)(smem + lay.off_v);
-  float* vh = (float*)(smem + lay.off_u);
+  float* idiag = (float*)(smem + lay.off_v);
+  float* vh = (float*)(smem + lay.off_u);       // covariance phase
   float* vl = (float*)(smem + lay.off_vl);
-  float* Pt = (float*)(smem + lay.off_u);                 // FP32 panel, column-major
-  unsigned char* opnd = smem + lay.off_u;                 // BF16 panel pieces
-  float4* part = (float4*)(smem + lay.off_u);             // residual partial sums
-  float* A = GA ? P.gA + (size_t)blockIdx.x * lay.a_floats : (float*)(smem + lay.off_A);
-  float* tab_h = (float*)(smem + lay.off_tab);   // covariance phase only
+  float* tab_h = (float*)(smem + lay.off_tab);
   float* tab_l = tab_h + 256;
+  float* Pt = (float*)(smem + lay.off_u);       // factorisation phase
+  float2* s_tile = (float2*)(smem + lay.off_stile);
+  float* G = P.gbase + (size_t)blockIdx.x * lay.g_stride;
+  float2* S = (float2*)G;                       // double-float Sigma, N x N, column-major
+  float* Rg = G + lay.g_R;                      // residual block, then L^{-1} R
+  float2* Spg = (float2*)(G + lay.g_Sp);        // partial conditional system
+  float* A = GA ? G + lay.g_A : (float*)(smem + lay.off_A);
+  float* Xr = GA ? G + lay.g_X : (float*)(smem + lay.off_X);
   __shared__ unsigned int s_item;
   __shared__ int s_fail;
-  __shared__ double red[2 * MX_WARPS];
+  __shared__ double red[2 * NW];
   __shared__ float s_org_h[SBV_MAX_DIM], s_org_l[SBV_MAX_DIM];
   __shared__ float s_grid;
-  __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t mma_bar;
-  __shared__ int s_timeout;
+  __shared__ __align__(16) float s_col[2 * NB];   // column broadcast of the tile factorisation
   const DfConsts& C = c_df;
-  float2* S = P.scratch + (size_t)blockIdx.x * P.scratch_stride;
   const int d = a.d, cap = lay.ncap, PS = lay.pstride;
-  const uint32_t opnd_piece = lay.opnd_piece;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const unsigned int total = PRED ? (unsigned int)P.nt : (unsigned int)(a.bc * a.B);
   const double log2pi = 1.8378770664093454836;
-  const int vs = (cap + 4) & ~3;   // vector stride, a multiple of four floats
-  float* x0 = vec;
-  float* x0J = vec + vs;
-  float* r1 = vec + 2 * vs;
-  float* r2 = vec + 3 * vs;
-  float* ldiag = vec + 4 * vs;
-  float* idiag = vec + 5 * vs;
-  float* c1 = (float*)(smem + lay.off_c);   // live during refinement only
-  float* c2 = c1 + (cap + 1);
-  // refinement steps: one for the likelihood (its quadratic forms are second
-  // order in the solve error); three for prediction, whose variance
-  // sigma^2 + tau^2 - Sigma_*J z cancels and is first order in the error of z
-  constexpr int NREF = PRED ? 3 : 6;   // at most
-  // Likelihood: y^T Sigma^-1 y = y^T x + x^T r + r^T Sigma^-1 r exactly, for
-  // any x and r = y - Sigma x.  Every step forms r at the current x (double
-  // float) and w = L^-1 r (forward solve with the FP32 factor), and takes
-  // q = y^T x + x^T r + |w|^2 for both systems: the error is rho |w|^2, rho
-  // the FP32 factor's contraction, i.e. third order in the error of x.  The
-  // block stops once |w|^2 (both systems) is below REF_TOL per point of the
-  // block, or stops halving (the residual's rounding floor); only otherwise
-  // does the backward solve complete the correction of x for another step.
-  // Well-conditioned blocks finish after one residual and one forward solve.
-  constexpr double REF_TOL = 1e-6;
-  __shared__ double s_qvar;   // x^T r of the full system minus that of J
-  __shared__ __align__(16) float s_col[2 * NB];   // column broadcast of the tile factorisation
-  float2* s_tile = (float2*)(smem + lay.off_stile);  // a diagonal tile's originals (factorisation)
-
-  if (threadIdx.x == 0) s_timeout = 0;
-  uint32_t tmem_base = 0, mma_phase = 0;
-  if (TC) {
-    // 256 TMEM columns: two 128 x (<= 128) FP32 accumulators
-    if (warp == 0) umma::tmem_alloc(&s_tmem, 256);
-    if (threadIdx.x == 0) umma::mbar_init(&mma_bar, 1);
-    umma::fence_before_sync();
-    __syncthreads();
-    umma::fence_after_sync();
-    tmem_base = s_tmem;
-  }
-  __syncthreads();
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
 
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
+    if (tid == 0) s_item = atomicAdd(a.counter, 1u);
     __syncthreads();
     const unsigned int item = s_item;
     if (item >= total) break;
@@ -254,9 +122,11 @@ loglik_mixed_kernel(MixedArgs P) {
     const int bs = PRED ? 1 : (int)(a.ptr[blk + 1] - a.ptr[blk]);
     const int mb = PRED ? a.m : a.cnt[blk];
     const int N = mb + bs;
-    if (N > cap) {
-      if (threadIdx.x == 0) {
-        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    const int nr = bs + 1;               // rows of the right-hand-side block: B, then y
+    const int xs = rhs_stride(mb);
+    const int mb4 = (mb + 3) & ~3;
+    if (N > cap || mb > lay.mcap) {
+      if (tid == 0) {
         if (PRED) {
           P.mean[item] = nan;
           P.var[item] = nan;
@@ -270,38 +140,55 @@ loglik_mixed_kernel(MixedArgs P) {
       __syncthreads();
       continue;
     }
+    // hand the item to the FP64 kernel (capacity, or a pivot that is not positive)
+    auto hand_over = [&]() {
+      if (tid == 0) {
+        const unsigned int k = atomicAdd(P.fb_count, 1u);
+        P.fb_list[k] = item;
+        atomicAdd(&a.dstat->reruns, 1);
+      }
+      __syncthreads();
+    };
+    if ((size_t)nr * (nr + 1) > lay.x_floats) {
+      hand_over();
+      continue;
+    }
     const int64_t base = PRED ? 0 : a.ptr[blk];
+    // row i (0 <= i <= N) of the factorisation: J rows in A, B' rows in X
+    auto rowp = [&](int i) -> float* {
+      return i < mb ? A + trp(i, 0) : Xr + (size_t)(i - mb) * xs;
+    };
+
     // ---- 1. gather and scale in double-float; centre on point 0
-    if (threadIdx.x == 0) s_fail = 0;
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    if (tid == 0) s_fail = 0;
+    for (int i = tid; i < 256; i += THREADS) {
       tab_h[i] = C.tab_h[i];
       tab_l[i] = C.tab_l[i];
     }
-    for (int p = threadIdx.x; p < N; p += blockDim.x) {
+    for (int p = tid; p < N; p += THREADS) {
       if (PRED && p == mb) {
         yv[p] = make_float2(0.0f, 0.0f);  // the test point's observation is unknown
         continue;
       }
-      int64_t id = p < mb ? (int64_t)a.nbr[blk * a.m + p] : (int64_t)a.pts[base + (p - mb)];
+      const int64_t id = p < mb ? (int64_t)a.nbr[blk * a.m + p] : (int64_t)a.pts[base + (p - mb)];
       const double yy = a.y[id];
       const float yh = (float)yy;
       yv[p] = make_float2(yh, (float)(yy - (double)yh));
     }
-    for (int e = threadIdx.x; e < N * d; e += blockDim.x) {
+    for (int e = tid; e < N * d; e += THREADS) {
       const int p = e / d, t = e - p * d;
       df x;
       if (PRED && p == mb) {
         if (a.dtype == SBV_F64) {
-          const double xv = ((const double*)P.Xt)[(int64_t)item * d + t];
-          x = df_from_double(xv);
+          x = df_from_double(((const double*)P.Xt)[(int64_t)item * d + t]);
         } else {
           x = {((const float*)P.Xt)[(int64_t)item * d + t], 0.0f};
         }
       } else {
-        int64_t id = p < mb ? (int64_t)a.nbr[blk * a.m + p] : (int64_t)a.pts[base + (p - mb)];
+        const int64_t id = p < mb ? (int64_t)a.nbr[blk * a.m + p] : (int64_t)a.pts[base + (p - mb)];
         if (P.Xs) {
-          const float2 xs = P.Xs[id * d + t];
-          x = {xs.x, xs.y};
+          const float2 q = P.Xs[id * d + t];
+          x = {q.x, q.y};
         } else {
           x = {((const float*)a.X)[id * d + t], 0.0f};
         }
@@ -311,13 +198,13 @@ loglik_mixed_kernel(MixedArgs P) {
       vl[t * N + p] = u.l;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < d; t += blockDim.x) {
+    for (int t = tid; t < d; t += THREADS) {
       s_org_h[t] = vh[t * N];
       s_org_l[t] = vl[t * N];
     }
     __syncthreads();
     float mx = 0.0f;
-    for (int e = threadIdx.x; e < N * d; e += blockDim.x) {
+    for (int e = tid; e < N * d; e += THREADS) {
       const int t = e / N;
       const df v = df_sub_acc(df{vh[e], vl[e]}, df{s_org_h[t], s_org_l[t]});
       vh[e] = v.h;
@@ -327,9 +214,9 @@ loglik_mixed_kernel(MixedArgs P) {
     for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) red[warp] = (double)mx;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       float M = 0.0f;
-      for (int q = 0; q < MX_WARPS; ++q) M = fmaxf(M, (float)red[q]);
+      for (int q = 0; q < NW; ++q) M = fmaxf(M, (float)red[q]);
       int ex;
       frexpf(M * 1.0001f + 1e-30f, &ex);  // M < 2^ex
       s_grid = ldexpf(1.0f, ex - 22);      // |head| / grid < 2^22: heads and their differences exact
@@ -337,7 +224,7 @@ loglik_mixed_kernel(MixedArgs P) {
     __syncthreads();
     {
       const float g = s_grid, ig = 1.0f / g;  // powers of two: exact scaling
-      for (int e = threadIdx.x; e < N * d; e += blockDim.x) {
+      for (int e = tid; e < N * d; e += THREADS) {
         const float h = vh[e];
         const float hq = rintf(h * ig) * g;   // on the grid, exact
         vh[e] = hq;
@@ -350,9 +237,9 @@ loglik_mixed_kernel(MixedArgs P) {
       const df s2 = {th.s2_h, th.s2_l};
       const df diag = {th.diag_h, th.diag_l};
       const int npair = N * (N + 1) / 2;
-      int i = 0, j = threadIdx.x;
+      int i = 0, j = tid;
       while (j > i) { j -= i + 1; ++i; }
-      for (int l = threadIdx.x; l < npair; l += blockDim.x) {
+      for (int l = tid; l < npair; l += THREADS) {
         df K;
         if (i == j) {
           K = diag;
@@ -373,35 +260,35 @@ loglik_mixed_kernel(MixedArgs P) {
           const df r = df_sqrt(s);
           K = df_mul(s2, df_matern(r, s, a.nu2, C, tab_h, tab_l));
         }
-        // diagonal-tile entries start at 0 in A: A accumulates minus the updates
-        A[trp(i, j)] = (i / NB == j / NB) ? 0.0f : K.h;
+        if (j < mb) {
+          // the J columns: diagonal-tile entries of Sigma_JJ start at 0 in A
+          // (A accumulates minus the updates); B' rows carry the float head
+          if (i < mb)
+            A[trp(i, j)] = (i / NB == j / NB) ? 0.0f : K.h;
+          else
+            Xr[(size_t)(i - mb) * xs + j] = K.h;
+        }
         S[(size_t)j * N + i] = make_float2(K.h, K.l);
         S[(size_t)i * N + j] = make_float2(K.h, K.l);
-        j += blockDim.x;
+        j += THREADS;
         while (j > i) { j -= i + 1; ++i; }
       }
-      for (int p = threadIdx.x; p < N; p += blockDim.x) A[trp(N, p)] = yv[p].x;
+      for (int p = tid; p < mb; p += THREADS) Xr[(size_t)bs * xs + p] = yv[p].x;
     }
     __syncthreads();
-    // ---- 3. blocked Cholesky.  CUDA-core variant with look-ahead: while the
-    // other warps apply panel k to the trailing matrix, warp 0 first updates
-    // the next diagonal tile (the first ten 4 x 4 blocks of the trailing
-    // triangle) and factors it, so the tile factorisation overlaps the
-    // trailing update instead of following it.  The tensor-core variant
-    // factors each tile before its panel.
+    // ---- 3. FP32 POTRF of Sigma_JJ; the B' rows ride along as extra rows.
+    // While the other warps apply panel k to the trailing matrix, warp 0
+    // first updates the next diagonal tile and factors it (look-ahead).
     //
-    // factor_tile(k0), warp 0 only, lane r holding row r of the tile: the
+    // factor_tile(kt), warp 0 only, lane r holding row r of the tile: the
     // double-float original (staged in s_tile) plus the accumulated FP32
     // updates (held negated in A), one exact subtraction, then an FP32
-    // factorisation in registers; L, its diagonal and inverse diagonal are
-    // stored.
+    // factorisation in registers; L and its inverse diagonal are stored.
     // stage_tile(kt), warp 0: asynchronous copies (cp.async, 8 bytes each) of
-    // tile kt's double-float originals, lower triangle, column-major 16 x 16,
-    // from the scratch matrix into s_tile.  Issued one panel ahead, right
-    // after the previous tile was factored, so that the scratch matrix's DRAM
-    // latency is off the critical path; factor_tile waits for them.
+    // tile kt's double-float originals from the global copy of Sigma, one
+    // panel ahead, so that their latency is off the critical path.
     auto stage_tile = [&](const int kt) {
-      const int nt = min(kt + NB, N) - kt;
+      const int nt = min(kt + NB, mb) - kt;
       __syncwarp();   // the previous tile's reads of s_tile are done
 #pragma unroll
       for (int e = lane; e < NB * NB; e += 32) {
@@ -415,7 +302,7 @@ loglik_mixed_kernel(MixedArgs P) {
       asm volatile("cp.async.commit_group;" ::: "memory");
     };
     auto factor_tile = [&](const int kt) {
-      const int nt = min(kt + NB, N) - kt;
+      const int nt = min(kt + NB, mb) - kt;
       const int r = lane;
       asm volatile("cp.async.wait_all;" ::: "memory");
       __syncwarp();
@@ -432,8 +319,6 @@ loglik_mixed_kernel(MixedArgs P) {
         }
         row[c] = v;
       }
-      // right-looking elimination; column c is broadcast through shared memory
-      // (double-buffered, four floats per load) instead of one shuffle per entry
       bool bad = false;
       float rinv = 0.0f;   // 1 / L[r][r]
 #pragma unroll
@@ -443,10 +328,7 @@ loglik_mixed_kernel(MixedArgs P) {
         __syncwarp();
         const float dcc = cb[c];
         bad |= !(dcc > 0.0f);
-        // one reciprocal square root gives both the pivot and its inverse
-        // (a few ulp: ~1e-8 per point of the log-determinant, random)
         const float inv = rsqrtf(fmaxf(dcc, 1e-30f));
-        // a[r][c2] -= L[r][c] L[c2][c] = (a[r][c] / a[c][c]) a[c2][c]
         const float t = r > c ? row[c] * (inv * inv) : 0.0f;
         row[c] = r == c ? dcc * inv : row[c] * inv;
         if (r == c) rinv = inv;
@@ -460,31 +342,24 @@ loglik_mixed_kernel(MixedArgs P) {
         }
       }
       if (r < nt) {
-        float Lrr = 0.0f;
 #pragma unroll
-        for (int c = 0; c < NB; ++c) {
+        for (int c = 0; c < NB; ++c)
           if (c <= r) A[trp(kt + r, kt + c)] = row[c];
-          if (c == r) Lrr = row[c];
-        }
-        ldiag[kt + r] = Lrr;
         idiag[kt + r] = rinv;
       }
       if (bad && lane == 0) s_fail = 1;
     };
     // invert_tile(k0), one warp, lane r = row r: the tile's L is replaced in
-    // place by L^{-1}, row by row (forward substitution).  Row c is final
-    // once rows 0..c-1 are applied; lane c scales and stores it (16-byte
-    // aligned rows, zeros past the diagonal land in the row's padding) and
-    // the rows below read it back as broadcast float4 loads.  Only the
-    // triangle q <= c is touched.
+    // place by L^{-1}, row by row; only the triangle q <= c is touched (the
+    // zeros past the diagonal land in the row's padding).
     auto invert_tile = [&](const int k0) {
-      const int nbk = min(NB, N - k0);
+      const int nbk = min(NB, mb - k0);
       const int r = lane;
-      float Lr[NB], Xr[NB];
+      float Lr[NB], Xv[NB];
 #pragma unroll
       for (int c = 0; c < NB; ++c) {
         Lr[c] = (r < nbk && c <= r) ? A[trp(k0 + r, k0 + c)] : 0.0f;
-        Xr[c] = (c == r) ? 1.0f : 0.0f;
+        Xv[c] = (c == r) ? 1.0f : 0.0f;
       }
 #pragma unroll
       for (int c = 0; c < NB; ++c) {
@@ -493,10 +368,10 @@ loglik_mixed_kernel(MixedArgs P) {
           if (r == c) {
             const float ic = idiag[k0 + c];
 #pragma unroll
-            for (int q = 0; q <= c; ++q) Xr[q] *= ic;
+            for (int q = 0; q <= c; ++q) Xv[q] *= ic;
 #pragma unroll
             for (int q4 = 0; q4 <= c; q4 += 4)
-              *(float4*)(Xc + q4) = make_float4(Xr[q4], Xr[q4 + 1], Xr[q4 + 2], Xr[q4 + 3]);
+              *(float4*)(Xc + q4) = make_float4(Xv[q4], Xv[q4 + 1], Xv[q4 + 2], Xv[q4 + 3]);
           }
           __syncwarp();
           if (r > c) {
@@ -506,38 +381,30 @@ loglik_mixed_kernel(MixedArgs P) {
               const float x4[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
               for (int u = 0; u < 4; ++u)
-                if (q4 + u <= c) Xr[q4 + u] = fmaf(-Lr[c], x4[u], Xr[q4 + u]);
+                if (q4 + u <= c) Xv[q4 + u] = fmaf(-Lr[c], x4[u], Xv[q4 + u]);
             }
           }
         }
       }
       __syncwarp();
     };
-    if (!TC) {
+    if (mb > 0) {
       if (warp == 0) {
         stage_tile(0);
         factor_tile(0);
-        if (NB < N) stage_tile(NB);
+        if (NB < mb) stage_tile(NB);
       }
       __syncthreads();
     }
-    for (int k0 = 0; k0 < N; k0 += NB) {
-      const int k1 = min(k0 + NB, N), nbk = k1 - k0;
-      if (TC) {
-        if (warp == 0) {
-          if (k0 == 0) stage_tile(0);
-          factor_tile(k0);
-          if (k1 < N) stage_tile(k1);
-        }
-        __syncthreads();
-      }
+    for (int k0 = 0; k0 < mb; k0 += NB) {
+      const int k1 = min(k0 + NB, mb), nbk = k1 - k0;
       if (s_fail) break;
-      // panel solve: rows k1..N, A(i, k0:k1) <- A(i, k0:k1) L_kk^{-T}; the panel
-      // is also stored as the update operand (FP32 column-major, or BF16 pieces)
-      const int T = N + 1 - k1;  // trailing rows k1..N (the last one is y)
-      for (int i = k1 + threadIdx.x; i <= N; i += blockDim.x) {
+      // panel solve: rows k1..N, A(i, k0:k1) <- A(i, k0:k1) L_kk^{-T}; the
+      // panel is also stored column-major (Pt) as the update operand
+      const int T = N + 1 - k1;  // trailing rows k1..N (J rows, then B')
+      for (int i = k1 + tid; i <= N; i += THREADS) {
         float v[NB];
-        float* Ai = A + trp(i, 0) + k0;   // 16-byte aligned (padded rows)
+        float* Ai = rowp(i) + k0;   // 16-byte aligned
         const bool full = nbk == NB;
         if (full) {
 #pragma unroll
@@ -552,8 +419,6 @@ loglik_mixed_kernel(MixedArgs P) {
 #pragma unroll
         for (int c = 0; c < NB; ++c) {
           if (c < nbk) {
-            // row c of the tile, four entries per (broadcast) load; the
-            // entries at and past the diagonal are read but not used
             const float* Lc = A + trp(k0 + c, k0);
             float s = v[c];
 #pragma unroll
@@ -575,350 +440,422 @@ loglik_mixed_kernel(MixedArgs P) {
 #pragma unroll
         for (int c = 0; c < NB; ++c) {
           if (!full && c < nbk) Ai[c] = v[c];
-          if (TC) {
-            const __nv_bfloat16 bh = __float2bfloat16_rn(v[c]);
-            const float rr = v[c] - __bfloat162float(bh);           // exact
-            const __nv_bfloat16 bm = __float2bfloat16_rn(rr);
-            const __nv_bfloat16 bl = __float2bfloat16_rn(rr - __bfloat162float(bm));
-            const uint32_t o = umma::op_offset(row, c);
-            *(__nv_bfloat16*)(opnd + o) = bh;
-            *(__nv_bfloat16*)(opnd + opnd_piece + o) = bm;
-            *(__nv_bfloat16*)(opnd + 2 * opnd_piece + o) = bl;
-          } else {
-            Pt[c * PS + row] = v[c];
-          }
+          Pt[c * PS + row] = c < nbk ? v[c] : 0.0f;
         }
       }
-      if (!TC) {
-        // pad rows T .. round4(T) of the panel with zeros (read by the 4-row blocks)
-        for (int e = threadIdx.x; e < NB * 4; e += blockDim.x) {
-          const int c = e >> 2, row = T + (e & 3);
-          if (row < PS) Pt[c * PS + row] = 0.0f;
-        }
+      // pad rows T .. round4(T) of the panel with zeros (read by the 4-row blocks)
+      for (int e = tid; e < NB * 4; e += THREADS) {
+        const int c = e >> 2, row = T + (e & 3);
+        if (row < PS) Pt[c * PS + row] = 0.0f;
       }
-      if (TC) umma::fence_proxy_async();
       __syncthreads();
-      const int ncols_all = T - 1;  // matrix columns k1..N-1
-      if (!TC) {
-        // trailing update on the CUDA cores: 4 x 4 register blocks over the
-        // lower triangle, both operands read as float4 from the panel copy
-        if (ncols_all > 0) {
-          const int RB = (T + 3) >> 2;
-          const int nblk = RB * (RB + 1) / 2;
-          // blocks 0..9 (rows and columns k1 .. k1+15: the next diagonal tile)
-          // go to lanes 0..9 of warp 0, the rest to warps 1..
-          const int first = warp == 0 ? lane : 10 + (int)threadIdx.x - 32;
-          const int stride = warp == 0 ? 1 << 30 : (int)blockDim.x - 32;
-          const int lend = warp == 0 ? min(10, nblk) : nblk;
-          int bi = 0, bj = first;
-          while (bj > bi) { bj -= bi + 1; ++bi; }
-          for (int l = first; l < lend; l += stride) {
-            float acc[4][4];
+      // trailing update of the J columns k1..mb-1: 4 x 4 register blocks,
+      // (bi, bj <= bi) over the J rows, then every B' row block against every
+      // J column block; both operands read as float4 from the panel copy
+      const int CJ = (mb - k1 + 3) >> 2;     // J column blocks
+      if (CJ > 0) {
+        const int RB = (T + 3) >> 2;
+        const int ntri = CJ * (CJ + 1) / 2;
+        const int nblk = ntri + (RB - CJ) * CJ;
+        const int c4n = CJ < 4 ? CJ : 4;
+        const int nfirst = c4n * (c4n + 1) / 2;   // blocks of the next diagonal tile
+        const int first = warp == 0 ? lane : nfirst + tid - 32;
+        const int stride = warp == 0 ? 1 << 30 : THREADS - 32;
+        const int lend = warp == 0 ? nfirst : nblk;
+        for (int l = first; l < lend; l += stride) {
+          int bi, bj;
+          if (l < ntri) {
+            bi = (int)((sqrtf(8.0f * (float)l + 1.0f) - 1.0f) * 0.5f);
+            while (bi * (bi + 1) / 2 > l) --bi;
+            while ((bi + 1) * (bi + 2) / 2 <= l) ++bi;
+            bj = l - bi * (bi + 1) / 2;
+          } else {
+            const int q = l - ntri;
+            bi = CJ + q / CJ;
+            bj = q - (q / CJ) * CJ;
+          }
+          float acc[4][4];
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[p][q] = 0.0f;
+#pragma unroll 4
+          for (int k = 0; k < nbk; ++k) {
+            const float4 ar = *(const float4*)(Pt + k * PS + 4 * bi);
+            const float4 ac = *(const float4*)(Pt + k * PS + 4 * bj);
+            const float rr[4] = {ar.x, ar.y, ar.z, ar.w};
+            const float cc[4] = {ac.x, ac.y, ac.z, ac.w};
 #pragma unroll
             for (int p = 0; p < 4; ++p)
 #pragma unroll
-              for (int q = 0; q < 4; ++q) acc[p][q] = 0.0f;
-#pragma unroll 4
-            for (int k = 0; k < nbk; ++k) {
-              const float4 ar = *(const float4*)(Pt + k * PS + 4 * bi);
-              const float4 ac = *(const float4*)(Pt + k * PS + 4 * bj);
-              const float rr[4] = {ar.x, ar.y, ar.z, ar.w};
-              const float cc[4] = {ac.x, ac.y, ac.z, ac.w};
+              for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(rr[p], cc[q], acc[p][q]);
+          }
+          // one aligned float4 read-modify-write per block row; entries past
+          // the diagonal or past column mb - 1 land in padding that nothing
+          // reads as data (the B' rows' padding is cleared after the loop)
 #pragma unroll
-              for (int p = 0; p < 4; ++p)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(rr[p], cc[q], acc[p][q]);
-            }
-            // one aligned float4 read-modify-write per block row; in a
-            // diagonal block the entries past the diagonal land in the row's
-            // padding, which nothing reads
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-              const int ii = k1 + 4 * bi + p;
-              if (ii > N) continue;
-              float4* a4 = (float4*)(A + trp(ii, k1 + 4 * bj));
-              float4 w = *a4;
-              w.x -= acc[p][0];
-              w.y -= acc[p][1];
-              w.z -= acc[p][2];
-              w.w -= acc[p][3];
-              *a4 = w;
-            }
-            if (l + stride >= lend) break;   // before walking (bi, bj) that far
-            bj += stride;
-            while (bj > bi) { bj -= bi + 1; ++bi; }
+          for (int p = 0; p < 4; ++p) {
+            const int ii = k1 + 4 * bi + p;
+            if (ii > N) continue;
+            float4* a4 = (float4*)(rowp(ii) + k1 + 4 * bj);
+            float4 w = *a4;
+            w.x -= acc[p][0];
+            w.y -= acc[p][1];
+            w.z -= acc[p][2];
+            w.w -= acc[p][3];
+            *a4 = w;
           }
         }
-        if (warp == 0 && k1 < N) {
+        if (warp == 0) {
           __syncwarp();
           factor_tile(k1);
-          if (k1 + NB < N) stage_tile(k1 + NB);
-        }
-      } else {
-        // trailing update on the tensor cores: for each 128-row tile of P and
-        // each chunk of <= 128 columns, BF16 MMAs accumulate in TMEM (FP32):
-        // hi.hi alone in one accumulator, the five smaller cross products
-        // (lo.hi, hi.lo, mid.mid, mid.hi, hi.mid, small first) in a second
-        // one, so that no small product is added to a large partial sum
-        // inside the tensor core; the epilogue subtracts both from A.
-        for (int r0 = 0; r0 < T && ncols_all > 0; r0 += 128) {
-          const int ncols = min(r0 + 128, ncols_all);
-          for (int c0 = 0; c0 < ncols; c0 += 128) {
-            const int nc = min(128, ((ncols - c0 + 15) / 16) * 16);
-            if (threadIdx.x == 0) {
-              umma::fence_after_sync();
-              const uint32_t sb = umma::smem_u32(opnd);
-              const uint32_t idesc = umma::idesc_bf16_f32(128, nc);
-              const uint32_t arow = (uint32_t)(r0 / 8) * 256, brow = (uint32_t)(c0 / 8) * 256;
-              const int pa[6] = {0, 2, 0, 1, 1, 0}, pb[6] = {0, 0, 2, 1, 0, 1};
-#pragma unroll
-              for (int q = 0; q < 6; ++q) {
-                const uint64_t ad = umma::smem_desc(sb + pa[q] * opnd_piece + arow, 128, 256);
-                const uint64_t bd = umma::smem_desc(sb + pb[q] * opnd_piece + brow, 128, 256);
-                umma::mma_bf16(tmem_base + (q == 0 ? 0u : 128u), ad, bd, idesc, q > 1);
-              }
-              umma::mma_commit(&mma_bar);
-            }
-            const bool done = umma::mbar_wait(&mma_bar, mma_phase, 1u << 24);
-            mma_phase ^= 1u;
-            if (!done && threadIdx.x == 0) s_timeout = 1;
-            umma::fence_after_sync();
-            if (done) {
-              // warp w reads TMEM lanes 32 (w % 4) ..; the w / 4 groups split the columns
-              const int q = warp & 3, grp = warp >> 2;
-              const int ii = k1 + r0 + 32 * q + lane;  // matrix row of this lane
-              for (int cc = grp * 16; cc < nc; cc += 16 * (MX_WARPS / 4)) {
-                float dv[16], ds[16];
-                const uint32_t ta = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)cc;
-                umma::tmem_ld16(ta, dv);
-                umma::tmem_ld16(ta + 128u, ds);
-                umma::tmem_wait_ld();
-                if (ii <= N) {
-#pragma unroll
-                  for (int e = 0; e < 16; ++e) {
-                    const int jj = k1 + c0 + cc + e;
-                    if (jj <= ii && jj < N) A[trp(ii, jj)] = (A[trp(ii, jj)] - ds[e]) - dv[e];
-                  }
-                }
-              }
-            }
-            umma::fence_before_sync();
-            __syncthreads();
-            if (s_timeout) break;
-          }
-          if (s_timeout) break;
-        }
-        if (s_timeout) {
-          if (threadIdx.x == 0) s_fail = 2;
-          break;
+          if (k1 + NB < mb) stage_tile(k1 + NB);
         }
       }
       __syncthreads();
     }
     // a failed or cut-short factorisation can leave a staged tile in flight
     asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
     if (s_fail) {
-      if (threadIdx.x == 0) {
-        const int code = s_fail == 2 ? SBV_ETIMEOUT : SBV_ENOTSPD;
-        const double nan = __longlong_as_double(0x7ff8000000000000ll);
-        if (PRED) {
-          P.mean[item] = nan;
-          P.var[item] = nan;
-          P.var_latent[item] = nan;
-        } else {
-          a.terms[item] = nan;
-          if (a.status) a.status[item] = code;
-        }
-        record_failure(a.dstat, code, (int)blk, th_i);
-      }
-      __syncthreads();
-      if (s_timeout) break;  // leave the item loop; TMEM is released below
+      hand_over();
       continue;
     }
-    // ---- right-hand sides, read before the diagonal tiles are overwritten:
-    // x0 = w0 (row N of A, w0 = L^{-1} y) and x0J = w0_J, to become L^-T w0 and
-    // L_JJ^-T w0_J.  Prediction: x0 = w0_J (-> Sigma_JJ^-1 y_J) and x0J = l_*,
-    // the test point's row of L, which lies in the last diagonal tile
-    // (-> Sigma_JJ^-1 Sigma_J*); both vanish beyond J.
-    for (int p = threadIdx.x; p < N; p += blockDim.x) {
-      const float w = A[trp(N, p)];
-      if (PRED) {
-        x0[p] = p < mb ? w : 0.0f;
-        x0J[p] = p < mb ? A[trp(mb, p)] : 0.0f;
-      } else {
-        x0[p] = w;
-        x0J[p] = p < mb ? w : 0.0f;
-      }
+    // clear the padding of the B' rows (columns mb .. xs-1)
+    for (int e = tid; e < nr * (xs - mb); e += THREADS) {
+      const int r = e / (xs - mb);
+      Xr[(size_t)r * xs + mb + (e - r * (xs - mb))] = 0.0f;
     }
-    __syncthreads();
     // ---- 4. diagonal tiles -> their inverses (one warp per tile)
-    for (int k0 = warp * NB; k0 < N; k0 += MX_WARPS * NB) invert_tile(k0);
+    for (int k0 = warp * NB; k0 < mb; k0 += NW * NB) invert_tile(k0);
     __syncthreads();
-    bwd_solve2(A, N, x0, x0J);
-    for (int p = threadIdx.x; p < N; p += blockDim.x) {
-      c1[p] = 0.0f;
-      c2[p] = 0.0f;
-    }
-    __syncthreads();
-    double dq_prev = INFINITY;   // per item
-#pragma unroll 1
-    for (int it = 0; it < NREF; ++it) {
-    // ---- 5. residuals in double-float for x = x0 + c1 and x0J + c2; all
-    // warps: (32-row group, column chunk) tasks
-    {
-      const int G = (N + 31) / 32;
-      // column chunks: the count (within the partial-sum buffer) that
-      // minimises the columns the busiest warp walks
-      int CH = 1;
-      {
-        const int chmax = max(1, min(16, lay.part_cap / max(N, 1)));
-        int best = G * N;
-        for (int ch = 1; ch <= chmax; ++ch) {
-          const int cols = ((G * ch + MX_WARPS - 1) / MX_WARPS) * ((N + ch - 1) / ch);
-          if (cols < best) {
-            best = cols;
-            CH = ch;
+    const int ntile = (mb + NB - 1) / NB;
+    // ---- 5. X <- L^{-T} X (backward substitution, tile by tile)
+    for (int kt = ntile - 1; kt >= 0; --kt) {
+      const int k0 = kt * NB, nbk = min(NB, mb - k0);
+      // diagonal step, one thread per row: x = (L_kk^{-1})^T p
+      for (int r = tid; r < nr; r += THREADS) {
+        float* pr = Xr + (size_t)r * xs + k0;
+        float p[NB];
+#pragma unroll
+        for (int c = 0; c < NB; ++c) p[c] = c < nbk ? pr[c] : 0.0f;
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+          if (c < nbk) {
+            float s = 0.0f;
+#pragma unroll
+            for (int c2 = c; c2 < NB; ++c2)
+              if (c2 < nbk) s = fmaf(A[trp(k0 + c2, k0 + c)], p[c2], s);
+            pr[c] = s;
           }
         }
       }
-      const int chunk = (N + CH - 1) / CH;
-      for (int task = warp; task < G * CH; task += MX_WARPS) {
-        const int g = task / CH, c = task % CH;
-        const int i = g * 32 + lane;
-        const int j0 = c * chunk, j1 = min(N, j0 + chunk);
-        float h1 = 0.0f, l1 = 0.0f, h2 = 0.0f, l2 = 0.0f;
-        if (i < N) {
-          const bool inJ = i < mb;
-          // sixteen columns of the scratch matrix in flight per lane, then
-          // their products in column order
-          constexpr int RB = 16;
-          for (int jb = j0; jb < j1; jb += RB) {
-          float2 sv[RB];
+      __syncthreads();
+      // update of the columns before the tile: p[j] -= sum_c L[k0+c][j] x[k0+c]
+      const int nj4 = k0 >> 2;
+      for (int t = tid; t < nr * nj4; t += THREADS) {
+        const int r = t / nj4, j = (t - r * nj4) * 4;
+        float* pr = Xr + (size_t)r * xs;
+        float4 acc = *(const float4*)(pr + j);
+#pragma unroll 4
+        for (int c = 0; c < nbk; ++c) {
+          const float xc = pr[k0 + c];
+          const float4 l = *(const float4*)(A + trp(k0 + c, j));
+          acc.x = fmaf(-l.x, xc, acc.x);
+          acc.y = fmaf(-l.y, xc, acc.y);
+          acc.z = fmaf(-l.z, xc, acc.z);
+          acc.w = fmaf(-l.w, xc, acc.w);
+        }
+        *(float4*)(pr + j) = acc;
+      }
+      __syncthreads();
+    }
+    // ---- 6. the residual and the conditional system, 16 right-hand sides
+    // (columns r of X) at a time.  Products with Sigma are accumulated
+    // exactly on a per-column fixed-point grid: with Pmax_r = (sigma^2 +
+    // tau^2) max_k |X[r][k]| (every |Sigma_ij| <= sigma^2 + tau^2) and g_r =
+    // 2^(ceil(log2(max(mb, 4) Pmax_r)) - 24), the head of each product
+    // s.h x rounded to the grid (one FMA with C_r = 1.5 2^23 g_r) is exact and
+    // so is its sum over k' (< 2^24 g_r); the remainder s.h x - head (an
+    // FMA) plus s.l x is summed in FP32 over four terms and then folded into
+    // a float pair.
+    float* Rb = (float*)(smem + lay.off_u);      // residual block, then L^{-1} of it
+    float* colC = (float*)(smem + lay.off_cc);   // C_r per right-hand side
+    float2* Sch = (float2*)(smem + lay.off_sch); // staged columns of Sigma_JJ
+    float* Qg = Rg;                              // L^{-1} R for every column, global
+    for (int r = warp; r < nr; r += NW) {
+      float mxv = 0.0f;
+      for (int k = lane; k < mb; k += 32) mxv = fmaxf(mxv, fabsf(Xr[(size_t)r * xs + k]));
+      for (int o = 16; o; o >>= 1) mxv = fmaxf(mxv, __shfl_xor_sync(0xffffffffu, mxv, o));
+      if (lane == 0) {
+        const float pm = (float)(th.sigma2 + th.tau2) * mxv * (float)max(mb, 4) * 1.0001f;
+        int ex = -100;
+        if (pm > 0.0f) frexpf(pm, &ex);   // pm < 2^ex
+        colC[r] = 1.5f * ldexpf(1.0f, max(ex, -100) - 1);   // 1.5 * 2^23 * 2^(ex - 24)
+      }
+    }
+    __syncthreads();
+    constexpr int W = 16;
+    for (int cb = 0; cb < nr; cb += W) {
+      const int nc = min(W, nr - cb);
+      // 6a. Rb[c][k] = Sigma_{J,B'}[k][cb+c] - sum_k' Sigma_JJ[k][k'] X[cb+c][k']
+      // Sigma_JJ is streamed through shared memory in chunks of 8 columns
+      // (cp.async, double-buffered); thread (k, c0) keeps eight columns'
+      // accumulators in registers
+      {
+        constexpr int KC = 8;
+        const int nch = (mb + KC - 1) / KC;
+        auto stage_chunk = [&](int ch) {
+          float2* dst = Sch + (size_t)(ch & 1) * KC * lay.mcap;
+          const int kp0 = ch * KC, kn = min(KC, mb - kp0);
+          for (int e = tid; e < kn * mb; e += THREADS) {
+            const int c = e / mb, kk = e - c * mb;
+            const uint32_t sa = (uint32_t)__cvta_generic_to_shared(dst + (size_t)c * lay.mcap + kk);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa),
+                         "l"(S + (size_t)(kp0 + c) * N + kk) : "memory");
+          }
+          asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        // (k, c0) tasks: 2 mb of them, one pass of the CTA per THREADS tasks
+        for (int t0 = 0; t0 < 2 * mb; t0 += THREADS) {
+        const int tk = t0 + tid;
+        const bool act = tk < 2 * mb;
+        const int k = act ? tk % mb : 0, c0 = act ? (tk / mb) * 8 : 0;
+        float Cq[8], ahi[8];
+        df atot[8];
 #pragma unroll
-          for (int u = 0; u < RB; ++u)
-            sv[u] = jb + u < j1 ? S[(size_t)(jb + u) * N + i] : make_float2(0.0f, 0.0f);
+        for (int q = 0; q < 8; ++q) {
+          Cq[q] = act && c0 + q < nc ? colC[cb + c0 + q] : 1.0f;
+          ahi[q] = 0.0f;
+          atot[q] = {0.0f, 0.0f};
+        }
+        const float* xc = Xr + (size_t)(cb + c0) * xs;
+        if (nch > 0) stage_chunk(0);
+        for (int ch = 0; ch < nch; ++ch) {
+          if (ch + 1 < nch) {
+            stage_chunk(ch + 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+          } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+          }
+          __syncthreads();
+          if (act) {
+            const float2* sc = Sch + (size_t)(ch & 1) * KC * lay.mcap + k;
+            const int kp0 = ch * KC;
 #pragma unroll
-          for (int u = 0; u < RB; ++u) {
-            const int j = jb + u;
-            if (j >= j1) break;
-            const float2 s = sv[u];
-            const float xj = x0[j];
-            const float p = __fmul_rn(s.x, xj);
-            float pe = __fmaf_rn(s.x, xj, -p);
-            pe = __fmaf_rn(s.y, xj, pe);
-            pe = __fmaf_rn(s.x, c1[j], pe);
-            const df q = two_sum(h1, p);
-            h1 = q.h;
-            l1 = __fadd_rn(l1, __fadd_rn(q.l, pe));
-            if (inJ && j < mb) {
-              const float zj = x0J[j];
-              const float p2 = __fmul_rn(s.x, zj);
-              float pe2 = __fmaf_rn(s.x, zj, -p2);
-              pe2 = __fmaf_rn(s.y, zj, pe2);
-              pe2 = __fmaf_rn(s.x, c2[j], pe2);
-              const df q2 = two_sum(h2, p2);
-              h2 = q2.h;
-              l2 = __fadd_rn(l2, __fadd_rn(q2.l, pe2));
+            for (int h = 0; h < KC; h += 4) {
+              const int kp = kp0 + h;
+              if (kp < mb4) {
+                float2 sv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                  sv[u] = kp + u < mb ? sc[(size_t)(h + u) * lay.mcap] : make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                  if (c0 + q < nc) {
+                    const float4 x4 = *(const float4*)(xc + (size_t)q * xs + kp);
+                    const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+                    float alo = 0.0f;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                      const float ph = __fsub_rn(__fmaf_rn(sv[u].x, xv[u], Cq[q]), Cq[q]);
+                      float rr = __fmaf_rn(sv[u].x, xv[u], -ph);
+                      rr = __fmaf_rn(sv[u].y, xv[u], rr);
+                      ahi[q] = __fadd_rn(ahi[q], ph);
+                      alo = __fadd_rn(alo, rr);
+                    }
+                    const df u2 = two_sum(atot[q].h, alo);
+                    atot[q].h = u2.h;
+                    atot[q].l = __fadd_rn(atot[q].l, u2.l);
+                  }
+                }
+              }
             }
           }
+          __syncthreads();   // the chunk's buffer is refilled two steps later
+        }
+        if (act) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int r = cb + c0 + q;
+            if (c0 + q < nc) {
+              const float2 v = r < bs ? S[(size_t)(mb + r) * N + k] : yv[k];
+              df rv = df_sub_acc(df{v.x, v.y}, df{ahi[q], 0.0f});
+              rv = df_sub_acc(rv, atot[q]);
+              Rb[(size_t)(c0 + q) * xs + k] = __fadd_rn(rv.h, rv.l);
+            }
           }
-          part[(size_t)c * N + i] = make_float4(h1, l1, h2, l2);
+        }
+        }   // task passes
+      }
+      for (int e = tid; e < nc * (mb4 - mb); e += THREADS) {
+        const int c = e / (mb4 - mb);
+        Rb[(size_t)c * xs + mb + (e - c * (mb4 - mb))] = 0.0f;
+      }
+      __syncthreads();
+      // ---- 7. partial conditional system for the block's columns r < bs, rows a >= r:
+      // Sp[a][r] = Sigma_{B'B'}[a][r] - Sigma_{B'J}[a] X[r] (double-float)
+      //            - X[a] . R[r] (FP32)
+      // (row a = bs is the bordered y row: Sigma_{B'J}[bs] = y_J and
+      // Sigma_{B'B'}[bs][r] = y_{B,r})
+      {
+        const int ncb = min(nc, bs - cb);   // columns of Sigma^new in this block
+        const int na = nr - cb;
+        for (int t = tid; t < max(ncb, 0) * na; t += THREADS) {
+          const int c = t % ncb, ar = cb + t / ncb, r = cb + c;
+          if (ar < r) continue;
+          const float2 v0 = ar < bs ? S[(size_t)(mb + r) * N + (mb + ar)] : yv[mb + r];
+          df e = {v0.x, v0.y};
+          float d1 = 0.0f;
+          const float* xa = Xr + (size_t)ar * xs;
+          const float* xr = Xr + (size_t)r * xs;
+          const float* rr = Rb + (size_t)c * xs;
+          const float2* sa = ar < bs ? S + (size_t)(mb + ar) * N : yv;
+          for (int k = 0; k < mb4; k += 4) {
+            const float4 x4 = *(const float4*)(xr + k);
+            const float4 a4 = *(const float4*)(xa + k);
+            const float4 r4 = *(const float4*)(rr + k);
+            const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+            float2 sv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) sv[u] = k + u < mb ? sa[k + u] : make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) df_fnma_acc(e, sv[u], xv[u]);
+            d1 = fmaf(a4.x, r4.x, d1);
+            d1 = fmaf(a4.y, r4.y, d1);
+            d1 = fmaf(a4.z, r4.z, d1);
+            d1 = fmaf(a4.w, r4.w, d1);
+          }
+          e = fast_two_sum(e.h, e.l);
+          const df sres = df_add_f(e, -d1);
+          Spg[tri0(ar, r)] = make_float2(sres.h, sres.l);
+        }
+      }
+      // ---- 8. Rb <- L^{-1} Rb (forward substitution, tile by tile), then to global
+      for (int kt = 0; kt < ntile; ++kt) {
+        const int k0 = kt * NB, k1 = min(k0 + NB, mb), nbk = k1 - k0;
+        __syncthreads();   // the previous step's (or pass A's) reads of Rb are done
+        float xo = 0.0f;
+        const int c = tid >> 4, rr = tid & 15;   // 256 threads: 16 columns x 16 tile rows
+        const bool act = tid < 256 && c < nc && rr < nbk;
+        if (act) {
+          const float* Lr = A + trp(k0 + rr, k0);
+          const float* pc = Rb + (size_t)c * xs + k0;
+          for (int r2 = 0; r2 <= rr; ++r2) xo = fmaf(Lr[r2], pc[r2], xo);
+        }
+        __syncthreads();
+        if (act) Rb[(size_t)c * xs + k0 + rr] = xo;
+        __syncthreads();
+        const int ni4 = (mb - k1 + 3) >> 2;
+        for (int t = tid; t < nc * ni4; t += THREADS) {
+          const int cc = t / ni4, i = k1 + (t - cc * ni4) * 4;
+          float* pr = Rb + (size_t)cc * xs;
+          const float4 acc = *(const float4*)(pr + i);
+          float av[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll 4
+          for (int q = 0; q < nbk; ++q) {
+            const float qc = pr[k0 + q];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (i + u < mb) av[u] = fmaf(-A[trp(i + u, k0 + q)], qc, av[u]);
+          }
+          *(float4*)(pr + i) = make_float4(av[0], av[1], av[2], av[3]);
         }
       }
       __syncthreads();
-      for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        df s1 = {0.0f, 0.0f}, s2 = {0.0f, 0.0f};
-        for (int c = 0; c < CH; ++c) {
-          const float4 q = part[(size_t)c * N + i];
-          s1 = df_add(s1, fast_two_sum(q.x, q.y));
-          s2 = df_add(s2, fast_two_sum(q.z, q.w));
-        }
-        const df y = {yv[i].x, yv[i].y};
-        if (PRED) {
-          // both systems are J-only: r1 = y_J - Sigma_JJ x0, r2 = Sigma_J* - Sigma_JJ x0J
-          const float2 kst = S[(size_t)mb * N + i];
-          r1[i] = i < mb ? df_sub_acc(y, s1).h : 0.0f;
-          r2[i] = i < mb ? df_sub_acc(df{kst.x, kst.y}, s2).h : 0.0f;
-        } else {
-          r1[i] = df_sub_acc(y, s1).h;
-          r2[i] = i < mb ? df_sub_acc(y, s2).h : 0.0f;
-        }
+      for (int e = tid; e < nc * (mb4 >> 2); e += THREADS) {
+        const int c = e / (mb4 >> 2), k = (e - c * (mb4 >> 2)) * 4;
+        *(float4*)(Qg + (size_t)(cb + c) * xs + k) = *(const float4*)(Rb + (size_t)c * xs + k);
       }
       __syncthreads();
     }
-    double t1 = 0.0, t2 = 0.0;
-    if (!PRED) {
-      for (int p = threadIdx.x; p < N; p += blockDim.x) {
-        t1 += ((double)x0[p] + (double)c1[p]) * (double)r1[p];
-        if (p < mb) t2 += ((double)x0J[p] + (double)c2[p]) * (double)r2[p];
+    // ---- 9. conditional system S' = Sp - Q[a] . Q[b] (Q = L^{-1} R), as
+    // double-float into the X region (X is no longer needed)
+    float2* Sf = (float2*)Xr;
+    for (int t = tid; t < nr * bs; t += THREADS) {
+      const int ar = t / bs, b = t - ar * bs;
+      if (b > ar) continue;
+      float d2 = 0.0f;
+      const float* qa = Qg + (size_t)ar * xs;
+      const float* qb = Qg + (size_t)b * xs;
+      for (int k = 0; k < mb4; k += 4) {
+        const float4 a4 = *(const float4*)(qa + k);
+        const float4 b4 = *(const float4*)(qb + k);
+        d2 = fmaf(a4.x, b4.x, d2);
+        d2 = fmaf(a4.y, b4.y, d2);
+        d2 = fmaf(a4.z, b4.z, d2);
+        d2 = fmaf(a4.w, b4.w, d2);
       }
-      const double2 t = cta_sum2_mx(t1, t2, red);   // the same in every thread
-      t1 = t.x;
-      t2 = t.y;
-    }
-    // corrections: (L L^T)^{-1} r and (L_JJ L_JJ^T)^{-1} r_J
-    fwd_solve2(A, N, r1, r2);
-    for (int p = mb + threadIdx.x; p < N; p += blockDim.x) {
-      r2[p] = 0.0f;
-      if (PRED) r1[p] = 0.0f;
+      const float2 sp = Spg[tri0(ar, b)];
+      const df sres = df_add_f(df{sp.x, sp.y}, -d2);
+      Sf[tri0(ar, b)] = make_float2(sres.h, sres.l);
     }
     __syncthreads();
-    if (!PRED) {
-      double u1 = 0.0, u2 = 0.0;
-      for (int p = threadIdx.x; p < N; p += blockDim.x) {
-        u1 += (double)r1[p] * (double)r1[p];
-        u2 += (double)r2[p] * (double)r2[p];
-      }
-      const double2 uu = cta_sum2_mx(u1, u2, red);
-      u1 = uu.x;
-      u2 = uu.y;
-      if (threadIdx.x == 0) s_qvar = (t1 + u1) - (t2 + u2);
-      const double u = u1 + u2;
-      if (u <= REF_TOL * (double)bs || u > 0.5 * dq_prev || it == NREF - 1) break;
-      dq_prev = u;
-    }
-    bwd_solve2(A, N, r1, r2);
-    for (int p = threadIdx.x; p < N; p += blockDim.x) {
-      c1[p] += r1[p];
-      c2[p] += r2[p];
-    }
-    __syncthreads();
-    }  // refinement steps
     if (PRED) {
-      // mean = Sigma_*J x, var = sigma^2 + tau^2 - Sigma_*J z, sums in FP64
-      double vm = 0.0, vq = 0.0;
-      for (int p = threadIdx.x; p < mb; p += blockDim.x) {
-        const float2 k = S[(size_t)p * N + mb];
-        const double kp = (double)k.x + (double)k.y;
-        vm += kp * ((double)x0[p] + (double)c1[p]);
-        vq += kp * ((double)x0J[p] + (double)c2[p]);
-      }
-      const double sm = cta_sum_mx(vm, red);
-      const double sq = cta_sum_mx(vq, red);
-      if (threadIdx.x == 0) {
-        const double var = th.sigma2 + th.tau2 - sq;
-        P.mean[item] = sm;
+      // mean = mu^new, var = Sigma^new (1 x 1); the bordered row holds 0 - mu
+      if (tid == 0) {
+        const float2 v = Sf[tri0(0, 0)], mu = Sf[tri0(1, 0)];
+        const double var = (double)v.x + (double)v.y;
+        const double mean = -((double)mu.x + (double)mu.y);
+        P.mean[item] = mean;
         P.var[item] = var;
         P.var_latent[item] = var - th.tau2;
-        if (!isfinite(sm) || !isfinite(var)) record_failure(a.dstat, SBV_ENOTSPD, (int)blk, 0);
+        if (!isfinite(mean) || !isfinite(var)) record_failure(a.dstat, SBV_ENOTSPD, (int)blk, 0);
       }
       __syncthreads();
       continue;
     }
-    // ---- 6. log-determinant and quadratic forms, summed in FP64
-    double v = 0.0;
-    for (int p = threadIdx.x; p < N; p += blockDim.x) {
-      const double yp = (double)yv[p].x + (double)yv[p].y;
-      v += yp * ((double)x0[p] + (double)c1[p]);
-      if (p < mb) v -= yp * ((double)x0J[p] + (double)c2[p]);
-      if (p >= mb) {
-        int ex;
-        const float mant = frexpf(ldiag[p], &ex);  // L = mant 2^ex, mant in [0.5, 1)
-        v += 2.0 * ((double)ex * 0.69314718055994530942 + (double)logf(mant));
+    // ---- 10. LDL^T of Sigma^new (bs x bs) bordered by z = y_B - mu^new, in
+    // double-float, one column per step (the step's entries spread over the
+    // CTA): S_ij -= (S_ik / d_k) S_jk for k < j <= i (i <= bs, j < bs);
+    // then log det = sum log d_k and the quadratic form = sum z_k^2 / d_k
+    // (z in the bordered row)
+    {
+      bool bad = false;
+      for (int k = 0; k < bs; ++k) {
+        const float2 dk2 = Sf[tri0(k, k)];
+        if (!(dk2.x > 0.0f)) {   // the same value in every thread
+          bad = true;
+          break;
+        }
+        const df inv = df_recip(df{dk2.x, dk2.y});
+        const int Tn = bs - 1 - k;               // trailing matrix rows k+1 .. bs-1
+        const int ntri = Tn * (Tn + 1) / 2;
+        const int ntr = ntri + Tn;               // plus the bordered row's Tn entries
+        for (int l = tid; l < ntr; l += THREADS) {
+          int i, j;
+          if (l < ntri) {
+            int ii = (int)((sqrtf(8.0f * (float)l + 1.0f) - 1.0f) * 0.5f);
+            while (ii * (ii + 1) / 2 > l) --ii;
+            while ((ii + 1) * (ii + 2) / 2 <= l) ++ii;
+            i = k + 1 + ii;
+            j = k + 1 + (l - ii * (ii + 1) / 2);
+          } else {
+            i = bs;
+            j = k + 1 + (l - ntri);
+          }
+          const float2 sik = Sf[tri0(i, k)], sjk = Sf[tri0(j, k)], sij = Sf[tri0(i, j)];
+          const df lik = df_mul(df{sik.x, sik.y}, inv);
+          const df r = df_sub_acc(df{sij.x, sij.y}, df_mul(lik, df{sjk.x, sjk.y}));
+          Sf[tri0(i, j)] = make_float2(r.h, r.l);
+        }
+        __syncthreads();
       }
+      if (tid == 0) s_fail = bad ? 1 : 0;
     }
-    const double s = cta_sum_mx(v, red) + s_qvar;
-    if (threadIdx.x == 0) {
+    __syncthreads();
+    if (s_fail) {
+      hand_over();
+      continue;
+    }
+    double v = 0.0;
+    for (int t = tid; t < bs; t += THREADS) {
+      const float2 dk = Sf[tri0(t, t)], z = Sf[tri0(bs, t)];
+      const double dd = (double)dk.x + (double)dk.y, zz = (double)z.x + (double)z.y;
+      v += log(dd) + zz * zz / dd;
+    }
+    const double s = cta_sum_mx(v, red);
+    if (tid == 0) {
       const double term = -0.5 * ((double)bs * log2pi + s);
       a.terms[item] = term;
       const bool ok = isfinite(term);
@@ -926,14 +863,6 @@ loglik_mixed_kernel(MixedArgs P) {
       if (!ok) record_failure(a.dstat, SBV_ENOTSPD, (int)blk, th_i);
     }
     __syncthreads();
-  }
-  if (TC) {
-    // after a timed-out wait, give the outstanding MMAs one more bounded wait
-    // before the accumulator columns are released
-    if (s_timeout) umma::mbar_wait(&mma_bar, mma_phase ^ 1u, 1u << 24);
-    umma::fence_before_sync();
-    __syncthreads();
-    if (warp == 0) umma::tmem_dealloc(tmem_base, 256);
   }
 }
 
@@ -957,27 +886,22 @@ static int upload_df_consts(sbv_ctx* ctx) {
   return SBV_OK;
 }
 
-template <int THREADS, bool TC, bool PRED, bool GA>
+template <int THREADS, bool PRED, bool GA>
 static int occ(sbv_ctx* ctx, size_t bytes, int* out) {
   SBV_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        out, loglik_mixed_kernel<THREADS, TC, PRED, GA>, THREADS, bytes));
+                        out, loglik_mixed_kernel<THREADS, PRED, GA>, THREADS, bytes));
   return SBV_OK;
 }
 
 template <int THREADS>
-static int occ_t(sbv_ctx* ctx, bool tc, bool pred, bool ga, size_t bytes, int* out) {
-  if (ga) {
-    if (tc) return pred ? occ<THREADS, true, true, true>(ctx, bytes, out) : occ<THREADS, true, false, true>(ctx, bytes, out);
-    return pred ? occ<THREADS, false, true, true>(ctx, bytes, out) : occ<THREADS, false, false, true>(ctx, bytes, out);
-  }
-  if (tc) return pred ? occ<THREADS, true, true, false>(ctx, bytes, out) : occ<THREADS, true, false, false>(ctx, bytes, out);
-  return pred ? occ<THREADS, false, true, false>(ctx, bytes, out) : occ<THREADS, false, false, false>(ctx, bytes, out);
+static int occ_t(sbv_ctx* ctx, bool pred, bool ga, size_t bytes, int* out) {
+  if (ga) return pred ? occ<THREADS, true, true>(ctx, bytes, out) : occ<THREADS, false, true>(ctx, bytes, out);
+  return pred ? occ<THREADS, true, false>(ctx, bytes, out) : occ<THREADS, false, false>(ctx, bytes, out);
 }
 
-static int mixed_occupancy(sbv_ctx* ctx, int threads, bool tc, bool pred, bool ga, size_t bytes,
-                           int* out) {
-  return threads == 512 ? occ_t<512>(ctx, tc, pred, ga, bytes, out)
-                        : occ_t<256>(ctx, tc, pred, ga, bytes, out);
+static int mixed_occupancy(sbv_ctx* ctx, int threads, bool pred, bool ga, size_t bytes, int* out) {
+  return threads == 512 ? occ_t<512>(ctx, pred, ga, bytes, out)
+                        : occ_t<256>(ctx, pred, ga, bytes, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -988,16 +912,14 @@ static int mixed_occupancy(sbv_ctx* ctx, int threads, bool tc, bool pred, bool g
 // ---------------------------------------------------------------------------
 static int mixed_static_smem(sbv_ctx* ctx, size_t* out);
 
-int mixed_plan(sbv_ctx* ctx, int nmax, int d, int precision, bool pred, int64_t items,
+int mixed_plan(sbv_ctx* ctx, int nmax, int mcap, int d, int precision, bool pred, int64_t items,
                MixedPlan* o) {
-  const bool tc = precision == SBV_PREC_MIXED_BF16;
   const int ncap = std::max(nmax, 1);
-  o->tc = tc;
   o->pred = pred;
-  o->lay = mixed_layout(ncap, d, tc);
+  o->lay = mixed_layout(ncap, mcap, d);
   size_t static_smem = 0;
   if (int st0 = mixed_static_smem(ctx, &static_smem)) return st0;
-  if (o->lay.bytes + static_smem > ctx->smem_optin) o->lay = mixed_layout(ncap, d, tc, true);
+  if (o->lay.bytes + static_smem > ctx->smem_optin) o->lay = mixed_layout(ncap, mcap, d, true);
   if (o->lay.bytes + static_smem > ctx->smem_optin)
     return fail(ctx, SBV_EUNSUPPORTED,
                 "mixed path: a block with N=%d (d=%d) needs %zu bytes of shared memory", nmax, d,
@@ -1015,10 +937,8 @@ int mixed_plan(sbv_ctx* ctx, int nmax, int d, int precision, bool pred, int64_t 
         per_sm = t.per_sm;
       }
   }
-  // resident CTAs per SM for this variant and shared-memory size, from the
-  // runtime's occupancy calculator (registers, shared memory, reservations)
   int fit = 0;
-  if ((st = mixed_occupancy(ctx, threads, tc, pred, o->lay.ga, o->lay.bytes, &fit))) return st;
+  if ((st = mixed_occupancy(ctx, threads, pred, o->lay.ga, o->lay.bytes, &fit))) return st;
   if (fit < 1)
     return fail(ctx, SBV_EUNSUPPORTED, "mixed path: no CTA of %d threads fits an SM (N=%d, d=%d)",
                 threads, nmax, d);
@@ -1027,7 +947,6 @@ int mixed_plan(sbv_ctx* ctx, int nmax, int d, int precision, bool pred, int64_t 
   if (grid > items) grid = (int)std::max<int64_t>(items, 1);
   o->threads = threads;
   o->grid = grid;
-  o->scratch_stride = align_up((size_t)ncap * ncap, 64);
   return SBV_OK;
 }
 
@@ -1040,26 +959,26 @@ int mixed_split(sbv_ctx* ctx, const void* X, int dtype, int64_t total, float2* x
   return SBV_OK;
 }
 
-template <int THREADS, bool TC, bool PRED>
+template <int THREADS, bool PRED>
 static int launch_variant(sbv_ctx* ctx, const MixedArgs& P, int grid, cudaStream_t s) {
   if (P.lay.ga)
-    loglik_mixed_kernel<THREADS, TC, PRED, true><<<grid, THREADS, P.lay.bytes, s>>>(P);
+    loglik_mixed_kernel<THREADS, PRED, true><<<grid, THREADS, P.lay.bytes, s>>>(P);
   else
-    loglik_mixed_kernel<THREADS, TC, PRED, false><<<grid, THREADS, P.lay.bytes, s>>>(P);
+    loglik_mixed_kernel<THREADS, PRED, false><<<grid, THREADS, P.lay.bytes, s>>>(P);
   SBV_LAUNCH_CHECK(ctx, "loglik_mixed_kernel");
   return SBV_OK;
 }
 
 // Both variants may use the largest dynamic shared memory; the global-A
 // variant prefers the smallest shared-memory carve-out so that the rest of
-// the SM's 256 KB serves as L1 for its triangles.
-template <int THREADS, bool TC, bool PRED>
+// the SM's 256 KB serves as L1 for its slices.
+template <int THREADS, bool PRED>
 static int allow_smem(sbv_ctx* ctx, int bytes) {
-  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<THREADS, TC, PRED, false>,
+  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<THREADS, PRED, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<THREADS, TC, PRED, true>,
+  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<THREADS, PRED, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<THREADS, TC, PRED, true>,
+  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<THREADS, PRED, true>,
                                          cudaFuncAttributePreferredSharedMemoryCarveout, 0));
   return SBV_OK;
 }
@@ -1067,27 +986,24 @@ static int allow_smem(sbv_ctx* ctx, int bytes) {
 static bool g_mixed_ready[64];
 static size_t g_mixed_static[64];
 
-template <int THREADS, bool TC, bool PRED>
+template <int THREADS, bool PRED>
 static size_t static_smem_of() {
   cudaFuncAttributes a{}, b{};
-  if (cudaFuncGetAttributes(&a, loglik_mixed_kernel<THREADS, TC, PRED, false>) != cudaSuccess ||
-      cudaFuncGetAttributes(&b, loglik_mixed_kernel<THREADS, TC, PRED, true>) != cudaSuccess)
+  if (cudaFuncGetAttributes(&a, loglik_mixed_kernel<THREADS, PRED, false>) != cudaSuccess ||
+      cudaFuncGetAttributes(&b, loglik_mixed_kernel<THREADS, PRED, true>) != cudaSuccess)
     return 0;
   return std::max(a.sharedSizeBytes, b.sharedSizeBytes);
 }
 
-// The largest static shared memory of the variants (the tables, the staged
-// diagonal tile, the reduction buffers), queried once per device.
+// The largest static shared memory of the variants, queried once per device.
 static int mixed_static_smem(sbv_ctx* ctx, size_t* out) {
   const int dev = ctx->device;
   if (dev < 64 && g_mixed_static[dev]) {
     *out = g_mixed_static[dev];
     return SBV_OK;
   }
-  const size_t v[8] = {static_smem_of<256, false, false>(), static_smem_of<256, true, false>(),
-                       static_smem_of<256, false, true>(),  static_smem_of<256, true, true>(),
-                       static_smem_of<512, false, false>(), static_smem_of<512, true, false>(),
-                       static_smem_of<512, false, true>(),  static_smem_of<512, true, true>()};
+  const size_t v[4] = {static_smem_of<256, false>(), static_smem_of<256, true>(),
+                       static_smem_of<512, false>(), static_smem_of<512, true>()};
   size_t m = 0;
   for (size_t x : v) {
     if (x == 0) return fail(ctx, SBV_ECUDA, "mixed path: cudaFuncGetAttributes failed");
@@ -1108,40 +1024,32 @@ int mixed_prepare(sbv_ctx* ctx) {
   size_t stat = 0;
   if ((st = mixed_static_smem(ctx, &stat))) return st;
   const int b = (int)(ctx->smem_optin - stat);
-  if ((st = allow_smem<256, false, false>(ctx, b)) || (st = allow_smem<256, true, false>(ctx, b)) ||
-      (st = allow_smem<256, false, true>(ctx, b)) || (st = allow_smem<256, true, true>(ctx, b)) ||
-      (st = allow_smem<512, false, false>(ctx, b)) || (st = allow_smem<512, true, false>(ctx, b)) ||
-      (st = allow_smem<512, false, true>(ctx, b)) || (st = allow_smem<512, true, true>(ctx, b)))
+  if ((st = allow_smem<256, false>(ctx, b)) || (st = allow_smem<256, true>(ctx, b)) ||
+      (st = allow_smem<512, false>(ctx, b)) || (st = allow_smem<512, true>(ctx, b)))
     return st;
   if (ctx->device < 64) g_mixed_ready[ctx->device] = true;
   return SBV_OK;
 }
 
-// Enqueue the kernel; P carries the arguments, Xs (or NULL) and the scratch.
+// Enqueue the kernel; P carries the arguments, Xs (or NULL), the scratch and
+// the hand-over list.
 int mixed_enqueue(sbv_ctx* ctx, MixedArgs& P, const MixedPlan& o, cudaStream_t s) {
   int st = 0;
   if ((st = mixed_prepare(ctx))) return st;
   P.lay = o.lay;
-  P.scratch_stride = o.scratch_stride;
-  const bool tc = o.tc, pred = o.pred;
-  if (o.threads == 512) {
-    if (pred) return tc ? launch_variant<512, true, true>(ctx, P, o.grid, s)
-                        : launch_variant<512, false, true>(ctx, P, o.grid, s);
-    return tc ? launch_variant<512, true, false>(ctx, P, o.grid, s)
-              : launch_variant<512, false, false>(ctx, P, o.grid, s);
-  }
-  if (pred) return tc ? launch_variant<256, true, true>(ctx, P, o.grid, s)
-                      : launch_variant<256, false, true>(ctx, P, o.grid, s);
-  return tc ? launch_variant<256, true, false>(ctx, P, o.grid, s)
-            : launch_variant<256, false, false>(ctx, P, o.grid, s);
+  if (o.threads == 512)
+    return o.pred ? launch_variant<512, true>(ctx, P, o.grid, s)
+                  : launch_variant<512, false>(ctx, P, o.grid, s);
+  return o.pred ? launch_variant<256, true>(ctx, P, o.grid, s)
+                : launch_variant<256, false>(ctx, P, o.grid, s);
 }
 
 // Plan, split the points and take the scratch from the context workspace.
-static int launch_mixed(sbv_ctx* ctx, MixedArgs& P, int nmax, int precision, bool pred,
+static int launch_mixed(sbv_ctx* ctx, MixedArgs& P, int nmax, int mcap, int precision, bool pred,
                         int64_t items, cudaStream_t s) {
   int st = 0;
   MixedPlan o;
-  if ((st = mixed_plan(ctx, nmax, P.a.d, precision, pred, items, &o))) return st;
+  if ((st = mixed_plan(ctx, nmax, mcap, P.a.d, precision, pred, items, &o))) return st;
   const int64_t total = P.a.n * P.a.d;
   P.Xs = nullptr;
   if (P.a.dtype == SBV_F64) {
@@ -1150,25 +1058,26 @@ static int launch_mixed(sbv_ctx* ctx, MixedArgs& P, int nmax, int precision, boo
     if ((st = mixed_split(ctx, P.a.X, P.a.dtype, total, xs, s))) return st;
     P.Xs = xs;
   }
-  unsigned char* buf = (unsigned char*)ws_get(ctx, WS_MATRIX, o.scratch_bytes(), &st);
+  float* buf = (float*)ws_get(ctx, WS_MATRIX, o.scratch_bytes(), &st);
   if (!buf) return st;
-  P.scratch = (float2*)buf;
-  P.gA = o.lay.ga ? (float*)(buf + o.ga_offset()) : nullptr;
+  P.gbase = buf;
   return mixed_enqueue(ctx, P, o, s);
 }
 
 int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a0, int nmax, int precision,
-                        cudaStream_t s) {
+                        unsigned int* fb_list, unsigned int* fb_count, cudaStream_t s) {
   MixedArgs P;
   memset(&P, 0, sizeof(P));
   P.a = a0;
-  return launch_mixed(ctx, P, nmax, precision, false, a0.bc * (int64_t)a0.B, s);
+  P.fb_list = fb_list;
+  P.fb_count = fb_count;
+  return launch_mixed(ctx, P, nmax, a0.m, precision, false, a0.bc * (int64_t)a0.B, s);
 }
 
 // Prediction: a0 carries X, y, d, nbr (ntest x m), m, theta, nu2, dstat, counter.
 int launch_predict_mixed(sbv_ctx* ctx, const LoglikArgs& a0, const void* Xt, int64_t nt,
                          double* mean, double* var, double* var_latent, int precision,
-                         cudaStream_t s) {
+                         unsigned int* fb_list, unsigned int* fb_count, cudaStream_t s) {
   MixedArgs P;
   memset(&P, 0, sizeof(P));
   P.a = a0;
@@ -1177,7 +1086,9 @@ int launch_predict_mixed(sbv_ctx* ctx, const LoglikArgs& a0, const void* Xt, int
   P.mean = mean;
   P.var = var;
   P.var_latent = var_latent;
-  return launch_mixed(ctx, P, a0.m + 1, precision, true, nt, s);
+  P.fb_list = fb_list;
+  P.fb_count = fb_count;
+  return launch_mixed(ctx, P, a0.m + 1, a0.m, precision, true, nt, s);
 }
 
 }  // namespace sbv

@@ -12,18 +12,7 @@ namespace sbv {
 // threads per CTA: 256 (two CTAs per SM when shared memory allows) or 512
 // (one CTA per SM); the autotuner picks per structure
 constexpr int MX_MAX_WARPS = 16;
-constexpr int NB = 16;  // panel width = diagonal tile size
-
-struct MixedLayout {
-  int ncap;             // largest N held (rows 0..ncap-1 plus the bordered row)
-  int d;
-  int pstride;          // row stride of the FP32 column-major panel (CUDA-core update)
-  uint32_t opnd_piece;  // bytes of one BF16 operand piece (tensor-core update)
-  bool ga;              // the packed triangle A lives in global memory (per-CTA slice)
-  size_t a_floats;      // floats of one padded packed triangle (rounded to 64)
-  int part_cap;         // float4 partial sums the residual phase may hold
-  size_t off_y, off_v, off_u, off_vl, off_c, off_tab, off_stile, off_A, bytes;
-};
+constexpr int NB = 16;  // panel width = diagonal tile size of the FP32 factor of Sigma_JJ
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -40,61 +29,108 @@ __host__ __device__ inline size_t trp_size(int rows) {
   return 4 * (a + 1) * (2 * a + b);
 }
 
-// One shared-memory region (off_u) serves three phases in turn: the scaled
-// coordinates and the exp2 tables (covariance), the panel operand and the
-// staged diagonal tile (factorisation) and, during refinement, the residual
-// partial sums followed (off_c) by the two accumulated corrections.
-// With ga, the packed triangle (the largest piece, 4 (N+1)(N+2)/2 bytes) is
-// left out of shared memory; the kernel then addresses a per-CTA slice of a
-// global buffer, which stays in L1/L2 for the CTA's lifetime.
-__host__ __device__ inline MixedLayout mixed_layout(int ncap, int d, bool tc, bool ga = false) {
+// Row stride (floats) of the right-hand-side block of an item with mb
+// neighbours: at least mb rounded up to four, and 4 (mod 32), so that lanes
+// reading float4 segments of consecutive rows hit distinct banks.
+__host__ __device__ __forceinline__ int rhs_stride(int mb) { return ((mb + 27) / 32) * 32 + 4; }
+
+// Packed lower triangle without padding (the bs x bs conditional system).
+__host__ __device__ __forceinline__ int tri0(int i, int j) { return (i * (i + 1) >> 1) + j; }
+
+// Shared memory of one CTA (one item at a time):
+//   y       observations of the item's points as float pairs
+//   idiag   1 / L_tt of the FP32 factor of Sigma_JJ
+//   union   covariance phase: scaled coordinates (hi, lo) and the exp2 table;
+//           factorisation: the FP32 panel copy and a staged diagonal tile
+//   A       packed lower triangle of Sigma_JJ -> its FP32 factor L (diagonal
+//           tiles later replaced by their inverses)
+//   X       right-hand-side block: row r < bs holds Sigma_{J, b_r}, row bs
+//           holds y_J; they become L^{-1} (.), then Sigma_JJ^{-1} (.); after
+//           the Schur-complement passes the region holds the bs x bs
+//           conditional system (bordered by y_B - mu) in double-float
+// With ga, A and X live in a per-CTA slice of global memory instead.
+//   union   residual phase: a block of 16 residual columns (then L^{-1} of
+//           them), the fixed-point grid constant of every right-hand side and
+//           two staged chunks of 8 columns of Sigma_JJ
+// Per-CTA global memory: the double-float joint covariance (N x N, both
+// triangles), L^{-1} R for every right-hand side and the partial
+// Schur-complement system.
+struct MixedLayout {
+  int ncap;             // largest N = mb + bs held
+  int mcap;             // largest mb (neighbour count)
+  int d;
+  int pstride;          // column stride of the FP32 panel copy (floats)
+  bool ga;              // A and X in global memory
+  size_t a_floats;      // floats of A (rounded to 64)
+  size_t x_floats;      // floats of the X region (rounded to 64)
+  size_t off_y, off_v, off_u, off_vl, off_tab, off_stile, off_cc, off_sch, off_A, off_X, bytes;
+  // per-CTA global slice, in floats
+  size_t g_R, g_Sp, g_A, g_X, g_stride;
+};
+
+__host__ __device__ inline MixedLayout mixed_layout(int ncap, int mcap, int d, bool ga = false) {
   MixedLayout L;
   L.ncap = ncap;
+  L.mcap = mcap < ncap ? mcap : ncap;
   L.d = d;
   L.ga = ga;
-  L.a_floats = align_up(trp_size(ncap + 1), 64);
+  L.a_floats = align_up(trp_size(L.mcap), 64);
+  // the largest right-hand-side block: nr = N + 1 - mb rows of rhs_stride(mb)
+  size_t xf = 8;
+  for (int mb = 0; mb <= L.mcap; ++mb) {
+    const size_t v = (size_t)(ncap + 1 - mb) * rhs_stride(mb);
+    if (v > xf) xf = v;
+  }
+  L.x_floats = align_up(xf, 64);
   L.pstride = (int)align_up((size_t)ncap + 1, 4);
-  L.opnd_piece = (uint32_t)(((ncap + 1 + 127) / 128) * 128 * 32);
   size_t o = 0;
   L.off_y = o;  o += align_up((size_t)(ncap + 1) * sizeof(float2), 16);
-  // x0 x0J r1 r2 ldiag idiag, each 16-byte aligned
-  L.off_v = o;  o += (size_t)6 * align_up((size_t)ncap + 1, 4) * sizeof(float);
+  L.off_v = o;  o += align_up((size_t)(L.mcap + 4) * sizeof(float), 16);
   o = align_up(o, 128);
   const size_t coord = align_up((size_t)d * ncap * sizeof(float), 16);
-  const size_t tab = 2 * 256 * sizeof(float);          // exp2 table, hi and lo
-  const size_t stile = (size_t)NB * NB * sizeof(float2);  // a diagonal tile's originals
+  const size_t tab = 2 * 256 * sizeof(float);             // exp2 table, hi and lo
+  const size_t stile = (size_t)NB * NB * sizeof(float2);   // a diagonal tile's originals
+  const size_t panel = align_up((size_t)NB * L.pstride * sizeof(float), 16);
+  // residual phase: a block of 16 right-hand sides of the residual, then one
+  // grid constant per right-hand side
+  const size_t rblk = align_up((size_t)16 * rhs_stride(L.mcap) * sizeof(float), 16);
+  const size_t cc = align_up((size_t)(ncap + 2) * sizeof(float), 16);
+  const size_t sch = (size_t)2 * 8 * L.mcap * sizeof(float2);   // two chunks of 8 columns
   size_t uni = 2 * coord + tab;
-  const size_t panel =
-      align_up(tc ? 3 * (size_t)L.opnd_piece : (size_t)NB * L.pstride * sizeof(float), 16) + stile;
-  size_t part = (size_t)(32 * MX_MAX_WARPS > ncap ? 32 * MX_MAX_WARPS : ncap) * sizeof(float4);
-  const size_t corr = align_up((size_t)2 * (ncap + 1) * sizeof(float), 16);
-  if (panel > uni) uni = panel;
-  if (part + corr > uni) uni = part + corr;
-  // the partial sums take whatever the region holds anyway (more column
-  // chunks for the residual), up to 16 chunks
-  const size_t part_max = (size_t)16 * (ncap + 1) * sizeof(float4);
-  part = (uni - corr) / sizeof(float4) * sizeof(float4);
-  if (part > part_max) part = part_max;
-  L.part_cap = (int)(part / sizeof(float4));
+  if (panel + stile > uni) uni = panel + stile;
+  if (rblk + cc + sch > uni) uni = rblk + cc + sch;
   L.off_u = o;
   L.off_vl = o + coord;
   L.off_tab = o + 2 * coord;
-  L.off_stile = o + panel - stile;
-  L.off_c = o + part;
-  o += align_up(uni, 16);
+  L.off_stile = o + panel;
+  L.off_cc = o + rblk;
+  L.off_sch = o + rblk + cc;
+  o += align_up(uni, 128);
   L.off_A = o;
-  if (!ga) o += align_up(trp_size(ncap + 1) * sizeof(float), 16);
+  if (!ga) o += L.a_floats * sizeof(float);
+  L.off_X = o;
+  if (!ga) o += L.x_floats * sizeof(float);
   L.bytes = o;
+  // global slice: S (ncap^2 float pairs), R, Sp, then A and X when ga
+  size_t g = align_up((size_t)2 * ncap * ncap, 64);
+  L.g_R = g;  g += L.x_floats;
+  L.g_Sp = g; g += L.x_floats;
+  L.g_A = g;  if (ga) g += L.a_floats;
+  L.g_X = g;  if (ga) g += L.x_floats;
+  L.g_stride = align_up(g, 64);
   return L;
 }
 
 struct MixedArgs {
   LoglikArgs a;
   const float2* Xs;      // split FP64 points, or NULL for FP32 points (a.X read directly)
-  float2* scratch;
-  size_t scratch_stride;
-  float* gA;             // packed triangles, lay.a_floats per CTA (lay.ga only)
+  float* gbase;          // per-CTA global slices (lay.g_stride floats each)
   MixedLayout lay;
+  // items the mixed kernel hands to the FP64 kernel: a pivot that is not
+  // positive in FP32 or double-float, or a conditional system larger than the
+  // X region; fb_count and the list are read by the FP64 kernel in list mode
+  unsigned int* fb_list;
+  unsigned int* fb_count;
   // prediction mode: one item per test point, J = its m nearest training points
   const void* Xt;        // test points (dtype of a.X)
   int64_t nt;
@@ -105,18 +141,12 @@ struct MixedArgs {
 
 struct MixedPlan {
   MixedLayout lay;
-  bool tc, pred;
+  bool pred;
   int threads, grid;
-  size_t scratch_stride;  // float2 elements per CTA slice
-  // bytes of the per-CTA scratch buffer: the FP32-pair copy of Sigma, then
-  // (lay.ga) the packed triangles from byte offset ga_offset
-  size_t scratch_bytes() const {
-    return ga_offset() + (lay.ga ? lay.a_floats * sizeof(float) * (size_t)grid : 0);
-  }
-  size_t ga_offset() const { return align_up(scratch_stride * sizeof(float2) * (size_t)grid, 256); }
+  size_t scratch_bytes() const { return lay.g_stride * sizeof(float) * (size_t)grid; }
 };
 
-int mixed_plan(sbv_ctx* ctx, int nmax, int d, int precision, bool pred, int64_t items,
+int mixed_plan(sbv_ctx* ctx, int nmax, int mcap, int d, int precision, bool pred, int64_t items,
                MixedPlan* o);
 int mixed_split(sbv_ctx* ctx, const void* X, int dtype, int64_t total, float2* xs,
                 cudaStream_t s);

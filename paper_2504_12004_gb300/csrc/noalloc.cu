@@ -134,6 +134,7 @@ extern "C" int sbv_loglik_fp64_noalloc(const void* X, int dtype, const double* y
     return SBV_ECUDA;
 
   LoglikArgs a;
+  memset(&a, 0, sizeof(a));
   a.X = X;
   a.dtype = dtype;
   a.y = y;

@@ -257,6 +257,17 @@ extern "C" int sbv_sync_status(sbv_ctx* ctx, void* stream) {
   return SBV_OK;
 }
 
+extern "C" int sbv_fp64_reruns(sbv_ctx* ctx, void* stream, int64_t* count) {
+  if (!ctx || !count) return SBV_EINVAL;
+  cudaSetDevice(ctx->device);
+  DevStatus h;
+  cudaStream_t s = (cudaStream_t)stream;
+  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(&h, ctx->d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
+  SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  *count = h.reruns;
+  return SBV_OK;
+}
+
 static int predict_common(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n,
                           int32_t d, const void* Xtest, int64_t ntest, const double* beta_scale,
                           int32_t m_pred, const double* theta, int32_t nu2, int32_t precision,

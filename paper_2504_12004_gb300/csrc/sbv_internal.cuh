@@ -17,6 +17,8 @@ struct DevStatus {
   int32_t item;      // block or test-point index of the first failure
   int32_t theta;     // parameter row of the first failure
   int32_t count;     // number of failures
+  int32_t reruns;    // items the mixed kernels handed to the FP64 kernels
+  int32_t pad[3];
 };
 
 // Grow-only device buffer owned by the context.
@@ -57,6 +59,8 @@ enum WsSlot {
   WS_PRED,        // prediction neighbour lists when the caller passes NULL
   WS_GRAD,        // per-block gradients when the caller passes NULL
   WS_GRADZ,       // per-CTA right-hand sides of the gradient kernel
+  WS_RERUN,       // items the mixed kernels hand to the FP64 kernels
+  WS_GMAT64,      // global matrices of the FP64 kernel after a mixed launch
   WS_COUNT
 };
 
