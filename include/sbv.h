@@ -60,7 +60,8 @@ extern "C" {
 #define SBV_PREC_MIXED      1  /* FP32 factor of Sigma_JJ; double-float covariance, residual
                                   and Schur complement (third-order corrected); double-float
                                   LDL^T of the bs x bs conditional system */
-#define SBV_PREC_MIXED_BF16 2  /* as SBV_PREC_MIXED (the same kernel in this version) */
+#define SBV_PREC_MIXED_BF16 2  /* as SBV_PREC_MIXED with the residual's products on the tensor
+                                  cores: exact BF16 digit products (tcgen05, TMEM) */
 
 /* compiled limits */
 #define SBV_MAX_DIM      64     /* d */

@@ -101,10 +101,14 @@ extern "C" int sbv_loglik_graph_create(sbv_ctx* ctx, const void* X, int dtype, c
   *out = nullptr;
   cudaStream_t cap = nullptr;
   SBV_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-  if (nmax <= 0 && (st = run_max_n(ctx, ptr, cnt, bc, &nmax, cap))) {
+  // the largest block sizes fix the mixed kernel's layout (one read at creation)
+  int nmax_s = 0, bsmax = 0;
+  if ((st = run_max_sizes(ctx, ptr, cnt, bc, &nmax_s, &bsmax, cap))) {
     cudaStreamDestroy(cap);
     return st;
   }
+  if (nmax <= 0) nmax = nmax_s;
+  if (nmax < nmax_s) bsmax = 0;   // a smaller hint: the blocks above it are reported, not held
   if (nmax > SBV_MAX_BLOCK_N) {
     cudaStreamDestroy(cap);
     return fail(ctx, SBV_EUNSUPPORTED, "a block has m_i + bs_i = %d > %d", nmax, SBV_MAX_BLOCK_N);
@@ -162,7 +166,7 @@ extern "C" int sbv_loglik_graph_create(sbv_ctx* ctx, const void* X, int dtype, c
   if (mixed) {
     memset(&P, 0, sizeof(P));
     P.a = a;
-    if ((st = mixed_plan(ctx, nmax, m, d, precision, false, items, &mp))) return bail(st);
+    if ((st = mixed_plan(ctx, nmax, m, bsmax, d, precision, false, items, &mp))) return bail(st);
     if (dtype == SBV_F64) {  // X is fixed: split it once, outside the graph
       if ((st = own(g, 3, (size_t)n * d * sizeof(float2), &p))) return bail(st);
       if ((st = mixed_split(ctx, X, dtype, n * d, (float2*)p, cap))) return bail(st);
@@ -241,7 +245,9 @@ extern "C" int sbv_autotune(sbv_ctx* ctx, const void* X, int dtype, const double
   if (st) return st;
   if ((st = check_theta_rows(ctx, theta, B, d))) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  if (nmax <= 0 && (st = run_max_n(ctx, ptr, cnt, bc, &nmax, s))) return st;
+  int nmax_s = 0, bsmax = 0;
+  if ((st = run_max_sizes(ctx, ptr, cnt, bc, &nmax_s, &bsmax, s))) return st;
+  if (nmax <= 0) nmax = nmax_s;
   std::vector<LaunchShape> shapes;
   if (precision == SBV_PREC_FP64) {
     for (int k = 1; k <= 4; ++k) shapes.push_back({256, k});
@@ -262,7 +268,9 @@ extern "C" int sbv_autotune(sbv_ctx* ctx, const void* X, int dtype, const double
     float t = INFINITY;
     for (int rep = 0; rep < 3 && !st; ++rep) {
       cudaEventRecord(e0, s);
-      st = run_loglik(ctx, X, dtype, y, n, d, ptr, pts, nbr, cnt, bc, m, nmax, theta, B, nu2,
+      // size hint 0: the call reads both sizes, as a graph created later does
+      st = run_loglik(ctx, X, dtype, y, n, d, ptr, pts, nbr, cnt, bc, m, nmax == nmax_s ? 0 : nmax,
+                      theta, B, nu2,
                       precision, ll, nullptr, nullptr, s);
       cudaEventRecord(e1, s);
       if (cudaEventSynchronize(e1) != cudaSuccess) st = cuda_fail(ctx, cudaGetLastError(), "autotune");

@@ -224,6 +224,26 @@ __global__ void max_n_kernel(const int64_t* __restrict__ ptr, const int32_t* __r
   if ((threadIdx.x & 31) == 0) atomicMax(out, v);
 }
 
+// Largest m_i + bs_i (out[0]) and largest bs_i (out[1]) over blocks.
+__global__ void max_sizes_kernel(const int64_t* __restrict__ ptr, const int32_t* __restrict__ cnt,
+                                 int64_t bc, int* __restrict__ out) {
+  int v = 0, w = 0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < bc;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int bs = (int)(ptr[j + 1] - ptr[j]);
+    v = max(v, bs + cnt[j]);
+    w = max(w, bs);
+  }
+  for (int o = 16; o; o >>= 1) {
+    v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    w = max(w, __shfl_xor_sync(0xffffffffu, w, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out, v);
+    atomicMax(out + 1, w);
+  }
+}
+
 static std::vector<ThetaDev> derive_theta(const double* h, int B, int d) {
   std::vector<ThetaDev> out(B);
   for (int b = 0; b < B; ++b) {
@@ -292,7 +312,7 @@ static int structure_max_n(sbv_ctx* ctx, const int64_t* ptr, const int32_t* cnt,
   return SBV_OK;
 }
 
-int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a, int nmax, int precision,
+int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a, int nmax, int bsmax, int precision,
                         unsigned int* fb_list, unsigned int* fb_count, cudaStream_t s);
 int launch_predict_mixed(sbv_ctx* ctx, const LoglikArgs& a0, const void* Xt, int64_t nt,
                          double* mean, double* var, double* var_latent, int precision,
@@ -301,6 +321,29 @@ int launch_predict_mixed(sbv_ctx* ctx, const LoglikArgs& a0, const void* Xt, int
 int run_max_n(sbv_ctx* ctx, const int64_t* ptr, const int32_t* cnt, int64_t bc, int* out,
               cudaStream_t s) {
   return structure_max_n(ctx, ptr, cnt, bc, out, s);
+}
+
+// Largest m_i + bs_i and largest bs_i (one small kernel and a host read).
+int run_max_sizes(sbv_ctx* ctx, const int64_t* ptr, const int32_t* cnt, int64_t bc, int* nmax,
+                  int* bsmax, cudaStream_t s) {
+  int st = 0;
+  int* d = (int*)ws_get(ctx, WS_SMALL, 64, &st);
+  if (!d) return st;
+  SBV_CUDA_TRY(ctx, cudaMemsetAsync(d, 0, 8, s));
+  int g = (int)std::min<int64_t>((bc + 255) / 256, (int64_t)ctx->num_sms * 8);
+  max_sizes_kernel<<<std::max(g, 1), 256, 0, s>>>(ptr, cnt, bc, d);
+  SBV_LAUNCH_CHECK(ctx, "max_sizes_kernel");
+  int h[2] = {0, 0};
+  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(h, d, 8, cudaMemcpyDeviceToHost, s));
+  SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  *nmax = h[0];
+  *bsmax = h[1];
+  ctx->sz_ptr = ptr;
+  ctx->sz_cnt = cnt;
+  ctx->sz_bc = bc;
+  ctx->sz_nmax = h[0];
+  ctx->sz_bsmax = h[1];
+  return SBV_OK;
 }
 
 std::vector<ThetaDev> derive_theta_rows(const double* h, int B, int d) {
@@ -400,8 +443,13 @@ int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t 
   int st = 0;
   if ((uint64_t)bc * (uint64_t)B >= 0xffffffffull)
     return fail(ctx, SBV_EUNSUPPORTED, "bc*B too large");
-  int nmax = nmax_hint;
-  if (nmax <= 0 && (st = structure_max_n(ctx, ptr, cnt, bc, &nmax, s))) return st;
+  // with a size hint the largest block size is not read back, and the mixed
+  // kernel's layout assumes the largest bs the hint allows
+  int nmax = nmax_hint, bsmax = 0;
+  if (nmax <= 0 && (st = run_max_sizes(ctx, ptr, cnt, bc, &nmax, &bsmax, s))) return st;
+  if (nmax_hint > 0 && ctx->sz_ptr == (const void*)ptr && ctx->sz_cnt == (const void*)cnt &&
+      ctx->sz_bc == bc && ctx->sz_nmax == nmax_hint)
+    bsmax = ctx->sz_bsmax;
   if (nmax > SBV_MAX_BLOCK_N)
     return fail(ctx, SBV_EUNSUPPORTED, "a block has m_i + bs_i = %d > %d", nmax, SBV_MAX_BLOCK_N);
   ThetaDev* dth = nullptr;
@@ -444,7 +492,7 @@ int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t 
     unsigned int* list =
         (unsigned int*)ws_get(ctx, WS_RERUN, (size_t)B * bc * sizeof(unsigned int), &st);
     if (!list) return st;
-    if ((st = launch_loglik_mixed(ctx, a, nmax, precision, list, counter + 1, s))) return st;
+    if ((st = launch_loglik_mixed(ctx, a, nmax, bsmax, precision, list, counter + 1, s))) return st;
     // the items handed over (pivots, capacity) go through the FP64 kernel
     if ((st = fp64_fallback_enqueue(ctx, a, nmax, list, counter + 1, counter + 2, s))) return st;
   } else {
@@ -682,8 +730,13 @@ int run_loglik_grad(sbv_ctx* ctx, const void* X, int dtype, const double* y, int
   const int p = d + 2;
   if ((uint64_t)bc * (uint64_t)B >= 0xffffffffull)
     return fail(ctx, SBV_EUNSUPPORTED, "bc*B too large");
-  int nmax = nmax_hint;
-  if (nmax <= 0 && (st = structure_max_n(ctx, ptr, cnt, bc, &nmax, s))) return st;
+  // with a size hint the largest block size is not read back, and the mixed
+  // kernel's layout assumes the largest bs the hint allows
+  int nmax = nmax_hint, bsmax = 0;
+  if (nmax <= 0 && (st = run_max_sizes(ctx, ptr, cnt, bc, &nmax, &bsmax, s))) return st;
+  if (nmax_hint > 0 && ctx->sz_ptr == (const void*)ptr && ctx->sz_cnt == (const void*)cnt &&
+      ctx->sz_bc == bc && ctx->sz_nmax == nmax_hint)
+    bsmax = ctx->sz_bsmax;
   if (nmax > SBV_MAX_BLOCK_N)
     return fail(ctx, SBV_EUNSUPPORTED, "a block has m_i + bs_i = %d > %d", nmax, SBV_MAX_BLOCK_N);
   ThetaDev* dth = nullptr;

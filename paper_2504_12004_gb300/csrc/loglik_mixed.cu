@@ -20,8 +20,12 @@
 //  4. the diagonal tiles are replaced by their inverses;
 //  5. backward substitution: X <- Sigma~_JJ^{-1} Sigma_{J,B'} (FP32), i.e.
 //     the kriging weights of B and x_J = Sigma~^{-1} y_J;
-//  6. residual R = Sigma_{J,B'} - Sigma_JJ X in double-float from the global
-//     copy of Sigma (one extended-precision pass);
+//  6. residual R = Sigma_{J,B'} - Sigma_JJ X from the global copy of Sigma,
+//     exact to about 2^-38 of the products: for mb <= 128 on the tensor
+//     cores (X held on a 24-bit fixed-point grid per column and split into
+//     three BF16 digits, Sigma_JJ into five, the digit products of equal
+//     weight summed exactly in five FP32 TMEM accumulators), otherwise on the
+//     CUDA cores with exact fixed-point product heads;
 //  7. the conditional system of Alg. 5 (GEMM, GEMV and the Schur
 //     subtraction, l.10-13) by the exact identity
 //        S' = Sigma_{B'B'} - Sigma_{B'J} X - X^T R - R^T Sigma_JJ^{-1} R,
@@ -43,10 +47,13 @@
 #include <algorithm>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "block_common.cuh"
 #include "dfloat.cuh"
 #include "mixed.cuh"
 #include "sbv_internal.cuh"
+#include "umma.cuh"
 
 namespace sbv {
 
@@ -75,7 +82,7 @@ __global__ void split_points_kernel(const double* __restrict__ X, int64_t total,
   }
 }
 
-template <int THREADS, bool PRED, bool GA>
+template <int THREADS, bool TC, bool PRED, bool GA>
 __global__ void __launch_bounds__(THREADS, THREADS == 256 ? 2 : 1)
 loglik_mixed_kernel(MixedArgs P) {
   constexpr int NW = THREADS / 32;
@@ -108,6 +115,21 @@ loglik_mixed_kernel(MixedArgs P) {
   const unsigned int total = PRED ? (unsigned int)P.nt : (unsigned int)(a.bc * a.B);
   const double log2pi = 1.8378770664093454836;
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  // tensor-core residual: 5 accumulator groups x 16 columns of TMEM and one
+  // mbarrier for MMA completion
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ int s_timeout;
+  if (TC && warp == 0) umma::tmem_alloc(&s_tmem, 128);
+  if (tid == 0) {
+    if (TC) umma::mbar_init(&mma_bar, 1);
+    s_timeout = 0;
+  }
+  if (TC) umma::fence_before_sync();
+  __syncthreads();
+  if (TC) umma::fence_after_sync();
+  const uint32_t tmem_base = TC ? s_tmem : 0u;
+  uint32_t mma_phase = 0;
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(a.counter, 1u);
@@ -580,28 +602,204 @@ loglik_mixed_kernel(MixedArgs P) {
     // FMA) plus s.l x is summed in FP32 over four terms and then folded into
     // a float pair.
     float* Rb = (float*)(smem + lay.off_u);      // residual block, then L^{-1} of it
-    float* colC = (float*)(smem + lay.off_cc);   // C_r per right-hand side
-    float2* Sch = (float2*)(smem + lay.off_sch); // staged columns of Sigma_JJ
+    float* colC = (float*)(smem + lay.off_cc);   // C_r per right-hand side (CUDA-core residual)
+    float* colX = colC + lay.ncap + 2;           // grid unit of X^ per right-hand side
+    float2* Sch = (float2*)(smem + lay.off_sch); // staged columns of Sigma_JJ (CUDA cores)
+    unsigned char* Ab = smem + lay.off_sch;      // five BF16 digit tiles of Sigma_JJ (tensor cores)
+    unsigned char* Bb = Ab + 5 * 4096;           // three BF16 digit tiles of X^ (tensor cores)
     float* Qg = Rg;                              // L^{-1} R for every column, global
+    const bool tc = TC && mb <= 128;
+    // X <- X^ on a 24-bit fixed-point grid per column (unit 2^(ex - 24),
+    // |X| < 2^ex): every later use (residual, conditional system) sees the
+    // same X^, whose digits the tensor cores take exactly
     for (int r = warp; r < nr; r += NW) {
       float mxv = 0.0f;
       for (int k = lane; k < mb; k += 32) mxv = fmaxf(mxv, fabsf(Xr[(size_t)r * xs + k]));
       for (int o = 16; o; o >>= 1) mxv = fmaxf(mxv, __shfl_xor_sync(0xffffffffu, mxv, o));
+      int ex = -100;
+      if (mxv > 0.0f) frexpf(mxv * 1.0001f, &ex);   // max |X_r| < 2^ex
+      ex = max(ex, -100);
+      const float up = ldexpf(1.0f, 24 - ex), unit = ldexpf(1.0f, ex - 24);
+      for (int k = lane; k < mb; k += 32) {
+        float* xp = Xr + (size_t)r * xs + k;
+        *xp = rintf(*xp * up) * unit;
+      }
       if (lane == 0) {
+        colX[r] = unit;
         const float pm = (float)(th.sigma2 + th.tau2) * mxv * (float)max(mb, 4) * 1.0001f;
-        int ex = -100;
-        if (pm > 0.0f) frexpf(pm, &ex);   // pm < 2^ex
-        colC[r] = 1.5f * ldexpf(1.0f, max(ex, -100) - 1);   // 1.5 * 2^23 * 2^(ex - 24)
+        int eg = -100;
+        if (pm > 0.0f) frexpf(pm, &eg);   // pm < 2^eg
+        colC[r] = 1.5f * ldexpf(1.0f, max(eg, -100) - 1);   // 1.5 * 2^23 * 2^(eg - 24)
       }
     }
+    // Sigma_JJ digits: Sigma = 2^(eA - 8) (a1 + a2 2^-8 + ... + a5 2^-32),
+    // |Sigma| <= sigma^2 + tau^2 < 2^eA
+    int eA;
+    frexpf((float)(th.sigma2 + th.tau2) * 1.0001f, &eA);
     __syncthreads();
     constexpr int W = 16;
     for (int cb = 0; cb < nr; cb += W) {
       const int nc = min(W, nr - cb);
       // 6a. Rb[c][k] = Sigma_{J,B'}[k][cb+c] - sum_k' Sigma_JJ[k][k'] X[cb+c][k']
-      // Sigma_JJ is streamed through shared memory in chunks of 8 columns
-      // (cp.async, double-buffered); thread (k, c0) keeps eight columns'
-      // accumulators in registers
+      if (tc) {
+        // Tensor cores, K-steps of 16: every step writes the digit tiles of
+        // Sigma_JJ (128 x 16, rows past mb zero) and of X^ (16 x 16) into
+        // shared memory in the K-major core-matrix layout, then one thread
+        // issues the 12 digit products (s, t) with s + t <= 6 as
+        // 128 x 16 x 16 BF16 MMAs into TMEM group g = s + t - 2.  With
+        // |a_1|, |b_1| <= 256 and the other digits <= 128, every group's
+        // sum over K <= 128 stays below 2^24 (integers): exact in FP32.
+        const int nks = (mb + 15) >> 4;
+        const int am = tid >> 1, ak = (tid & 1) * 8;   // A digits: row am, k ak..ak+7
+        float2 sv[8];
+        auto load_sv = [&](int ks) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int kk = ks * 16 + ak + j;
+            sv[j] = (tid < 256 && am < mb && kk < mb) ? S[(size_t)kk * N + am]
+                                                      : make_float2(0.0f, 0.0f);
+          }
+        };
+        load_sv(0);
+        const float sc8 = ldexpf(1.0f, 8 - eA);
+        for (int ks = 0; ks < nks; ++ks) {
+          if (ks > 0) {   // the previous step's MMAs have read the digit tiles
+            const bool ok = umma::mbar_wait(&mma_bar, mma_phase, 1u << 24);
+            mma_phase ^= 1u;
+            if (!ok) s_timeout = 1;
+          }
+          if (tid < 256) {
+            // five digits of 8 entries of Sigma_JJ, packed two BF16 per word
+            uint32_t dg[5][4];
+#pragma unroll
+            for (int j = 0; j < 8; j += 2) {
+              float dv[2][5];
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                // the float head gives the first three digits exactly (|t| < 256,
+                // every step an exact power-of-two scaling or subtraction); the
+                // tail joins before the fourth
+                float t = sv[j + h].x * sc8;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                  const float dq = rintf(t);
+                  dv[h][q] = dq;
+                  t = __fsub_rn(t, dq) * 256.0f;
+                }
+                t = __fmaf_rn(sv[j + h].y, sc8 * 16777216.0f, t);
+                const float d4 = rintf(t);
+                dv[h][3] = d4;
+                dv[h][4] = rintf(__fsub_rn(t, d4) * 256.0f);
+              }
+#pragma unroll
+              for (int q = 0; q < 5; ++q) {
+                const __nv_bfloat162 p2 = __floats2bfloat162_rn(dv[0][q], dv[1][q]);
+                dg[q][j >> 1] = *(const uint32_t*)&p2;
+              }
+            }
+            const uint32_t off = umma::op_offset(am, ak);
+#pragma unroll
+            for (int q = 0; q < 5; ++q)
+              *(uint4*)(Ab + q * 4096 + off) = make_uint4(dg[q][0], dg[q][1], dg[q][2], dg[q][3]);
+            if (tid < 32) {
+              // three digits of 8 entries of X^ (row n = column cb + n of X)
+              const int n = tid >> 1;
+              const int r = cb + n;
+              uint32_t bd[3][4];
+              const float iu = r < nr ? 1.0f / colX[r] : 0.0f;   // a power of two
+#pragma unroll
+              for (int j = 0; j < 8; j += 2) {
+                float bv[2][3];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  const int kk = ks * 16 + ak + j + h;
+                  // integer T = X^ / unit, |T| < 2^24: exact in FP32
+                  const float T = (r < nr && kk < mb) ? Xr[(size_t)r * xs + kk] * iu : 0.0f;
+                  const float b1 = rintf(T * (1.0f / 65536.0f));
+                  const float r1 = __fsub_rn(T, b1 * 65536.0f);
+                  const float b2 = rintf(r1 * (1.0f / 256.0f));
+                  bv[h][0] = b1;
+                  bv[h][1] = b2;
+                  bv[h][2] = __fsub_rn(r1, b2 * 256.0f);
+                }
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                  const __nv_bfloat162 p2 = __floats2bfloat162_rn(bv[0][q], bv[1][q]);
+                  bd[q][j >> 1] = *(const uint32_t*)&p2;
+                }
+              }
+              const uint32_t boff = umma::op_offset(n, ak);
+#pragma unroll
+              for (int q = 0; q < 3; ++q)
+                *(uint4*)(Bb + q * 512 + boff) = make_uint4(bd[q][0], bd[q][1], bd[q][2], bd[q][3]);
+            }
+          }
+          if (ks + 1 < nks) load_sv(ks + 1);
+          umma::fence_proxy_async();
+          umma::fence_before_sync();
+          __syncthreads();
+          if (tid == 0 && !s_timeout) {
+            umma::fence_after_sync();
+            const uint32_t ab = umma::smem_u32(Ab), bb = umma::smem_u32(Bb);
+            const uint32_t idesc = umma::idesc_bf16_f32(128, 16);
+            // (s, t, group) with s + t <= 6; the first product of a group at
+            // the first K-step overwrites the accumulator
+            const int ps[12] = {1, 1, 2, 1, 2, 3, 2, 3, 4, 3, 4, 5};
+            const int pt[12] = {1, 2, 1, 3, 2, 1, 3, 2, 1, 3, 2, 1};
+            const int first[12] = {1, 1, 0, 1, 0, 0, 1, 0, 0, 1, 0, 0};
+#pragma unroll
+            for (int q = 0; q < 12; ++q) {
+              const uint64_t ad = umma::smem_desc(ab + (ps[q] - 1) * 4096, 128, 256);
+              const uint64_t bdsc = umma::smem_desc(bb + (pt[q] - 1) * 512, 128, 256);
+              const uint32_t g = (uint32_t)(ps[q] + pt[q] - 2);
+              umma::mma_bf16(tmem_base + g * 16, ad, bdsc, idesc, (ks > 0 || !first[q]) ? 1u : 0u);
+            }
+            umma::mma_commit(&mma_bar);
+          }
+        }
+        // the last step's products, then the five groups are read back by
+        // warps 0-3 (TMEM lanes = rows k) and combined in double-float:
+        // D = 2^(eA + 8) unit_r sum_g G_g 2^(-8 g)
+        if (nks > 0) {
+          const bool ok = umma::mbar_wait(&mma_bar, mma_phase, 1u << 24);
+          mma_phase ^= 1u;
+          if (!ok) s_timeout = 1;
+        }
+        umma::fence_after_sync();
+        if (warp < 4 && nks > 0 && !s_timeout) {
+          df acc[16];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) acc[c] = {0.0f, 0.0f};
+          const uint32_t ta = tmem_base + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+          for (int g = 4; g >= 0; --g) {   // smallest weight first
+            float gv[16];
+            umma::tmem_ld16(ta + (uint32_t)(g * 16), gv);
+            umma::tmem_wait_ld();
+            const float wg = ldexpf(1.0f, -8 * g);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[c] = df_add_f(acc[c], gv[c] * wg);
+          }
+          const int k = 32 * warp + lane;
+          if (k < mb) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const int r = cb + c;
+              if (c < nc) {
+                const float scl = ldexpf(colX[r], eA + 8);   // exact power of two
+                const df dd = {acc[c].h * scl, acc[c].l * scl};
+                const float2 v = r < bs ? S[(size_t)(mb + r) * N + k] : yv[k];
+                const df rv = df_sub_acc(df{v.x, v.y}, dd);
+                Rb[(size_t)c * xs + k] = __fadd_rn(rv.h, rv.l);
+              }
+            }
+          }
+        }
+        umma::fence_before_sync();
+      } else {
+      // CUDA cores: Sigma_JJ is streamed through shared memory in chunks of
+      // 8 columns (cp.async, double-buffered); thread (k, c0) keeps eight
+      // columns' accumulators in registers
       {
         constexpr int KC = 8;
         const int nch = (mb + KC - 1) / KC;
@@ -688,6 +886,7 @@ loglik_mixed_kernel(MixedArgs P) {
         }
         }   // task passes
       }
+      }   // tensor or CUDA-core residual
       for (int e = tid; e < nc * (mb4 - mb); e += THREADS) {
         const int c = e / (mb4 - mb);
         Rb[(size_t)c * xs + mb + (e - c * (mb4 - mb))] = 0.0f;
@@ -856,13 +1055,24 @@ loglik_mixed_kernel(MixedArgs P) {
     }
     const double s = cta_sum_mx(v, red);
     if (tid == 0) {
-      const double term = -0.5 * ((double)bs * log2pi + s);
+      double term = -0.5 * ((double)bs * log2pi + s);
+      if (s_timeout) term = nan;
       a.terms[item] = term;
       const bool ok = isfinite(term);
-      if (a.status) a.status[item] = ok ? 0 : SBV_ENOTSPD;
-      if (!ok) record_failure(a.dstat, SBV_ENOTSPD, (int)blk, th_i);
+      const int code = s_timeout ? SBV_ETIMEOUT : SBV_ENOTSPD;
+      if (a.status) a.status[item] = ok ? 0 : code;
+      if (!ok) record_failure(a.dstat, code, (int)blk, th_i);
     }
     __syncthreads();
+    if (s_timeout) break;   // leave the item loop; TMEM is released below
+  }
+  // after a timed-out wait, give the outstanding MMAs one more bounded wait
+  // before the accumulator columns are released
+  if (TC) {
+    if (s_timeout) umma::mbar_wait(&mma_bar, mma_phase, 1u << 24);
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_dealloc(tmem_base, 128);
   }
 }
 
@@ -886,22 +1096,27 @@ static int upload_df_consts(sbv_ctx* ctx) {
   return SBV_OK;
 }
 
-template <int THREADS, bool PRED, bool GA>
+template <int THREADS, bool TC, bool PRED, bool GA>
 static int occ(sbv_ctx* ctx, size_t bytes, int* out) {
   SBV_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        out, loglik_mixed_kernel<THREADS, PRED, GA>, THREADS, bytes));
+                        out, loglik_mixed_kernel<THREADS, TC, PRED, GA>, THREADS, bytes));
   return SBV_OK;
 }
 
-template <int THREADS>
+template <int THREADS, bool TC>
 static int occ_t(sbv_ctx* ctx, bool pred, bool ga, size_t bytes, int* out) {
-  if (ga) return pred ? occ<THREADS, true, true>(ctx, bytes, out) : occ<THREADS, false, true>(ctx, bytes, out);
-  return pred ? occ<THREADS, true, false>(ctx, bytes, out) : occ<THREADS, false, false>(ctx, bytes, out);
+  if (ga) return pred ? occ<THREADS, TC, true, true>(ctx, bytes, out)
+                      : occ<THREADS, TC, false, true>(ctx, bytes, out);
+  return pred ? occ<THREADS, TC, true, false>(ctx, bytes, out)
+              : occ<THREADS, TC, false, false>(ctx, bytes, out);
 }
 
-static int mixed_occupancy(sbv_ctx* ctx, int threads, bool pred, bool ga, size_t bytes, int* out) {
-  return threads == 512 ? occ_t<512>(ctx, pred, ga, bytes, out)
-                        : occ_t<256>(ctx, pred, ga, bytes, out);
+static int mixed_occupancy(sbv_ctx* ctx, int threads, bool tc, bool pred, bool ga, size_t bytes,
+                           int* out) {
+  if (tc) return threads == 512 ? occ_t<512, true>(ctx, pred, ga, bytes, out)
+                                : occ_t<256, true>(ctx, pred, ga, bytes, out);
+  return threads == 512 ? occ_t<512, false>(ctx, pred, ga, bytes, out)
+                        : occ_t<256, false>(ctx, pred, ga, bytes, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -912,14 +1127,18 @@ static int mixed_occupancy(sbv_ctx* ctx, int threads, bool pred, bool ga, size_t
 // ---------------------------------------------------------------------------
 static int mixed_static_smem(sbv_ctx* ctx, size_t* out);
 
-int mixed_plan(sbv_ctx* ctx, int nmax, int mcap, int d, int precision, bool pred, int64_t items,
-               MixedPlan* o) {
+int mixed_plan(sbv_ctx* ctx, int nmax, int mcap, int bcap, int d, int precision, bool pred,
+               int64_t items, MixedPlan* o) {
   const int ncap = std::max(nmax, 1);
+  // the tensor-core residual is the SBV_PREC_MIXED_BF16 variant (likelihood only)
+  const bool tc = precision == SBV_PREC_MIXED_BF16 && !pred;
   o->pred = pred;
-  o->lay = mixed_layout(ncap, mcap, d);
+  o->tc = tc;
+  o->lay = mixed_layout(ncap, mcap, bcap, d, tc);
   size_t static_smem = 0;
   if (int st0 = mixed_static_smem(ctx, &static_smem)) return st0;
-  if (o->lay.bytes + static_smem > ctx->smem_optin) o->lay = mixed_layout(ncap, mcap, d, true);
+  if (o->lay.bytes + static_smem > ctx->smem_optin)
+    o->lay = mixed_layout(ncap, mcap, bcap, d, tc, true);
   if (o->lay.bytes + static_smem > ctx->smem_optin)
     return fail(ctx, SBV_EUNSUPPORTED,
                 "mixed path: a block with N=%d (d=%d) needs %zu bytes of shared memory", nmax, d,
@@ -938,7 +1157,7 @@ int mixed_plan(sbv_ctx* ctx, int nmax, int mcap, int d, int precision, bool pred
       }
   }
   int fit = 0;
-  if ((st = mixed_occupancy(ctx, threads, pred, o->lay.ga, o->lay.bytes, &fit))) return st;
+  if ((st = mixed_occupancy(ctx, threads, tc, pred, o->lay.ga, o->lay.bytes, &fit))) return st;
   if (fit < 1)
     return fail(ctx, SBV_EUNSUPPORTED, "mixed path: no CTA of %d threads fits an SM (N=%d, d=%d)",
                 threads, nmax, d);
@@ -959,12 +1178,12 @@ int mixed_split(sbv_ctx* ctx, const void* X, int dtype, int64_t total, float2* x
   return SBV_OK;
 }
 
-template <int THREADS, bool PRED>
+template <int THREADS, bool TC, bool PRED>
 static int launch_variant(sbv_ctx* ctx, const MixedArgs& P, int grid, cudaStream_t s) {
   if (P.lay.ga)
-    loglik_mixed_kernel<THREADS, PRED, true><<<grid, THREADS, P.lay.bytes, s>>>(P);
+    loglik_mixed_kernel<THREADS, TC, PRED, true><<<grid, THREADS, P.lay.bytes, s>>>(P);
   else
-    loglik_mixed_kernel<THREADS, PRED, false><<<grid, THREADS, P.lay.bytes, s>>>(P);
+    loglik_mixed_kernel<THREADS, TC, PRED, false><<<grid, THREADS, P.lay.bytes, s>>>(P);
   SBV_LAUNCH_CHECK(ctx, "loglik_mixed_kernel");
   return SBV_OK;
 }
@@ -972,13 +1191,13 @@ static int launch_variant(sbv_ctx* ctx, const MixedArgs& P, int grid, cudaStream
 // Both variants may use the largest dynamic shared memory; the global-A
 // variant prefers the smallest shared-memory carve-out so that the rest of
 // the SM's 256 KB serves as L1 for its slices.
-template <int THREADS, bool PRED>
+template <int THREADS, bool TC, bool PRED>
 static int allow_smem(sbv_ctx* ctx, int bytes) {
-  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<THREADS, PRED, false>,
+  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<THREADS, TC, PRED, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<THREADS, PRED, true>,
+  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<THREADS, TC, PRED, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<THREADS, PRED, true>,
+  SBV_CUDA_TRY(ctx, cudaFuncSetAttribute(loglik_mixed_kernel<THREADS, TC, PRED, true>,
                                          cudaFuncAttributePreferredSharedMemoryCarveout, 0));
   return SBV_OK;
 }
@@ -986,11 +1205,11 @@ static int allow_smem(sbv_ctx* ctx, int bytes) {
 static bool g_mixed_ready[64];
 static size_t g_mixed_static[64];
 
-template <int THREADS, bool PRED>
+template <int THREADS, bool TC, bool PRED>
 static size_t static_smem_of() {
   cudaFuncAttributes a{}, b{};
-  if (cudaFuncGetAttributes(&a, loglik_mixed_kernel<THREADS, PRED, false>) != cudaSuccess ||
-      cudaFuncGetAttributes(&b, loglik_mixed_kernel<THREADS, PRED, true>) != cudaSuccess)
+  if (cudaFuncGetAttributes(&a, loglik_mixed_kernel<THREADS, TC, PRED, false>) != cudaSuccess ||
+      cudaFuncGetAttributes(&b, loglik_mixed_kernel<THREADS, TC, PRED, true>) != cudaSuccess)
     return 0;
   return std::max(a.sharedSizeBytes, b.sharedSizeBytes);
 }
@@ -1002,8 +1221,10 @@ static int mixed_static_smem(sbv_ctx* ctx, size_t* out) {
     *out = g_mixed_static[dev];
     return SBV_OK;
   }
-  const size_t v[4] = {static_smem_of<256, false>(), static_smem_of<256, true>(),
-                       static_smem_of<512, false>(), static_smem_of<512, true>()};
+  // prediction never takes the tensor-core residual: no <TC, PRED> variant
+  const size_t v[6] = {static_smem_of<256, false, false>(), static_smem_of<256, false, true>(),
+                       static_smem_of<512, false, false>(), static_smem_of<512, false, true>(),
+                       static_smem_of<256, true, false>(),  static_smem_of<512, true, false>()};
   size_t m = 0;
   for (size_t x : v) {
     if (x == 0) return fail(ctx, SBV_ECUDA, "mixed path: cudaFuncGetAttributes failed");
@@ -1024,8 +1245,9 @@ int mixed_prepare(sbv_ctx* ctx) {
   size_t stat = 0;
   if ((st = mixed_static_smem(ctx, &stat))) return st;
   const int b = (int)(ctx->smem_optin - stat);
-  if ((st = allow_smem<256, false>(ctx, b)) || (st = allow_smem<256, true>(ctx, b)) ||
-      (st = allow_smem<512, false>(ctx, b)) || (st = allow_smem<512, true>(ctx, b)))
+  if ((st = allow_smem<256, false, false>(ctx, b)) || (st = allow_smem<256, false, true>(ctx, b)) ||
+      (st = allow_smem<512, false, false>(ctx, b)) || (st = allow_smem<512, false, true>(ctx, b)) ||
+      (st = allow_smem<256, true, false>(ctx, b)) || (st = allow_smem<512, true, false>(ctx, b)))
     return st;
   if (ctx->device < 64) g_mixed_ready[ctx->device] = true;
   return SBV_OK;
@@ -1037,19 +1259,22 @@ int mixed_enqueue(sbv_ctx* ctx, MixedArgs& P, const MixedPlan& o, cudaStream_t s
   int st = 0;
   if ((st = mixed_prepare(ctx))) return st;
   P.lay = o.lay;
-  if (o.threads == 512)
-    return o.pred ? launch_variant<512, true>(ctx, P, o.grid, s)
-                  : launch_variant<512, false>(ctx, P, o.grid, s);
-  return o.pred ? launch_variant<256, true>(ctx, P, o.grid, s)
-                : launch_variant<256, false>(ctx, P, o.grid, s);
+  if (o.pred)
+    return o.threads == 512 ? launch_variant<512, false, true>(ctx, P, o.grid, s)
+                            : launch_variant<256, false, true>(ctx, P, o.grid, s);
+  if (o.tc)
+    return o.threads == 512 ? launch_variant<512, true, false>(ctx, P, o.grid, s)
+                            : launch_variant<256, true, false>(ctx, P, o.grid, s);
+  return o.threads == 512 ? launch_variant<512, false, false>(ctx, P, o.grid, s)
+                          : launch_variant<256, false, false>(ctx, P, o.grid, s);
 }
 
 // Plan, split the points and take the scratch from the context workspace.
-static int launch_mixed(sbv_ctx* ctx, MixedArgs& P, int nmax, int mcap, int precision, bool pred,
-                        int64_t items, cudaStream_t s) {
+static int launch_mixed(sbv_ctx* ctx, MixedArgs& P, int nmax, int mcap, int bcap, int precision,
+                        bool pred, int64_t items, cudaStream_t s) {
   int st = 0;
   MixedPlan o;
-  if ((st = mixed_plan(ctx, nmax, mcap, P.a.d, precision, pred, items, &o))) return st;
+  if ((st = mixed_plan(ctx, nmax, mcap, bcap, P.a.d, precision, pred, items, &o))) return st;
   const int64_t total = P.a.n * P.a.d;
   P.Xs = nullptr;
   if (P.a.dtype == SBV_F64) {
@@ -1064,14 +1289,14 @@ static int launch_mixed(sbv_ctx* ctx, MixedArgs& P, int nmax, int mcap, int prec
   return mixed_enqueue(ctx, P, o, s);
 }
 
-int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a0, int nmax, int precision,
+int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a0, int nmax, int bsmax, int precision,
                         unsigned int* fb_list, unsigned int* fb_count, cudaStream_t s) {
   MixedArgs P;
   memset(&P, 0, sizeof(P));
   P.a = a0;
   P.fb_list = fb_list;
   P.fb_count = fb_count;
-  return launch_mixed(ctx, P, nmax, a0.m, precision, false, a0.bc * (int64_t)a0.B, s);
+  return launch_mixed(ctx, P, nmax, a0.m, bsmax, precision, false, a0.bc * (int64_t)a0.B, s);
 }
 
 // Prediction: a0 carries X, y, d, nbr (ntest x m), m, theta, nu2, dstat, counter.
@@ -1088,7 +1313,7 @@ int launch_predict_mixed(sbv_ctx* ctx, const LoglikArgs& a0, const void* Xt, int
   P.var_latent = var_latent;
   P.fb_list = fb_list;
   P.fb_count = fb_count;
-  return launch_mixed(ctx, P, a0.m + 1, a0.m, precision, true, nt, s);
+  return launch_mixed(ctx, P, a0.m + 1, a0.m, 1, precision, true, nt, s);
 }
 
 }  // namespace sbv

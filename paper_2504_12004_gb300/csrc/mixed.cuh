@@ -50,8 +50,9 @@ __host__ __device__ __forceinline__ int tri0(int i, int j) { return (i * (i + 1)
 //           conditional system (bordered by y_B - mu) in double-float
 // With ga, A and X live in a per-CTA slice of global memory instead.
 //   union   residual phase: a block of 16 residual columns (then L^{-1} of
-//           them), the fixed-point grid constant of every right-hand side and
-//           two staged chunks of 8 columns of Sigma_JJ
+//           them), two constants per right-hand side, and either two staged
+//           chunks of 8 columns of Sigma_JJ (CUDA-core residual) or the BF16
+//           digit tiles of one K-step (tensor-core residual)
 // Per-CTA global memory: the double-float joint covariance (N x N, both
 // triangles), L^{-1} R for every right-hand side and the partial
 // Schur-complement system.
@@ -68,19 +69,26 @@ struct MixedLayout {
   size_t g_R, g_Sp, g_A, g_X, g_stride;
 };
 
-__host__ __device__ inline MixedLayout mixed_layout(int ncap, int mcap, int d, bool ga = false) {
+// bcap: the largest bs of the structure when known (0: any bs up to ncap).
+__host__ __device__ inline MixedLayout mixed_layout(int ncap, int mcap, int bcap, int d,
+                                                    bool tc, bool ga = false) {
   MixedLayout L;
   L.ncap = ncap;
   L.mcap = mcap < ncap ? mcap : ncap;
   L.d = d;
   L.ga = ga;
   L.a_floats = align_up(trp_size(L.mcap), 64);
-  // the largest right-hand-side block: nr = N + 1 - mb rows of rhs_stride(mb)
+  // the largest right-hand-side block: nr = N + 1 - mb rows (at most bcap + 1)
+  // of rhs_stride(mb); with bcap known, also room for the largest bordered
+  // conditional system, (bcap + 1) (bcap + 2) floats
+  const int nrcap = bcap > 0 && bcap < ncap ? bcap + 1 : ncap + 1;
   size_t xf = 8;
   for (int mb = 0; mb <= L.mcap; ++mb) {
-    const size_t v = (size_t)(ncap + 1 - mb) * rhs_stride(mb);
+    const int nr = ncap + 1 - mb < nrcap ? ncap + 1 - mb : nrcap;
+    const size_t v = (size_t)nr * rhs_stride(mb);
     if (v > xf) xf = v;
   }
+  if (bcap > 0 && (size_t)nrcap * (nrcap + 1) > xf) xf = (size_t)nrcap * (nrcap + 1);
   L.x_floats = align_up(xf, 64);
   L.pstride = (int)align_up((size_t)ncap + 1, 4);
   size_t o = 0;
@@ -94,17 +102,22 @@ __host__ __device__ inline MixedLayout mixed_layout(int ncap, int mcap, int d, b
   // residual phase: a block of 16 right-hand sides of the residual, then one
   // grid constant per right-hand side
   const size_t rblk = align_up((size_t)16 * rhs_stride(L.mcap) * sizeof(float), 16);
-  const size_t cc = align_up((size_t)(ncap + 2) * sizeof(float), 16);
-  const size_t sch = (size_t)2 * 8 * L.mcap * sizeof(float2);   // two chunks of 8 columns
+  const size_t cc = align_up((size_t)2 * (ncap + 2) * sizeof(float), 128);
+  // CUDA-core residual: two chunks of 8 columns of Sigma_JJ; tensor-core
+  // residual: five 128 x 16 BF16 digit tiles of Sigma_JJ and three 16 x 16
+  // digit tiles of X (K-major core-matrix layout)
+  const size_t sch_cuda = (size_t)2 * 8 * L.mcap * sizeof(float2);
+  const size_t sch_tc = 5 * 4096 + 3 * 512;
+  const size_t sch = tc ? (sch_cuda > sch_tc ? sch_cuda : sch_tc) : sch_cuda;
   size_t uni = 2 * coord + tab;
   if (panel + stile > uni) uni = panel + stile;
-  if (rblk + cc + sch > uni) uni = rblk + cc + sch;
+  if (align_up(rblk, 128) + cc + sch > uni) uni = align_up(rblk, 128) + cc + sch;
   L.off_u = o;
   L.off_vl = o + coord;
   L.off_tab = o + 2 * coord;
   L.off_stile = o + panel;
-  L.off_cc = o + rblk;
-  L.off_sch = o + rblk + cc;
+  L.off_cc = o + align_up(rblk, 128);
+  L.off_sch = L.off_cc + cc;   // 128-byte aligned (the digit tiles need 16)
   o += align_up(uni, 128);
   L.off_A = o;
   if (!ga) o += L.a_floats * sizeof(float);
@@ -141,13 +154,13 @@ struct MixedArgs {
 
 struct MixedPlan {
   MixedLayout lay;
-  bool pred;
+  bool pred, tc;
   int threads, grid;
   size_t scratch_bytes() const { return lay.g_stride * sizeof(float) * (size_t)grid; }
 };
 
-int mixed_plan(sbv_ctx* ctx, int nmax, int mcap, int d, int precision, bool pred, int64_t items,
-               MixedPlan* o);
+int mixed_plan(sbv_ctx* ctx, int nmax, int mcap, int bcap, int d, int precision, bool pred,
+               int64_t items, MixedPlan* o);
 int mixed_split(sbv_ctx* ctx, const void* X, int dtype, int64_t total, float2* xs,
                 cudaStream_t s);
 int mixed_enqueue(sbv_ctx* ctx, MixedArgs& P, const MixedPlan& o, cudaStream_t s);

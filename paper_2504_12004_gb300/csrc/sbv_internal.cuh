@@ -76,6 +76,13 @@ struct sbv_ctx {
   sbv::LaunchShape force;              // set while the autotuner times a shape
   std::vector<sbv::TunedShape> tuned;  // autotuning records
   int knn_mode = 0;                    // 0 automatic, 1 brute force, 2 pruned search
+  // largest block sizes last read for a structure (ptr, cnt, bc): calls with a
+  // size hint reuse bsmax for the same arrays (a stale value only makes the
+  // mixed kernel hand the oversized items to the FP64 kernel)
+  const void* sz_ptr = nullptr;
+  const void* sz_cnt = nullptr;
+  int64_t sz_bc = 0;
+  int sz_nmax = 0, sz_bsmax = 0;
   // pinned host ring for parameter rows: slot k is reused only after the
   // event recorded behind its previous copy has completed
   static const int kRing = 8;
@@ -123,6 +130,8 @@ int run_knn_blocks_all(sbv_ctx* ctx, const double* Z, int64_t n, int d, const in
                        int64_t bc, const double* Q, int64_t nq, int m, int32_t* nbr,
                        cudaStream_t s);
 // likelihood and prediction
+int run_max_sizes(sbv_ctx* ctx, const int64_t* ptr, const int32_t* cnt, int64_t bc, int* nmax,
+                  int* bsmax, cudaStream_t s);
 int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n,
                int d, const int64_t* ptr, const int32_t* pts, const int32_t* nbr,
                const int32_t* cnt, int64_t bc, int m, int nmax, const double* h_theta,

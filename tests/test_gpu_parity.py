@@ -296,19 +296,27 @@ def test_loglik_large_blocks_use_global_scratch(ctx, precision, tol):
 
 @pytest.mark.parametrize("precision", ["mixed", "mixed_bf16"])
 def test_mixed_hands_over_blocks_beyond_its_capacity(ctx, precision):
-    # one block of every point and no neighbours: its 300 x 300 conditional
-    # system exceeds the mixed kernel's capacity, so the FP64 kernel computes
-    # it in the same call; the singleton blocks stay on the mixed path
+    # one block of every point and no neighbours, evaluated with a size hint
+    # (so the kernel's layout cannot assume the block sizes): its 300 x 300
+    # conditional system exceeds the mixed kernel's capacity, so the FP64
+    # kernel computes it in the same call; without the hint the sizes are
+    # read and the mixed kernel holds it; singleton blocks stay mixed
     X = uniform_points(300, 2, 41)
     y = standard_normal(300, 42)
     th = np.array([1.0, 0.01, 0.3, 0.6])
     ctx.sbv_sync_status()
     one = dict(ptr=np.array([0, 300]), pts=np.arange(300), nbr=np.full((1, 1), -1),
                cnt=np.array([0]), rank=np.array([0]))
-    ll, _, st = gpu_loglik(ctx, X, y, one, th, 5, precision, terms=False)
     want = sbv.loglik(X, y, one["ptr"], one["pts"], one["nbr"], one["cnt"], one["rank"], th, 5)
-    assert np.all(st == 0)
-    assert abs(ll[0] - want) / 300 <= TOL_FP64
+    st = torch.empty(1, 1, dtype=torch.int32, device="cuda")
+    ll = ctx.sbv_loglik(cuda(X), cuda(y), cuda(one["ptr"], torch.int64), cuda(one["pts"], torch.int32),
+                        cuda(one["nbr"], torch.int32), cuda(one["cnt"], torch.int32), th, nu2=5,
+                        precision=precision, status=st, nmax=300)
+    assert torch.all(st == 0)
+    assert abs(ll[0].item() - want) / 300 <= TOL_FP64
+    assert ctx.sbv_fp64_reruns() == 1
+    ll, _, _ = gpu_loglik(ctx, X, y, one, th, 5, precision, terms=False)
+    assert abs(ll[0] - want) / 300 <= TOL_MIXED
     assert ctx.sbv_fp64_reruns() == 1
     sing = dict(ptr=np.arange(301), pts=np.arange(300), nbr=np.full((300, 1), -1),
                 cnt=np.zeros(300, dtype=np.int64), rank=np.arange(300))
