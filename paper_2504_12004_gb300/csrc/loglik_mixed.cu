@@ -604,7 +604,6 @@ loglik_mixed_kernel(MixedArgs P) {
     float* Rb = (float*)(smem + lay.off_u);      // residual block, then L^{-1} of it
     float* colC = (float*)(smem + lay.off_cc);   // C_r per right-hand side (CUDA-core residual)
     float* colX = colC + lay.ncap + 2;           // grid unit of X^ per right-hand side
-    float2* Sch = (float2*)(smem + lay.off_sch); // staged columns of Sigma_JJ (CUDA cores)
     unsigned char* Ab = smem + lay.off_sch;      // five BF16 digit tiles of Sigma_JJ (tensor cores)
     unsigned char* Bb = Ab + 5 * 4096;           // three BF16 digit tiles of X^ (tensor cores)
     float* Qg = Rg;                              // L^{-1} R for every column, global
@@ -797,94 +796,77 @@ loglik_mixed_kernel(MixedArgs P) {
         }
         umma::fence_before_sync();
       } else {
-      // CUDA cores: Sigma_JJ is streamed through shared memory in chunks of
-      // 8 columns (cp.async, double-buffered); thread (k, c0) keeps eight
-      // columns' accumulators in registers
+      // CUDA cores: thread (k, c0) streams row k of Sigma_JJ itself
+      // (S[kp N + k], coalesced over the warp's rows k) with the next four
+      // loads in flight, and keeps eight columns' accumulators in registers;
+      // no CTA barrier inside
       {
-        constexpr int KC = 8;
-        const int nch = (mb + KC - 1) / KC;
-        auto stage_chunk = [&](int ch) {
-          float2* dst = Sch + (size_t)(ch & 1) * KC * lay.mcap;
-          const int kp0 = ch * KC, kn = min(KC, mb - kp0);
-          for (int e = tid; e < kn * mb; e += THREADS) {
-            const int c = e / mb, kk = e - c * mb;
-            const uint32_t sa = (uint32_t)__cvta_generic_to_shared(dst + (size_t)c * lay.mcap + kk);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa),
-                         "l"(S + (size_t)(kp0 + c) * N + kk) : "memory");
-          }
-          asm volatile("cp.async.commit_group;" ::: "memory");
-        };
-        // (k, c0) tasks: 2 mb of them, one pass of the CTA per THREADS tasks
         for (int t0 = 0; t0 < 2 * mb; t0 += THREADS) {
-        const int tk = t0 + tid;
-        const bool act = tk < 2 * mb;
-        const int k = act ? tk % mb : 0, c0 = act ? (tk / mb) * 8 : 0;
-        float Cq[8], ahi[8];
-        df atot[8];
+          const int tk = t0 + tid;
+          // tasks whose eight columns all lie past the block do nothing
+          if (tk < 2 * mb && (tk / mb) * 8 < nc) {
+            const int k = tk % mb, c0 = (tk / mb) * 8;
+            float Cq[8], ahi[8];
+            df atot[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          Cq[q] = act && c0 + q < nc ? colC[cb + c0 + q] : 1.0f;
-          ahi[q] = 0.0f;
-          atot[q] = {0.0f, 0.0f};
-        }
-        const float* xc = Xr + (size_t)(cb + c0) * xs;
-        if (nch > 0) stage_chunk(0);
-        for (int ch = 0; ch < nch; ++ch) {
-          if (ch + 1 < nch) {
-            stage_chunk(ch + 1);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-          } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-          }
-          __syncthreads();
-          if (act) {
-            const float2* sc = Sch + (size_t)(ch & 1) * KC * lay.mcap + k;
-            const int kp0 = ch * KC;
+            for (int q = 0; q < 8; ++q) {
+              Cq[q] = c0 + q < nc ? colC[cb + c0 + q] : 1.0f;
+              ahi[q] = 0.0f;
+              atot[q] = {0.0f, 0.0f};
+            }
+            const float* xc = Xr + (size_t)(cb + c0) * xs;
+            const float2* sk = S + k;
+            float2 nx[4];
 #pragma unroll
-            for (int h = 0; h < KC; h += 4) {
-              const int kp = kp0 + h;
-              if (kp < mb4) {
-                float2 sv[4];
+            for (int u = 0; u < 4; ++u) nx[u] = u < mb ? sk[(size_t)u * N] : make_float2(0.0f, 0.0f);
+            float alo[8];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                  sv[u] = kp + u < mb ? sc[(size_t)(h + u) * lay.mcap] : make_float2(0.0f, 0.0f);
+            for (int q = 0; q < 8; ++q) alo[q] = 0.0f;
+            for (int kp = 0; kp < mb4; kp += 4) {
+              float2 sv[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                sv[u] = nx[u];
+                const int kn = kp + 4 + u;
+                nx[u] = kn < mb ? sk[(size_t)kn * N] : make_float2(0.0f, 0.0f);
+              }
+              // the eight columns' chains interleaved, one product each per step
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                  if (c0 + q < nc) {
-                    const float4 x4 = *(const float4*)(xc + (size_t)q * xs + kp);
-                    const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
-                    float alo = 0.0f;
+                  // columns past the block read column cb + c0 (c0 < nc: in
+                  // bounds) and are discarded
+                  const float xq = xc[(size_t)(c0 + q < nc ? q : 0) * xs + kp + u];
+                  const float ph = __fsub_rn(__fmaf_rn(sv[u].x, xq, Cq[q]), Cq[q]);
+                  float rr = __fmaf_rn(sv[u].x, xq, -ph);
+                  rr = __fmaf_rn(sv[u].y, xq, rr);
+                  ahi[q] = __fadd_rn(ahi[q], ph);
+                  alo[q] = __fadd_rn(alo[q], rr);
+                }
+              }
+              if ((kp & 4) || kp + 4 >= mb4) {   // fold every eight products
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                      const float ph = __fsub_rn(__fmaf_rn(sv[u].x, xv[u], Cq[q]), Cq[q]);
-                      float rr = __fmaf_rn(sv[u].x, xv[u], -ph);
-                      rr = __fmaf_rn(sv[u].y, xv[u], rr);
-                      ahi[q] = __fadd_rn(ahi[q], ph);
-                      alo = __fadd_rn(alo, rr);
-                    }
-                    const df u2 = two_sum(atot[q].h, alo);
-                    atot[q].h = u2.h;
-                    atot[q].l = __fadd_rn(atot[q].l, u2.l);
-                  }
+                for (int q = 0; q < 8; ++q) {
+                  const df u2 = two_sum(atot[q].h, alo[q]);
+                  atot[q].h = u2.h;
+                  atot[q].l = __fadd_rn(atot[q].l, u2.l);
+                  alo[q] = 0.0f;
                 }
               }
             }
-          }
-          __syncthreads();   // the chunk's buffer is refilled two steps later
-        }
-        if (act) {
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int r = cb + c0 + q;
-            if (c0 + q < nc) {
-              const float2 v = r < bs ? S[(size_t)(mb + r) * N + k] : yv[k];
-              df rv = df_sub_acc(df{v.x, v.y}, df{ahi[q], 0.0f});
-              rv = df_sub_acc(rv, atot[q]);
-              Rb[(size_t)(c0 + q) * xs + k] = __fadd_rn(rv.h, rv.l);
+            for (int q = 0; q < 8; ++q) {
+              const int r = cb + c0 + q;
+              if (c0 + q < nc) {
+                const float2 v = r < bs ? S[(size_t)(mb + r) * N + k] : yv[k];
+                df rv = df_sub_acc(df{v.x, v.y}, df{ahi[q], 0.0f});
+                rv = df_sub_acc(rv, atot[q]);
+                Rb[(size_t)(c0 + q) * xs + k] = __fadd_rn(rv.h, rv.l);
+              }
             }
           }
         }
-        }   // task passes
       }
       }   // tensor or CUDA-core residual
       for (int e = tid; e < nc * (mb4 - mb); e += THREADS) {

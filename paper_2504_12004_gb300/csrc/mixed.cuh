@@ -50,9 +50,8 @@ __host__ __device__ __forceinline__ int tri0(int i, int j) { return (i * (i + 1)
 //           conditional system (bordered by y_B - mu) in double-float
 // With ga, A and X live in a per-CTA slice of global memory instead.
 //   union   residual phase: a block of 16 residual columns (then L^{-1} of
-//           them), two constants per right-hand side, and either two staged
-//           chunks of 8 columns of Sigma_JJ (CUDA-core residual) or the BF16
-//           digit tiles of one K-step (tensor-core residual)
+//           them), two constants per right-hand side and (tensor-core
+//           residual) the BF16 digit tiles of one K-step
 // Per-CTA global memory: the double-float joint covariance (N x N, both
 // triangles), L^{-1} R for every right-hand side and the partial
 // Schur-complement system.
@@ -103,12 +102,9 @@ __host__ __device__ inline MixedLayout mixed_layout(int ncap, int mcap, int bcap
   // grid constant per right-hand side
   const size_t rblk = align_up((size_t)16 * rhs_stride(L.mcap) * sizeof(float), 16);
   const size_t cc = align_up((size_t)2 * (ncap + 2) * sizeof(float), 128);
-  // CUDA-core residual: two chunks of 8 columns of Sigma_JJ; tensor-core
-  // residual: five 128 x 16 BF16 digit tiles of Sigma_JJ and three 16 x 16
-  // digit tiles of X (K-major core-matrix layout)
-  const size_t sch_cuda = (size_t)2 * 8 * L.mcap * sizeof(float2);
-  const size_t sch_tc = 5 * 4096 + 3 * 512;
-  const size_t sch = tc ? (sch_cuda > sch_tc ? sch_cuda : sch_tc) : sch_cuda;
+  // tensor-core residual: five 128 x 16 BF16 digit tiles of Sigma_JJ and
+  // three 16 x 16 digit tiles of X (K-major core-matrix layout)
+  const size_t sch = tc ? 5 * 4096 + 3 * 512 : 0;
   size_t uni = 2 * coord + tab;
   if (panel + stile > uni) uni = panel + stile;
   if (align_up(rblk, 128) + cc + sch > uni) uni = align_up(rblk, 128) + cc + sch;
