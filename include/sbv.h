@@ -67,6 +67,7 @@ extern "C" {
 #define SBV_MAX_DIM      64     /* d */
 #define SBV_MAX_NU2      40     /* largest 2 nu of the FP64 paths (nu <= 20) */
 #define SBV_MAX_BLOCK_N  1024   /* m_i + bs_i of one block */
+#define SBV_MAX_DRAWS    (1 << 24)  /* draws per test point of sbv_simulate */
 
 typedef struct sbv_ctx sbv_ctx;
 
@@ -136,6 +137,49 @@ int sbv_blocking_partitioned(sbv_ctx* ctx, const void* X, int dtype, int64_t n, 
                              uint64_t seed, int32_t partitions, int32_t* blk, int64_t* ptr,
                              int32_t* pts, int32_t* rank, double* centres, int64_t* bc_eff,
                              void* stream);
+
+/*
+ * The pieces of sbv_blocking_partitioned for a distributed blocking, where
+ * worker q holds only the points of slab q (Alg. 2 redistributes them with an
+ * Alltoall; Alg. 3 then runs on every worker without communication).
+ *
+ * sbv_slabs -- slab of every point, int(x_dmax * P) as in
+ * sbv_blocking_partitioned.  slab: device, n int32 out.  Asynchronous on
+ * `stream`.  Errors: SBV_EINVAL, SBV_ECUDA.
+ *
+ * sbv_rac_plan -- the random choices of sbv_blocking_partitioned, which depend
+ * only on the seed, the slab sizes and bc: host arrays, no context, no GPU.
+ *   slab_counts  P sizes (the sizes of all slabs, in slab order)
+ *   quota        P int64 out (or NULL): anchors k_q per slab
+ *   anchor_pos   sum_q k_q int64 out (or NULL): slab by slab, the anchors of
+ *                slab q as positions in that slab's points listed in
+ *                increasing global index
+ *   bc_eff, rank rank (or NULL): bc_eff int32 out, the block order of
+ *                sbv_blocking_partitioned for bc_eff non-empty blocks numbered
+ *                slab by slab (the draws that follow the anchors in the stream)
+ * Errors: SBV_EINVAL (P < 1, negative counts, bc outside [max(P, 1), n],
+ * bc_eff outside [1, bc] when rank is given).
+ *
+ * sbv_blocking_anchored -- RAC (from the given anchors) plus up to
+ * kmeans_iters Lloyd iterations on one partition, as sbv_blocking does inside
+ * a slab, without the block order.
+ *   anchors      host, k distinct int64 point indices in [0, n)
+ *   blk, ptr, pts, centres, bc_eff   as sbv_blocking (blocks in anchor order;
+ *                empty ones dropped keeping that order)
+ * With the points of slab q in increasing global index and the anchors
+ * anchor_pos of slab q, the blocks equal those of slab q in
+ * sbv_blocking_partitioned bit for bit.  Synchronises `stream`.
+ * Errors: SBV_EINVAL (also for repeated or out-of-range anchors), SBV_ENOMEM,
+ * SBV_ECUDA.
+ */
+int sbv_slabs(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_t d,
+              const double* beta_scale, int32_t partitions, int32_t* slab, void* stream);
+int sbv_rac_plan(uint64_t seed, int32_t partitions, const int64_t* slab_counts, int64_t bc,
+                 int64_t* quota, int64_t* anchor_pos, int64_t bc_eff, int32_t* rank);
+int sbv_blocking_anchored(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_t d,
+                          const double* beta_scale, const int64_t* anchors, int64_t k,
+                          int32_t kmeans_iters, int32_t* blk, int64_t* ptr, int32_t* pts,
+                          double* centres, int64_t* bc_eff, void* stream);
 
 /*
  * sbv_knn -- earlier-ordered m nearest neighbours of every block (Alg. 4,
@@ -321,6 +365,58 @@ int sbv_predict_blocks(sbv_ctx* ctx, const void* X, int dtype, const double* y, 
                        const int64_t* ptr, const int32_t* pts, const int32_t* rank,
                        const double* centres, int64_t bc, double* mean, double* var,
                        double* var_latent, int32_t* nbr, void* stream);
+
+/*
+ * sbv_simulate -- conditional simulation at the test points (Sec. 5.5): for
+ * every test point j, ndraws samples x_jk ~ N(mean_j, var_j) (var_j is the
+ * variance, as sbv_predict's `var` output: the diagonal of Sigma^new), then
+ * the sample mean, the sample variance s_j^2 = sum_k (x_jk - mean~_j)^2 /
+ * (ndraws - 1) and the 95 % interval mean~_j -/+ z_{0.975} s_j,
+ * z_{0.975} = 1.959963984540054.
+ *
+ *   mean, var          device, ntest doubles (var >= 0; a negative or NaN
+ *                      variance gives NaN outputs for that point)
+ *   ndraws             draws per test point, 2 <= ndraws <= SBV_MAX_DRAWS
+ *                      (the paper takes 1000)
+ *   seed               key of the generator
+ *   index_base         counter index of test point 0: test point j draws as
+ *                      point index_base + j, so a caller that splits its test
+ *                      points into chunks (index_base = first point of the
+ *                      chunk) gets the draws of one call over all of them
+ *   sample_mean, sample_var, ci_lo, ci_hi   device, ntest doubles out
+ *   draws              device, ntest x ndraws doubles out (row j holds the
+ *                      draws of test point j in draw order), or NULL
+ *
+ * Draw k of test point j is a pure function of (seed, index_base + j, k): the
+ * Philox4x64-10 block of counter (k / 4, index_base + j, 0, 0) under key
+ * (seed, 0) (Salmon et al., SC
+ * 2011) gives two pairs of uniforms u = ((w >> 12) + 1/2) 2^-52, and the
+ * Box-Muller transform maps pair (u1, u2) to sqrt(-2 ln u1) cos(2 pi u2) for
+ * k mod 4 in {0, 2} and sqrt(-2 ln u1) sin(2 pi u2) for {1, 3};
+ * x_jk = mean_j + sqrt(var_j) z_jk.  FP64 throughout.  Asynchronous on
+ * `stream`; ntest = 0 is a no-op.  Errors: SBV_EINVAL, SBV_ECUDA.
+ */
+int sbv_simulate(sbv_ctx* ctx, const double* mean, const double* var, int64_t ntest,
+                 int32_t ndraws, uint64_t seed, uint64_t index_base, double* sample_mean,
+                 double* sample_var,
+                 double* ci_lo, double* ci_hi, double* draws, void* stream);
+
+/*
+ * sbv_matern -- the correlation function alone, M_nu(r) of Eq. (maternkernel)
+ * with nu = nu2 / 2 at r = sqrt(d2), through the arithmetic of one precision
+ * of the likelihood: SBV_PREC_FP64 takes the FP64 square root and the closed
+ * form (nu2 in {1, 3, 5, 7}) or the K_nu quadrature (other nu2 up to
+ * SBV_MAX_NU2); the mixed precisions split d2 into a float pair and take the
+ * double-float square root, exponential and closed-form polynomial of their
+ * covariance stage (nu2 in {1, 3, 5, 7}).
+ *
+ *   d2     device, n doubles >= 0: squared scaled distances sum_t (dx_t / beta_t)^2
+ *   out    device, n doubles out
+ *
+ * Asynchronous on `stream`; n = 0 is a no-op.  Errors: SBV_EINVAL, SBV_ECUDA.
+ */
+int sbv_matern(sbv_ctx* ctx, int32_t precision, int32_t nu2, const double* d2, int64_t n,
+               double* out, void* stream);
 
 /*
  * Captured evaluation (Sec. 5.4: all blocks of an evaluation in one batched

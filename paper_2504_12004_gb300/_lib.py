@@ -95,6 +95,12 @@ SIGNATURES = {
     "sbv_autotune": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64, _I32, _I32,
                                _P, _I32, _I32, _I32, C.POINTER(_I32), C.POINTER(_I32), _P]),
     "sbv_peak_probe": (C.c_int, [_P, _I32, C.POINTER(_D)]),
+    "sbv_simulate": (C.c_int, [_P, _P, _P, _I64, _I32, _U64, _U64, _P, _P, _P, _P, _P, _P]),
+    "sbv_matern": (C.c_int, [_P, _I32, _I32, _P, _I64, _P, _P]),
+    "sbv_slabs": (C.c_int, [_P, _P, C.c_int, _I64, _I32, _P, _I32, _P, _P]),
+    "sbv_rac_plan": (C.c_int, [_U64, _I32, _P, _I64, _P, _P, _I64, _P]),
+    "sbv_blocking_anchored": (C.c_int, [_P, _P, C.c_int, _I64, _I32, _P, _P, _I64, _I32,
+                                        _P, _P, _P, _P, C.POINTER(_I64), _P]),
     "sbv_mlp_num_params": (_I64, [_I32]),
     "sbv_mlp_create": (C.c_int, [_P, _I32, _U64, C.POINTER(_P)]),
     "sbv_mlp_destroy": (None, [_P]),
@@ -175,6 +181,26 @@ def _host_f64(a, name: str) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
 
 
+def rac_plan(seed: int, slab_counts, bc: int, bc_eff: int = 0):
+    """Random choices of a partitioned blocking from the slab sizes alone
+    (sbv_rac_plan): (quota per slab, anchor positions slab by slab, block
+    rank for bc_eff blocks or None)."""
+    lib = load()
+    cnt = np.ascontiguousarray(np.asarray(slab_counts, dtype=np.int64))
+    P = cnt.size
+    quota = np.zeros(P, dtype=np.int64)
+    rc = lib.sbv_rac_plan(int(seed) & 0xFFFFFFFFFFFFFFFF, P, _ptr(cnt), bc, _ptr(quota), None, 0, None)
+    if rc != SBV_OK:
+        raise SBVError(rc, "sbv_rac_plan: invalid arguments")
+    pos = np.zeros(int(quota.sum()), dtype=np.int64)
+    rank = np.zeros(bc_eff, dtype=np.int32) if bc_eff else None
+    rc = lib.sbv_rac_plan(int(seed) & 0xFFFFFFFFFFFFFFFF, P, _ptr(cnt), bc, _ptr(quota), _ptr(pos),
+                          bc_eff, _ptr(rank))
+    if rc != SBV_OK:
+        raise SBVError(rc, "sbv_rac_plan: invalid arguments")
+    return quota, pos, rank
+
+
 class Context:
     """An sbv_ctx on one CUDA device (owns the library's workspace)."""
 
@@ -228,6 +254,38 @@ class Context:
         k = bc_eff.value
         return dict(blk=blk, ptr=ptr[:k + 1].contiguous(), pts=pts, rank=rank[:k].contiguous(),
                     centres=centres[:k].contiguous(), bc_eff=k)
+
+    def sbv_slabs(self, X, beta_scale, partitions: int, stream=None) -> torch.Tensor:
+        """Slab of every point (Alg. 2 routing), int32 on the device."""
+        X = _dev(X, None, "X")
+        n, d = X.shape
+        slab = torch.empty(n, dtype=torch.int32, device=X.device)
+        if n:
+            self._check(self.lib.sbv_slabs(self.h, _ptr(X), _xdtype(X), n, d,
+                                           _ptr(_host_f64(beta_scale, "beta_scale")), partitions,
+                                           _ptr(slab), _stream(stream)))
+        return slab
+
+    def sbv_blocking_anchored(self, X, beta_scale, anchors, kmeans_iters: int, stream=None):
+        """RAC from the given anchors (host indices) plus Lloyd iterations on one
+        partition; blocks in anchor order, no block order."""
+        X = _dev(X, None, "X")
+        n, d = X.shape
+        a = np.ascontiguousarray(np.asarray(anchors, dtype=np.int64))
+        k = a.size
+        dev = X.device
+        blk = torch.empty(n, dtype=torch.int32, device=dev)
+        ptr = torch.empty(k + 1, dtype=torch.int64, device=dev)
+        pts = torch.empty(n, dtype=torch.int32, device=dev)
+        centres = torch.empty(k, d, dtype=torch.float64, device=dev)
+        bc_eff = C.c_int64(0)
+        self._check(self.lib.sbv_blocking_anchored(
+            self.h, _ptr(X), _xdtype(X), n, d, _ptr(_host_f64(beta_scale, "beta_scale")), _ptr(a), k,
+            kmeans_iters, _ptr(blk), _ptr(ptr), _ptr(pts), _ptr(centres), C.byref(bc_eff),
+            _stream(stream)))
+        e = bc_eff.value
+        return dict(blk=blk, ptr=ptr[:e + 1].contiguous(), pts=pts, centres=centres[:e].contiguous(),
+                    bc_eff=e)
 
     def sbv_set_knn_mode(self, mode: int):
         """0 automatic, 1 full scan, 2 pruned search (identical results)."""
@@ -415,6 +473,34 @@ class Context:
                 _ptr(var), _ptr(var_lat), _ptr(nbr), _stream(stream))
         self._check(rc)
         return mean, var, var_lat, nbr
+
+    def sbv_simulate(self, mean, var, ndraws: int = 1000, seed: int = 0, index_base: int = 0,
+                     want_draws=False, stream=None):
+        """Conditional simulation from predictive means and variances; returns
+        (sample_mean, sample_var, ci_lo, ci_hi, draws or None)."""
+        mean = _dev(mean, torch.float64, "mean")
+        var = _dev(var, torch.float64, "var")
+        if mean.shape != var.shape or mean.dim() != 1:
+            raise ValueError("mean and var must be 1-d tensors of one length")
+        nt = mean.numel()
+        out = [torch.empty(nt, dtype=torch.float64, device=mean.device) for _ in range(4)]
+        draws = (torch.empty(nt, int(ndraws), dtype=torch.float64, device=mean.device)
+                 if want_draws else None)
+        rc = self.lib.sbv_simulate(self.h, _ptr(mean), _ptr(var), nt, int(ndraws),
+                                   int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                   int(index_base) & 0xFFFFFFFFFFFFFFFF, *[_ptr(t) for t in out],
+                                   _ptr(draws), _stream(stream))
+        self._check(rc)
+        return (*out, draws)
+
+    def sbv_matern(self, d2, nu2: int = 5, precision="fp64", stream=None):
+        """Matern correlation M_nu(sqrt(d2)) through one precision's arithmetic."""
+        d2 = _dev(d2, torch.float64, "d2")
+        out = torch.empty_like(d2)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self._check(self.lib.sbv_matern(self.h, prec, nu2, _ptr(d2), d2.numel(), _ptr(out),
+                                        _stream(stream)))
+        return out
 
 
 class LoglikGraph:

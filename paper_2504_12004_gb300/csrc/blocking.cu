@@ -495,7 +495,7 @@ static int group_by_block(sbv_ctx* ctx, const int32_t* blk, int64_t n, int64_t k
 int run_blocking(sbv_ctx* ctx, const double* Z, const void* X, int dtype, const double* h_beta,
                  int64_t n, int d, int64_t bc, int kmeans_iters, uint64_t seed, int partitions,
                  int32_t* blk, int64_t* ptr, int32_t* pts, int32_t* rank, double* centres,
-                 int64_t* bc_eff, cudaStream_t s) {
+                 int64_t* bc_eff, cudaStream_t s, const int64_t* h_anchors) {
   int st = 0;
   // workspace: two centre buffers, old assignment, sort scratch, counts, ptr
   size_t cbytes = (size_t)bc * d * sizeof(double);
@@ -573,9 +573,13 @@ int run_blocking(sbv_ctx* ctx, const double* Z, const void* X, int dtype, const 
     SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));  // host vectors copied before they go
     bc = K;
   } else {
-    // RAC anchors: first bc entries of a Fisher-Yates shuffle of [0, n)
+    // RAC anchors: first bc entries of a Fisher-Yates shuffle of [0, n), or
+    // the caller's (one partition of a distributed blocking)
     std::vector<int64_t> a64(bc);
-    partial_shuffle(n, bc, rng, a64.data());
+    if (h_anchors)
+      std::copy(h_anchors, h_anchors + bc, a64.begin());
+    else
+      partial_shuffle(n, bc, rng, a64.data());
     std::vector<int32_t> anchors(a64.begin(), a64.end());
     SBV_CUDA_TRY(ctx, cudaMemcpyAsync(d_anchor, anchors.data(), bc * sizeof(int32_t),
                                       cudaMemcpyHostToDevice, s));
@@ -633,6 +637,11 @@ int run_blocking(sbv_ctx* ctx, const double* Z, const void* X, int dtype, const 
   centroid_kernel<<<grid_for(k_eff * d, 128, ctx->num_sms), 128, 0, s>>>(Z, d, ptr, pts, k_eff,
                                                                          nullptr, centres);
   SBV_LAUNCH_CHECK(ctx, "centroid_kernel");
+  *bc_eff = k_eff;
+  if (!rank) {   // anchored blocking: the caller orders the blocks
+    SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    return SBV_OK;
+  }
   // random block order: full Fisher-Yates shuffle from the same stream
   std::vector<int32_t> perm(k_eff), rk(k_eff);
   for (int64_t j = 0; j < k_eff; ++j) perm[j] = (int32_t)j;
@@ -645,6 +654,52 @@ int run_blocking(sbv_ctx* ctx, const double* Z, const void* X, int dtype, const 
                                     cudaMemcpyHostToDevice, s));
   SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
   *bc_eff = k_eff;
+  return SBV_OK;
+}
+
+// Slab of every point (Alg. 2) on its own: the routing step of a distributed
+// blocking.
+int run_slabs(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int d, const double* h_beta,
+              int P, int32_t* slab, cudaStream_t s) {
+  int dmax = 0;
+  for (int t = 1; t < d; ++t)
+    if (1.0 / h_beta[t] > 1.0 / h_beta[dmax]) dmax = t;
+  if (n == 0) return SBV_OK;
+  const int g = grid_for(n, 256, ctx->num_sms);
+  if (dtype == SBV_F64)
+    slab_kernel<double><<<g, 256, 0, s>>>((const double*)X, n, d, dmax, P, slab);
+  else
+    slab_kernel<float><<<g, 256, 0, s>>>((const float*)X, n, d, dmax, P, slab);
+  SBV_LAUNCH_CHECK(ctx, "slab_kernel");
+  return SBV_OK;
+}
+
+// Replay of the random choices of a partitioned blocking from the slab sizes
+// alone (the draws depend on nothing else): anchors per slab and their
+// positions, then, given the number of non-empty blocks, the block order.
+int rac_plan(uint64_t seed, int P, const int64_t* counts, int64_t bc, int64_t* quota,
+             int64_t* pos, int64_t k_eff, int32_t* rank) {
+  std::vector<int64_t> cnt(counts, counts + P);
+  const std::vector<int64_t> kq = slab_quota(cnt, bc);
+  SplitMix64 rng(seed);
+  int64_t o = 0;
+  for (int q = 0; q < P; ++q) {
+    if (quota) quota[q] = kq[q];
+    if (kq[q] == 0) continue;
+    std::vector<int64_t> tmp((size_t)kq[q]);
+    partial_shuffle(cnt[q], kq[q], rng, tmp.data());
+    if (pos) std::copy(tmp.begin(), tmp.end(), pos + o);
+    o += kq[q];
+  }
+  if (rank) {
+    std::vector<int32_t> perm((size_t)k_eff);
+    for (int64_t j = 0; j < k_eff; ++j) perm[j] = (int32_t)j;
+    for (int64_t j = 0; j + 1 < k_eff; ++j) {
+      const int64_t r = j + (int64_t)rng.below((uint64_t)(k_eff - j));
+      std::swap(perm[j], perm[r]);
+    }
+    for (int64_t r = 0; r < k_eff; ++r) rank[perm[r]] = (int32_t)r;
+  }
   return SBV_OK;
 }
 

@@ -989,4 +989,24 @@ int run_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t
   return SBV_OK;
 }
 
+// Matern correlation at squared scaled distances d2 through the FP64 paths'
+// arithmetic: r = sqrt(d2), then the closed form or the K_nu quadrature.
+__global__ void __launch_bounds__(256) matern_fp64_eval_kernel(const double* d2, int64_t n,
+                                                               int nu2, double* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = matern_fp64(sqrt(d2[i]), nu2);
+}
+
+int run_matern(sbv_ctx* ctx, int precision, int nu2, const double* d2, int64_t n, double* out,
+               cudaStream_t s) {
+  if (precision != SBV_PREC_FP64) return run_matern_df(ctx, nu2, d2, n, out, s);
+  if (n == 0) return SBV_OK;
+  const int64_t want = (n + 255) / 256;
+  const int grid = (int)std::min<int64_t>(want, (int64_t)ctx->num_sms * 8);
+  matern_fp64_eval_kernel<<<grid, 256, 0, s>>>(d2, n, nu2, out);
+  SBV_CUDA_TRY(ctx, cudaGetLastError());
+  return SBV_OK;
+}
+
 }  // namespace sbv

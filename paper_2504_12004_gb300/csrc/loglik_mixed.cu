@@ -1078,6 +1078,37 @@ static int upload_df_consts(sbv_ctx* ctx) {
   return SBV_OK;
 }
 
+// Matern correlation at squared scaled distances d2 through the covariance
+// arithmetic of the mixed kernel (stage 2): double-float square root,
+// exponential and closed-form polynomial, the input split into a float pair.
+__global__ void __launch_bounds__(256) matern_df_kernel(const double* d2, int64_t n, int nu2,
+                                                        double* out) {
+  __shared__ float tab_h[256], tab_l[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    tab_h[i] = c_df.tab_h[i];
+    tab_l[i] = c_df.tab_l[i];
+  }
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const df s = df_from_double(d2[i]);
+    const df r = df_sqrt(s);
+    out[i] = df_to_double(df_matern(r, s, nu2, c_df, tab_h, tab_l));
+  }
+}
+
+int run_matern_df(sbv_ctx* ctx, int nu2, const double* d2, int64_t n, double* out,
+                  cudaStream_t s) {
+  int st = upload_df_consts(ctx);
+  if (st) return st;
+  if (n == 0) return SBV_OK;
+  const int64_t want = (n + 255) / 256;
+  const int grid = (int)std::min<int64_t>(want, (int64_t)ctx->num_sms * 8);
+  matern_df_kernel<<<grid, 256, 0, s>>>(d2, n, nu2, out);
+  SBV_CUDA_TRY(ctx, cudaGetLastError());
+  return SBV_OK;
+}
+
 template <int THREADS, bool TC, bool PRED, bool GA>
 static int occ(sbv_ctx* ctx, size_t bytes, int* out) {
   SBV_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(

@@ -5,6 +5,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "sbv_internal.cuh"
 
 namespace sbv {
@@ -167,6 +170,62 @@ extern "C" int sbv_blocking(sbv_ctx* ctx, const void* X, int dtype, int64_t n, i
                             int32_t* rank, double* centres, int64_t* bc_eff, void* stream) {
   return sbv_blocking_partitioned(ctx, X, dtype, n, d, beta_scale, bc, kmeans_iters, seed, 1,
                                   blk, ptr, pts, rank, centres, bc_eff, stream);
+}
+
+extern "C" int sbv_slabs(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_t d,
+                         const double* beta_scale, int32_t partitions, int32_t* slab,
+                         void* stream) {
+  if (ctx && n == 0) return SBV_OK;
+  int st = check_common(ctx, X, dtype, n, d);
+  if (st) return st;
+  if ((st = check_beta(ctx, beta_scale, d, "beta_scale"))) return st;
+  if (partitions < 1) return fail(ctx, SBV_EINVAL, "partitions=%d must be >= 1", partitions);
+  if (!slab) return fail(ctx, SBV_EINVAL, "null output pointer");
+  return run_slabs(ctx, X, dtype, n, d, beta_scale, partitions, slab, (cudaStream_t)stream);
+}
+
+extern "C" int sbv_rac_plan(uint64_t seed, int32_t partitions, const int64_t* slab_counts,
+                            int64_t bc, int64_t* quota, int64_t* anchor_pos, int64_t bc_eff,
+                            int32_t* rank) {
+  if (partitions < 1 || !slab_counts) return SBV_EINVAL;
+  int64_t n = 0;
+  for (int q = 0; q < partitions; ++q) {
+    if (slab_counts[q] < 0) return SBV_EINVAL;
+    n += slab_counts[q];
+  }
+  if (n < 1 || bc < 1 || bc > n || (int64_t)partitions > bc) return SBV_EINVAL;
+  if (rank && (bc_eff < 1 || bc_eff > bc)) return SBV_EINVAL;
+  return rac_plan(seed, partitions, slab_counts, bc, quota, anchor_pos, rank ? bc_eff : 0, rank);
+}
+
+extern "C" int sbv_blocking_anchored(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int32_t d,
+                                     const double* beta_scale, const int64_t* anchors, int64_t k,
+                                     int32_t kmeans_iters, int32_t* blk, int64_t* ptr,
+                                     int32_t* pts, double* centres, int64_t* bc_eff,
+                                     void* stream) {
+  int st = check_common(ctx, X, dtype, n, d);
+  if (st) return st;
+  if ((st = check_beta(ctx, beta_scale, d, "beta_scale"))) return st;
+  if (k < 1 || k > n) return fail(ctx, SBV_EINVAL, "k=%lld outside [1, n]", (long long)k);
+  if (kmeans_iters < 0) return fail(ctx, SBV_EINVAL, "kmeans_iters must be >= 0");
+  if (!anchors || !blk || !ptr || !pts || !centres || !bc_eff)
+    return fail(ctx, SBV_EINVAL, "null pointer argument");
+  {
+    std::vector<int64_t> a(anchors, anchors + k);
+    std::sort(a.begin(), a.end());
+    for (int64_t j = 0; j < k; ++j) {
+      if (a[j] < 0 || a[j] >= n)
+        return fail(ctx, SBV_EINVAL, "anchor %lld outside [0, n)", (long long)a[j]);
+      if (j > 0 && a[j] == a[j - 1])
+        return fail(ctx, SBV_EINVAL, "anchor %lld repeated", (long long)a[j]);
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  double* Z = (double*)ws_get(ctx, WS_Z, (size_t)n * d * sizeof(double), &st);
+  if (!Z) return st;
+  if ((st = scale_points(ctx, X, dtype, n, d, nullptr, beta_scale, Z, s))) return st;
+  return run_blocking(ctx, Z, X, dtype, beta_scale, n, d, k, kmeans_iters, 0, 1, blk, ptr, pts,
+                      nullptr, centres, bc_eff, s, anchors);
 }
 
 extern "C" int sbv_set_knn_mode(sbv_ctx* ctx, int32_t mode) {
@@ -336,4 +395,35 @@ extern "C" int sbv_predict(sbv_ctx* ctx, const void* X, int dtype, const double*
   return predict_common(ctx, X, dtype, y, n, d, Xtest, ntest, beta_scale, m_pred, theta, nu2,
                         precision, nullptr, nullptr, nullptr, nullptr, 0, mean, var, var_latent,
                         nbr, stream);
+}
+
+extern "C" int sbv_matern(sbv_ctx* ctx, int32_t precision, int32_t nu2, const double* d2,
+                          int64_t n, double* out, void* stream) {
+  if (!ctx) return SBV_EINVAL;
+  if (n < 0) return fail(ctx, SBV_EINVAL, "n=%lld is negative", (long long)n);
+  if (n > 0 && (!d2 || !out)) return fail(ctx, SBV_EINVAL, "null pointer argument");
+  if (precision != SBV_PREC_FP64 && precision != SBV_PREC_MIXED &&
+      precision != SBV_PREC_MIXED_BF16)
+    return fail(ctx, SBV_EINVAL, "precision=%d unknown", precision);
+  if (!nu_ok_prec(nu2, precision))
+    return fail(ctx, SBV_EINVAL, "nu2=%d: FP64 takes 1..%d, the mixed precisions {1,3,5,7}", nu2,
+                SBV_MAX_NU2);
+  SBV_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  return run_matern(ctx, precision, nu2, d2, n, out, (cudaStream_t)stream);
+}
+
+extern "C" int sbv_simulate(sbv_ctx* ctx, const double* mean, const double* var, int64_t ntest,
+                            int32_t ndraws, uint64_t seed, uint64_t index_base,
+                            double* sample_mean,
+                            double* sample_var, double* ci_lo, double* ci_hi, double* draws,
+                            void* stream) {
+  if (!ctx) return SBV_EINVAL;
+  if (ntest < 0) return fail(ctx, SBV_EINVAL, "ntest=%lld is negative", (long long)ntest);
+  if (ndraws < 2 || ndraws > SBV_MAX_DRAWS)
+    return fail(ctx, SBV_EINVAL, "ndraws=%d outside [2, %d]", ndraws, SBV_MAX_DRAWS);
+  if (ntest > 0 && (!mean || !var || !sample_mean || !sample_var || !ci_lo || !ci_hi))
+    return fail(ctx, SBV_EINVAL, "null pointer argument");
+  SBV_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  return run_simulate(ctx, mean, var, ntest, ndraws, seed, index_base, sample_mean, sample_var, ci_lo, ci_hi,
+                      draws, (cudaStream_t)stream);
 }

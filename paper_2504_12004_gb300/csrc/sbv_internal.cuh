@@ -118,8 +118,12 @@ int scale_points(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int d,
 int run_blocking(sbv_ctx* ctx, const double* Z, const void* X, int dtype, const double* h_beta,
                  int64_t n, int d, int64_t bc, int kmeans_iters, uint64_t seed, int partitions,
                  int32_t* blk, int64_t* ptr, int32_t* pts, int32_t* rank, double* centres,
-                 int64_t* bc_eff, cudaStream_t s);
+                 int64_t* bc_eff, cudaStream_t s, const int64_t* h_anchors = nullptr);
 // kNN
+int run_slabs(sbv_ctx* ctx, const void* X, int dtype, int64_t n, int d, const double* h_beta,
+              int P, int32_t* slab, cudaStream_t s);
+int rac_plan(uint64_t seed, int P, const int64_t* counts, int64_t bc, int64_t* quota,
+             int64_t* pos, int64_t k_eff, int32_t* rank);
 int run_knn(sbv_ctx* ctx, const double* Z, int64_t n, int d, const int64_t* ptr,
             const int32_t* pts, const int32_t* rank, const double* centres,
             int64_t bc, int m, int32_t* nbr, int32_t* cnt, cudaStream_t s);
@@ -142,6 +146,15 @@ int run_loglik_grad(sbv_ctx* ctx, const void* X, int dtype, const double* y, int
                     const int32_t* cnt, int64_t bc, int m, int nmax_hint, const double* h_theta,
                     int B, int nu2, double* ll, double* grad, double* terms, double* gterms,
                     int32_t* status, cudaStream_t s);
+// covariance function alone (FP64 or double-float arithmetic of the likelihood)
+int run_matern(sbv_ctx* ctx, int precision, int nu2, const double* d2, int64_t n, double* out,
+               cudaStream_t s);
+int run_matern_df(sbv_ctx* ctx, int nu2, const double* d2, int64_t n, double* out,
+                  cudaStream_t s);
+// conditional simulation from predictive means and variances
+int run_simulate(sbv_ctx* ctx, const double* mean, const double* var, int64_t nt, int ndraws,
+                 uint64_t seed, uint64_t base, double* mu, double* var_s, double* lo, double* hi,
+                 double* draws, cudaStream_t s);
 int run_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n,
                 int d, const void* Xt, int64_t nt, const int32_t* nbr, int m,
                 const double* h_theta, int nu2, int precision, double* mean,
