@@ -5,11 +5,14 @@ the sine-sum family, 20,000 K-means blocks (~50 points), m = 120 neighbours,
 Matern-5/2, one theta per evaluation (the shape of the paper's Sec. 8
 performance study: d = 10 on [0,1]^10).  Blocking and kNN run once, untimed
 (reported separately); a step is one full log-likelihood evaluation: gather,
-covariance, factorisation, refinement, block terms and the deterministic sum.
+covariance, FP32 factor of the neighbour covariance, extended-precision
+residual, corrected Schur complement, LDL^T, block terms and the
+deterministic sum.
 
 The headline is the mixed path (SBV_PREC_MIXED); the FP64 path and the
-tensor-core split-BF16 variant are timed beside it on the same structure,
-with |l_path - l_fp64| / n.
+variant with the residual's products on the tensor cores (SBV_PREC_MIXED_BF16)
+are timed beside it on the same structure, each at its autotuned launch
+shape, with |l_path - l_fp64| / n.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -403,8 +406,9 @@ def main():
     # and replayed with the parameter row as its only input
     tuned = None
     if not args.no_autotune:
-        tuned = ctx.sbv_autotune(X, y, ptr, pts, nbr, cnt, th, nu2=w["nu2"],
-                                 precision=args.precision, nmax=nmax)
+        ctx.sbv_autotune(X, y, ptr, pts, nbr, cnt, th, nu2=w["nu2"],
+                         precision=args.precision, nmax=nmax)
+        tuned = ctx.sbv_tuned_shape(args.precision, nmax, X.shape[1])
     graph = None
     if args.launch == "graph":
         graph = ctx.sbv_loglik_graph_create(X, y, ptr, pts, nbr, cnt, B=1, nu2=w["nu2"],
@@ -471,6 +475,9 @@ def main():
             if prec in paths:
                 continue
             k = max(3, args.steps // 4)
+            if not args.no_autotune:   # each path at its own fastest launch shape
+                ctx.sbv_autotune(X, y, ptr, pts, nbr, cnt, th, nu2=w["nu2"], precision=prec,
+                                 nmax=nmax)
             t_tot, t_calls, t_ll = timed(prec, k, 1)
             paths[prec] = {"evals_per_s": k / (t_tot / 1000.0), "ms_per_call": statistics.median(t_calls),
                            "ll": float(t_ll[0].item())}
@@ -580,11 +587,15 @@ def main():
             "paths": paths,
             "preprocess_s": {"blocking": t_block, "knn": t_knn},
             "algorithmic_flops_per_eval": flops,
-            # graph replay: block kernel + reduction per step; direct call:
-            # also the float-pair split of the points
-            "gpu_launches": (2 if graph is not None else 3) * args.steps,
+            # graph replay: block kernel (+ in the mixed modes the FP64 kernel
+            # over the items it handed over, which returns at once when there
+            # are none) + reduction per step; a direct call in the mixed modes
+            # also splits the points into float pairs
+            "gpu_launches": ((2 if args.precision == "fp64" else 3)
+                             + (0 if graph is not None or args.precision == "fp64" else 1)) * args.steps,
             "launch": {"mode": args.launch,
-                       "shape": {"threads": tuned[0], "ctas_per_sm": tuned[1]} if tuned else None},
+                       "shape": {"threads": tuned[0], "ctas_per_sm": tuned[1],
+                                 "rhs_per_column_block": tuned[2]} if tuned else None},
             "clocks": clocks,
             "roofline": roof,
             "cpu_baseline": cpu,

@@ -446,18 +446,29 @@ void sbv_loglik_graph_destroy(sbv_graph* graph);
 /*
  * sbv_autotune -- time the launch shapes of the block kernel for one
  * structure (FP64: 1-4 resident CTAs of 256 threads per SM; mixed modes:
- * 256 threads with 2 or 1 CTAs per SM, or 512 threads with 1) on the given
+ * 256 threads with 2 or 1 CTAs per SM, or 512 threads with 1, each with a
+ * column-block width of 16, 32 or 64 right-hand sides for the residual and
+ * the conditional system, capped by the shared memory it has) on the given
  * arguments (one warm-up and two timed evaluations each, synchronising
  * `stream`) and record the fastest on the context; later sbv_loglik calls and
  * graphs with the same (precision, largest block size, d) use it.
- * *threads and *ctas_per_sm (host, may be NULL) receive the choice.
- * Errors: as sbv_loglik.
+ * *threads and *ctas_per_sm (host, may be NULL) receive the choice;
+ * sbv_tuned_shape reads back the whole record.  Errors: as sbv_loglik.
  */
 int sbv_autotune(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n,
                  int32_t d, const int64_t* ptr, const int32_t* pts, const int32_t* nbr,
                  const int32_t* cnt, int64_t bc, int32_t m, int32_t nmax,
                  const double* theta, int32_t B, int32_t nu2, int32_t precision,
                  int32_t* threads, int32_t* ctas_per_sm, void* stream);
+
+/*
+ * sbv_tuned_shape -- the autotuner's record for (precision, nmax = largest
+ * m_i + bs_i, d): *threads, *ctas_per_sm and *tile (host, each may be NULL;
+ * tile = right-hand sides per column block in the mixed modes, 0 for FP64).
+ * Returns SBV_EINVAL when no record exists.
+ */
+int sbv_tuned_shape(sbv_ctx* ctx, int32_t precision, int32_t nmax, int32_t d, int32_t* threads,
+                    int32_t* ctas_per_sm, int32_t* tile);
 
 /*
  * sbv_peak_probe -- measured FMA rate of the CUDA cores, for roofline

@@ -95,6 +95,8 @@ SIGNATURES = {
     "sbv_autotune": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64, _I32, _I32,
                                _P, _I32, _I32, _I32, C.POINTER(_I32), C.POINTER(_I32), _P]),
     "sbv_peak_probe": (C.c_int, [_P, _I32, C.POINTER(_D)]),
+    "sbv_tuned_shape": (C.c_int, [_P, _I32, _I32, _I32, C.POINTER(_I32), C.POINTER(_I32),
+                                  C.POINTER(_I32)]),
     "sbv_simulate": (C.c_int, [_P, _P, _P, _I64, _I32, _U64, _U64, _P, _P, _P, _P, _P, _P]),
     "sbv_matern": (C.c_int, [_P, _I32, _I32, _P, _I64, _P, _P]),
     "sbv_slabs": (C.c_int, [_P, _P, C.c_int, _I64, _I32, _P, _I32, _P, _P]),
@@ -369,6 +371,14 @@ class Context:
                                    C.byref(t), C.byref(c), _stream(stream))
         self._check(rc)
         return t.value, c.value
+
+    def sbv_tuned_shape(self, precision, nmax: int, d: int):
+        """The autotuner's record: (threads, ctas_per_sm, tile)."""
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        t, c, w = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+        self._check(self.lib.sbv_tuned_shape(self.h, prec, nmax, d, C.byref(t), C.byref(c),
+                                             C.byref(w)))
+        return t.value, c.value, w.value
 
     def sbv_peak_probe(self, kind: str = "fp64") -> float:
         """Measured FMA rate of the CUDA cores in TFLOP/s (kind "fp64" or "fp32")."""

@@ -252,9 +252,13 @@ extern "C" int sbv_autotune(sbv_ctx* ctx, const void* X, int dtype, const double
   if (precision == SBV_PREC_FP64) {
     for (int k = 1; k <= 4; ++k) shapes.push_back({256, k});
   } else {
-    shapes.push_back({256, 2});
-    shapes.push_back({256, 1});
-    shapes.push_back({512, 1});
+    // launch shape x right-hand sides per column block of the residual and
+    // the conditional system (the tile size the mixed kernel leaves open)
+    for (int tile : {16, 32, 64}) {
+      shapes.push_back({256, 2, tile});
+      shapes.push_back({256, 1, tile});
+      shapes.push_back({512, 1, tile});
+    }
   }
   double* ll = (double*)ws_get(ctx, WS_TUNE, (size_t)B * sizeof(double), &st);
   if (!ll) return st;
@@ -292,7 +296,7 @@ extern "C" int sbv_autotune(sbv_ctx* ctx, const void* X, int dtype, const double
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st) return st;
-  TunedShape rec = {precision, 0, nmax, d, pick.threads, pick.per_sm};
+  TunedShape rec = {precision, 0, nmax, d, pick.threads, pick.per_sm, pick.tile};
   bool replaced = false;
   for (auto& t : ctx->tuned)
     if (t.precision == rec.precision && t.pred == rec.pred && t.ncap == rec.ncap && t.d == rec.d) {
@@ -303,4 +307,18 @@ extern "C" int sbv_autotune(sbv_ctx* ctx, const void* X, int dtype, const double
   if (threads) *threads = pick.threads;
   if (ctas_per_sm) *ctas_per_sm = pick.per_sm;
   return sbv_sync_status(ctx, stream);
+}
+
+extern "C" int sbv_tuned_shape(sbv_ctx* ctx, int32_t precision, int32_t nmax, int32_t d,
+                               int32_t* threads, int32_t* ctas_per_sm, int32_t* tile) {
+  if (!ctx) return SBV_EINVAL;
+  for (const auto& t : ctx->tuned)
+    if (t.precision == precision && t.pred == 0 && t.ncap == nmax && t.d == d) {
+      if (threads) *threads = t.threads;
+      if (ctas_per_sm) *ctas_per_sm = t.per_sm;
+      if (tile) *tile = t.tile;
+      return SBV_OK;
+    }
+  return fail(ctx, SBV_EINVAL, "no autotuning record for precision %d, nmax %d, d %d", precision,
+              nmax, d);
 }

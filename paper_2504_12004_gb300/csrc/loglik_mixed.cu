@@ -12,29 +12,30 @@
 //     matrix goes to a per-CTA global slice, the float heads of Sigma_JJ to
 //     the packed triangle A and those of Sigma_{J,B'} = [Sigma_JB, y_J] to
 //     the right-hand-side block X (one row per member of B');
-//  3. POTRF of Sigma_JJ in FP32 (Alg. 5, l.7), blocked right-looking with
+//  3. POTRF of Sigma_JJ in FP32 (the first POTRF of Alg. 5), blocked right-looking with
 //     16-column panels; each diagonal tile is formed as (double-float
 //     original) - (FP32 updates) and factored by one warp, looked ahead
 //     during the trailing update; the rows of X ride along as extra rows, so
-//     they leave as L^{-1} Sigma_{J,B'} (the TRSM and TRSV of Alg. 5, l.8-9);
+//     they leave as L^{-1} Sigma_{J,B'} (the TRSM and TRSV of Alg. 5);
 //  4. the diagonal tiles are replaced by their inverses;
 //  5. backward substitution: X <- Sigma~_JJ^{-1} Sigma_{J,B'} (FP32), i.e.
 //     the kriging weights of B and x_J = Sigma~^{-1} y_J;
 //  6. residual R = Sigma_{J,B'} - Sigma_JJ X from the global copy of Sigma,
-//     exact to about 2^-38 of the products: for mb <= 128 on the tensor
-//     cores (X held on a 24-bit fixed-point grid per column and split into
-//     three BF16 digits, Sigma_JJ into five, the digit products of equal
-//     weight summed exactly in five FP32 TMEM accumulators), otherwise on the
-//     CUDA cores with exact fixed-point product heads;
-//  7. the conditional system of Alg. 5 (GEMM, GEMV and the Schur
-//     subtraction, l.10-13) by the exact identity
+//     exact to about 2^-38 of the products: in SBV_PREC_MIXED_BF16 with
+//     mb <= 128 on the tensor cores (X held on a 24-bit fixed-point grid per
+//     column and split into three BF16 digits, Sigma_JJ into five, the digit
+//     products of equal weight summed exactly in five FP32 TMEM
+//     accumulators, all right-hand sides of a pass in one MMA), otherwise on
+//     the CUDA cores with exact fixed-point product heads;
+//  7. the conditional system of Alg. 5 (its GEMM, GEMV and Schur
+//     subtraction) by the exact identity
 //        S' = Sigma_{B'B'} - Sigma_{B'J} X - X^T R - R^T Sigma_JJ^{-1} R,
 //     whose last term, taken with the FP32 factor as (L^{-1} R)^T (L^{-1} R),
 //     is the only approximation: the error is third order in the error of
 //     X.  S' holds Sigma^new (bs x bs) and, in its bordered row, y_B - mu^new;
 //  8. LDL^T of Sigma^new in double-float (one column per step), bordered
-//     by y_B - mu^new (POTRF and TRSV of Alg. 5, l.15-16); the log-
-//     determinant and the quadratic form (l.17-19) are summed in FP64:
+//     by y_B - mu^new (the second POTRF and the TRSV of Alg. 5); the log-
+//     determinant and the quadratic form are summed in FP64:
 //        l_i = -1/2 [bs log 2pi + sum_t log d_t + sum_t z_t^2 / d_t].
 // Prediction is the same pipeline with B = {test point} and no y_B: the
 // mean is mu^new and the variance Sigma^new (Sec. 5.5).
@@ -110,6 +111,11 @@ loglik_mixed_kernel(MixedArgs P) {
   __shared__ float s_grid;
   __shared__ __align__(16) float s_col[2 * NB];   // column broadcast of the tile factorisation
   const DfConsts& C = c_df;
+  // tensor-core residual: right-hand sides per MMA pass and TMEM columns
+  // (five accumulator groups of MX_NP columns; two CTAs of 256 threads or one
+  // of 512 share an SM's 512 columns)
+  constexpr int MX_NP = THREADS >= 512 ? 96 : 48;
+  constexpr uint32_t MX_TMEM_COLS = THREADS >= 512 ? 512u : 256u;
   const int d = a.d, cap = lay.ncap, PS = lay.pstride;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const unsigned int total = PRED ? (unsigned int)P.nt : (unsigned int)(a.bc * a.B);
@@ -120,7 +126,7 @@ loglik_mixed_kernel(MixedArgs P) {
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t mma_bar;
   __shared__ int s_timeout;
-  if (TC && warp == 0) umma::tmem_alloc(&s_tmem, 128);
+  if (TC && warp == 0) umma::tmem_alloc(&s_tmem, MX_TMEM_COLS);
   if (tid == 0) {
     if (TC) umma::mbar_init(&mma_bar, 1);
     s_timeout = 0;
@@ -604,8 +610,6 @@ loglik_mixed_kernel(MixedArgs P) {
     float* Rb = (float*)(smem + lay.off_u);      // residual block, then L^{-1} of it
     float* colC = (float*)(smem + lay.off_cc);   // C_r per right-hand side (CUDA-core residual)
     float* colX = colC + lay.ncap + 2;           // grid unit of X^ per right-hand side
-    unsigned char* Ab = smem + lay.off_sch;      // five BF16 digit tiles of Sigma_JJ (tensor cores)
-    unsigned char* Bb = Ab + 5 * 4096;           // three BF16 digit tiles of X^ (tensor cores)
     float* Qg = Rg;                              // L^{-1} R for every column, global
     const bool tc = TC && mb <= 128;
     // X <- X^ on a 24-bit fixed-point grid per column (unit 2^(ex - 24),
@@ -636,31 +640,36 @@ loglik_mixed_kernel(MixedArgs P) {
     int eA;
     frexpf((float)(th.sigma2 + th.tau2) * 1.0001f, &eA);
     __syncthreads();
-    constexpr int W = 16;
-    for (int cb = 0; cb < nr; cb += W) {
-      const int nc = min(W, nr - cb);
-      // 6a. Rb[c][k] = Sigma_{J,B'}[k][cb+c] - sum_k' Sigma_JJ[k][k'] X[cb+c][k']
-      if (tc) {
-        // Tensor cores, K-steps of 16: every step writes the digit tiles of
-        // Sigma_JJ (128 x 16, rows past mb zero) and of X^ (16 x 16) into
-        // shared memory in the K-major core-matrix layout, then one thread
-        // issues the 12 digit products (s, t) with s + t <= 6 as
-        // 128 x 16 x 16 BF16 MMAs into TMEM group g = s + t - 2.  With
-        // |a_1|, |b_1| <= 256 and the other digits <= 128, every group's
-        // sum over K <= 128 stays below 2^24 (integers): exact in FP32.
-        const int nks = (mb + 15) >> 4;
-        const int am = tid >> 1, ak = (tid & 1) * 8;   // A digits: row am, k ak..ak+7
-        float2 sv[8];
-        auto load_sv = [&](int ks) {
+    if (tc) {
+      // ---- 6t. tensor-core residual of all right-hand sides, MX_NP columns
+      // per pass: R[r][k] = Sigma_{J,B'}[k][r] - sum_k' Sigma_JJ[k][k'] X[r][k']
+      // into the global slice (column r at Rg + r xs).  Every K-step of 16
+      // writes the digit tiles of Sigma_JJ (128 x 16, rows past mb zero) and
+      // of X^ (MX_NP x 16) into shared memory in the K-major core-matrix
+      // layout, then one thread issues the 12 digit products (s, t) with
+      // s + t <= 6 as 128 x N x 16 BF16 MMAs into TMEM group g = s + t - 2
+      // (columns g MX_NP ..).  With |a_1|, |b_1| <= 256 and the other digits
+      // <= 192 (Sigma) or 128 (X^), every group's sum over K <= 128 stays
+      // below 2^24 (integers): exact in FP32.
+      unsigned char* Ab = smem + lay.off_sch;      // five BF16 digit tiles of Sigma_JJ
+      unsigned char* Bb = Ab + 5 * 4096;           // three BF16 digit tiles of X^
+      constexpr uint32_t BT = MX_NP * 32;          // bytes of one X^ digit tile
+      const int nks = (mb + 15) >> 4;
+      const int am = tid >> 1, ak = (tid & 1) * 8;   // A digits: row am, k ak..ak+7
+      const float sc8 = ldexpf(1.0f, 8 - eA);
+      float2 sv[8];
+      auto load_sv = [&](int ks) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int kk = ks * 16 + ak + j;
-            sv[j] = (tid < 256 && am < mb && kk < mb) ? S[(size_t)kk * N + am]
-                                                      : make_float2(0.0f, 0.0f);
-          }
-        };
+        for (int j = 0; j < 8; ++j) {
+          const int kk = ks * 16 + ak + j;
+          sv[j] = (tid < 256 && am < mb && kk < mb) ? S[(size_t)kk * N + am]
+                                                    : make_float2(0.0f, 0.0f);
+        }
+      };
+      for (int pb = 0; pb < nr; pb += MX_NP) {
+        const int npc = min(MX_NP, nr - pb);
+        const int nn = (npc + 15) & ~15;   // MMA N
         load_sv(0);
-        const float sc8 = ldexpf(1.0f, 8 - eA);
         for (int ks = 0; ks < nks; ++ks) {
           if (ks > 0) {   // the previous step's MMAs have read the digit tiles
             const bool ok = umma::mbar_wait(&mma_bar, mma_phase, 1u << 24);
@@ -668,16 +677,16 @@ loglik_mixed_kernel(MixedArgs P) {
             if (!ok) s_timeout = 1;
           }
           if (tid < 256) {
-            // five digits of 8 entries of Sigma_JJ, packed two BF16 per word
+            // five digits of 8 entries of Sigma_JJ, packed two BF16 per word:
+            // the float head gives the first three digits exactly (|t| < 256,
+            // every step an exact power-of-two scaling or subtraction); the
+            // tail joins before the fourth
             uint32_t dg[5][4];
 #pragma unroll
             for (int j = 0; j < 8; j += 2) {
               float dv[2][5];
 #pragma unroll
               for (int h = 0; h < 2; ++h) {
-                // the float head gives the first three digits exactly (|t| < 256,
-                // every step an exact power-of-two scaling or subtraction); the
-                // tail joins before the fourth
                 float t = sv[j + h].x * sc8;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
@@ -700,38 +709,38 @@ loglik_mixed_kernel(MixedArgs P) {
 #pragma unroll
             for (int q = 0; q < 5; ++q)
               *(uint4*)(Ab + q * 4096 + off) = make_uint4(dg[q][0], dg[q][1], dg[q][2], dg[q][3]);
-            if (tid < 32) {
-              // three digits of 8 entries of X^ (row n = column cb + n of X)
-              const int n = tid >> 1;
-              const int r = cb + n;
-              uint32_t bd[3][4];
-              const float iu = r < nr ? 1.0f / colX[r] : 0.0f;   // a power of two
+          }
+          if (tid < 2 * nn) {
+            // three digits of 8 entries of X^ (row n = right-hand side pb + n)
+            const int n = tid >> 1, bk = (tid & 1) * 8;
+            const int r = pb + n;
+            uint32_t bd[3][4];
+            const float iu = n < npc ? 1.0f / colX[r] : 0.0f;   // a power of two
 #pragma unroll
-              for (int j = 0; j < 8; j += 2) {
-                float bv[2][3];
+            for (int j = 0; j < 8; j += 2) {
+              float bv[2][3];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                  const int kk = ks * 16 + ak + j + h;
-                  // integer T = X^ / unit, |T| < 2^24: exact in FP32
-                  const float T = (r < nr && kk < mb) ? Xr[(size_t)r * xs + kk] * iu : 0.0f;
-                  const float b1 = rintf(T * (1.0f / 65536.0f));
-                  const float r1 = __fsub_rn(T, b1 * 65536.0f);
-                  const float b2 = rintf(r1 * (1.0f / 256.0f));
-                  bv[h][0] = b1;
-                  bv[h][1] = b2;
-                  bv[h][2] = __fsub_rn(r1, b2 * 256.0f);
-                }
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                  const __nv_bfloat162 p2 = __floats2bfloat162_rn(bv[0][q], bv[1][q]);
-                  bd[q][j >> 1] = *(const uint32_t*)&p2;
-                }
+              for (int h = 0; h < 2; ++h) {
+                const int kk = ks * 16 + bk + j + h;
+                // integer T = X^ / unit, |T| < 2^24: exact in FP32
+                const float T = (n < npc && kk < mb) ? Xr[(size_t)r * xs + kk] * iu : 0.0f;
+                const float b1 = rintf(T * (1.0f / 65536.0f));
+                const float r1 = __fsub_rn(T, b1 * 65536.0f);
+                const float b2 = rintf(r1 * (1.0f / 256.0f));
+                bv[h][0] = b1;
+                bv[h][1] = b2;
+                bv[h][2] = __fsub_rn(r1, b2 * 256.0f);
               }
-              const uint32_t boff = umma::op_offset(n, ak);
 #pragma unroll
-              for (int q = 0; q < 3; ++q)
-                *(uint4*)(Bb + q * 512 + boff) = make_uint4(bd[q][0], bd[q][1], bd[q][2], bd[q][3]);
+              for (int q = 0; q < 3; ++q) {
+                const __nv_bfloat162 p2 = __floats2bfloat162_rn(bv[0][q], bv[1][q]);
+                bd[q][j >> 1] = *(const uint32_t*)&p2;
+              }
             }
+            const uint32_t boff = umma::op_offset(n, bk);
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              *(uint4*)(Bb + q * BT + boff) = make_uint4(bd[q][0], bd[q][1], bd[q][2], bd[q][3]);
           }
           if (ks + 1 < nks) load_sv(ks + 1);
           umma::fence_proxy_async();
@@ -740,7 +749,7 @@ loglik_mixed_kernel(MixedArgs P) {
           if (tid == 0 && !s_timeout) {
             umma::fence_after_sync();
             const uint32_t ab = umma::smem_u32(Ab), bb = umma::smem_u32(Bb);
-            const uint32_t idesc = umma::idesc_bf16_f32(128, 16);
+            const uint32_t idesc = umma::idesc_bf16_f32(128, nn);
             // (s, t, group) with s + t <= 6; the first product of a group at
             // the first K-step overwrites the accumulator
             const int ps[12] = {1, 1, 2, 1, 2, 3, 2, 3, 4, 3, 4, 5};
@@ -749,62 +758,85 @@ loglik_mixed_kernel(MixedArgs P) {
 #pragma unroll
             for (int q = 0; q < 12; ++q) {
               const uint64_t ad = umma::smem_desc(ab + (ps[q] - 1) * 4096, 128, 256);
-              const uint64_t bdsc = umma::smem_desc(bb + (pt[q] - 1) * 512, 128, 256);
+              const uint64_t bdsc = umma::smem_desc(bb + (pt[q] - 1) * BT, 128, 256);
               const uint32_t g = (uint32_t)(ps[q] + pt[q] - 2);
-              umma::mma_bf16(tmem_base + g * 16, ad, bdsc, idesc, (ks > 0 || !first[q]) ? 1u : 0u);
+              umma::mma_bf16(tmem_base + g * MX_NP, ad, bdsc, idesc,
+                             (ks > 0 || !first[q]) ? 1u : 0u);
             }
             umma::mma_commit(&mma_bar);
           }
         }
-        // the last step's products, then the five groups are read back by
-        // warps 0-3 (TMEM lanes = rows k) and combined in double-float:
-        // D = 2^(eA + 8) unit_r sum_g G_g 2^(-8 g)
+        // the last step's products, then the five groups are read back (TMEM
+        // lane quadrant = warp mod 4, rows k = 32 (warp mod 4) + lane; the
+        // warps of a quadrant share its 16-column chunks) and combined in
+        // double-float: D = 2^(eA + 8) unit_r sum_g G_g 2^(-8 g)
         if (nks > 0) {
           const bool ok = umma::mbar_wait(&mma_bar, mma_phase, 1u << 24);
           mma_phase ^= 1u;
           if (!ok) s_timeout = 1;
         }
         umma::fence_after_sync();
-        if (warp < 4 && nks > 0 && !s_timeout) {
-          df acc[16];
+        if (nks > 0 && !s_timeout) {
+          const int qd = warp & 3, k = 32 * qd + lane;
+          const uint32_t ta = tmem_base + ((uint32_t)(32 * qd) << 16);
+          for (int ch = warp >> 2; ch < (nn >> 4); ch += NW / 4) {
+            df acc[16];
 #pragma unroll
-          for (int c = 0; c < 16; ++c) acc[c] = {0.0f, 0.0f};
-          const uint32_t ta = tmem_base + ((uint32_t)(32 * warp) << 16);
+            for (int c = 0; c < 16; ++c) acc[c] = {0.0f, 0.0f};
 #pragma unroll
-          for (int g = 4; g >= 0; --g) {   // smallest weight first
-            float gv[16];
-            umma::tmem_ld16(ta + (uint32_t)(g * 16), gv);
-            umma::tmem_wait_ld();
-            const float wg = ldexpf(1.0f, -8 * g);
+            for (int g = 4; g >= 0; --g) {   // smallest weight first
+              float gv[16];
+              umma::tmem_ld16(ta + (uint32_t)(g * MX_NP + 16 * ch), gv);
+              umma::tmem_wait_ld();
+              const float wg = ldexpf(1.0f, -8 * g);
 #pragma unroll
-            for (int c = 0; c < 16; ++c) acc[c] = df_add_f(acc[c], gv[c] * wg);
-          }
-          const int k = 32 * warp + lane;
-          if (k < mb) {
+              for (int c = 0; c < 16; ++c) acc[c] = df_add_f(acc[c], gv[c] * wg);
+            }
+            if (k < mb) {
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-              const int r = cb + c;
-              if (c < nc) {
-                const float scl = ldexpf(colX[r], eA + 8);   // exact power of two
-                const df dd = {acc[c].h * scl, acc[c].l * scl};
-                const float2 v = r < bs ? S[(size_t)(mb + r) * N + k] : yv[k];
-                const df rv = df_sub_acc(df{v.x, v.y}, dd);
-                Rb[(size_t)c * xs + k] = __fadd_rn(rv.h, rv.l);
+              for (int c = 0; c < 16; ++c) {
+                const int n = 16 * ch + c, r = pb + n;
+                if (n < npc) {
+                  const float scl = ldexpf(colX[r], eA + 8);   // exact power of two
+                  const df dd = {acc[c].h * scl, acc[c].l * scl};
+                  const float2 v = r < bs ? S[(size_t)(mb + r) * N + k] : yv[k];
+                  const df rv = df_sub_acc(df{v.x, v.y}, dd);
+                  Rg[(size_t)r * xs + k] = __fadd_rn(rv.h, rv.l);
+                }
               }
             }
           }
         }
         umma::fence_before_sync();
+        __syncthreads();   // TMEM and the digit tiles are free for the next pass
+      }
+    }
+    // right-hand sides per column block: as many as the residual block's
+    // room holds (at most 64), split evenly
+    const int Wroom = min(64, (int)((lay.off_cc - lay.off_u) / ((size_t)xs * sizeof(float))));
+    const int Wcap = P.wcap > 0 ? min(P.wcap, Wroom) : Wroom;
+    const int nwb = (nr + Wcap - 1) / Wcap;
+    const int W = (nr + nwb - 1) / nwb;
+    for (int cb = 0; cb < nr; cb += W) {
+      const int nc = min(W, nr - cb);
+      // 6a. Rb[c][k] = Sigma_{J,B'}[k][cb+c] - sum_k' Sigma_JJ[k][k'] X[cb+c][k']
+      if (tc) {
+        // the tensor-core residual of these columns, computed above
+        for (int e = tid; e < nc * (mb4 >> 2); e += THREADS) {
+          const int c = e / (mb4 >> 2), k = (e - c * (mb4 >> 2)) * 4;
+          *(float4*)(Rb + (size_t)c * xs + k) = *(const float4*)(Rg + (size_t)(cb + c) * xs + k);
+        }
       } else {
       // CUDA cores: thread (k, c0) streams row k of Sigma_JJ itself
       // (S[kp N + k], coalesced over the warp's rows k) with the next four
       // loads in flight, and keeps eight columns' accumulators in registers;
       // no CTA barrier inside
       {
-        for (int t0 = 0; t0 < 2 * mb; t0 += THREADS) {
+        const int ngrp = (nc + 7) >> 3;   // groups of eight columns
+        for (int t0 = 0; t0 < ngrp * mb; t0 += THREADS) {
           const int tk = t0 + tid;
           // tasks whose eight columns all lie past the block do nothing
-          if (tk < 2 * mb && (tk / mb) * 8 < nc) {
+          if (tk < ngrp * mb && (tk / mb) * 8 < nc) {
             const int k = tk % mb, c0 = (tk / mb) * 8;
             float Cq[8], ahi[8];
             df atot[8];
@@ -830,17 +862,19 @@ loglik_mixed_kernel(MixedArgs P) {
                 const int kn = kp + 4 + u;
                 nx[u] = kn < mb ? sk[(size_t)kn * N] : make_float2(0.0f, 0.0f);
               }
-              // the eight columns' chains interleaved, one product each per step
+              // the eight columns' chains, four products each, X^ read as
+              // float4 (xs and kp are multiples of four)
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
+              for (int q = 0; q < 8; ++q) {
+                // columns past the block read column cb + c0 (c0 < nc: in
+                // bounds) and are discarded
+                const float4 x4 = *(const float4*)(xc + (size_t)(c0 + q < nc ? q : 0) * xs + kp);
+                const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                  // columns past the block read column cb + c0 (c0 < nc: in
-                  // bounds) and are discarded
-                  const float xq = xc[(size_t)(c0 + q < nc ? q : 0) * xs + kp + u];
-                  const float ph = __fsub_rn(__fmaf_rn(sv[u].x, xq, Cq[q]), Cq[q]);
-                  float rr = __fmaf_rn(sv[u].x, xq, -ph);
-                  rr = __fmaf_rn(sv[u].y, xq, rr);
+                for (int u = 0; u < 4; ++u) {
+                  const float ph = __fsub_rn(__fmaf_rn(sv[u].x, xv[u], Cq[q]), Cq[q]);
+                  float rr = __fmaf_rn(sv[u].x, xv[u], -ph);
+                  rr = __fmaf_rn(sv[u].y, xv[u], rr);
                   ahi[q] = __fadd_rn(ahi[q], ph);
                   alo[q] = __fadd_rn(alo[q], rr);
                 }
@@ -879,6 +913,8 @@ loglik_mixed_kernel(MixedArgs P) {
       //            - X[a] . R[r] (FP32)
       // (row a = bs is the bordered y row: Sigma_{B'J}[bs] = y_J and
       // Sigma_{B'B'}[bs][r] = y_{B,r})
+      // Sigma_{B'J}[a] X[r] in double-float; the row of Sigma comes from the
+      // global slice (L2), so each thread keeps three quads of it in flight
       {
         const int ncb = min(nc, bs - cb);   // columns of Sigma^new in this block
         const int na = nr - cb;
@@ -892,14 +928,27 @@ loglik_mixed_kernel(MixedArgs P) {
           const float* xr = Xr + (size_t)r * xs;
           const float* rr = Rb + (size_t)c * xs;
           const float2* sa = ar < bs ? S + (size_t)(mb + ar) * N : yv;
+          float2 q0[4], q1[4], q2[4];
+          auto ldq = [&](float2 (&q)[4], int k) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) q[u] = k + u < mb ? sa[k + u] : make_float2(0.0f, 0.0f);
+          };
+          ldq(q0, 0);
+          ldq(q1, 4);
+          ldq(q2, 8);
           for (int k = 0; k < mb4; k += 4) {
+            float2 sv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              sv[u] = q0[u];
+              q0[u] = q1[u];
+              q1[u] = q2[u];
+            }
+            ldq(q2, k + 12);
             const float4 x4 = *(const float4*)(xr + k);
             const float4 a4 = *(const float4*)(xa + k);
             const float4 r4 = *(const float4*)(rr + k);
             const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
-            float2 sv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) sv[u] = k + u < mb ? sa[k + u] : make_float2(0.0f, 0.0f);
 #pragma unroll
             for (int u = 0; u < 4; ++u) df_fnma_acc(e, sv[u], xv[u]);
             d1 = fmaf(a4.x, r4.x, d1);
@@ -916,16 +965,27 @@ loglik_mixed_kernel(MixedArgs P) {
       for (int kt = 0; kt < ntile; ++kt) {
         const int k0 = kt * NB, k1 = min(k0 + NB, mb), nbk = k1 - k0;
         __syncthreads();   // the previous step's (or pass A's) reads of Rb are done
-        float xo = 0.0f;
-        const int c = tid >> 4, rr = tid & 15;   // 256 threads: 16 columns x 16 tile rows
-        const bool act = tid < 256 && c < nc && rr < nbk;
-        if (act) {
-          const float* Lr = A + trp(k0 + rr, k0);
-          const float* pc = Rb + (size_t)c * xs + k0;
-          for (int r2 = 0; r2 <= rr; ++r2) xo = fmaf(Lr[r2], pc[r2], xo);
+        // diagonal tile: thread (c, rr) for columns c = tid / 16 + j THREADS / 16
+        constexpr int CPS = THREADS / 16;          // columns per sweep
+        constexpr int NSW = (64 + CPS - 1) / CPS;  // sweeps for the widest block
+        const int rr = tid & 15;
+        float xo[NSW];
+#pragma unroll
+        for (int j = 0; j < NSW; ++j) {
+          const int c = (tid >> 4) + j * CPS;
+          xo[j] = 0.0f;
+          if (c < nc && rr < nbk) {
+            const float* Lr = A + trp(k0 + rr, k0);
+            const float* pc = Rb + (size_t)c * xs + k0;
+            for (int r2 = 0; r2 <= rr; ++r2) xo[j] = fmaf(Lr[r2], pc[r2], xo[j]);
+          }
         }
         __syncthreads();
-        if (act) Rb[(size_t)c * xs + k0 + rr] = xo;
+#pragma unroll
+        for (int j = 0; j < NSW; ++j) {
+          const int c = (tid >> 4) + j * CPS;
+          if (c < nc && rr < nbk) Rb[(size_t)c * xs + k0 + rr] = xo[j];
+        }
         __syncthreads();
         const int ni4 = (mb - k1 + 3) >> 2;
         for (int t = tid; t < nc * ni4; t += THREADS) {
@@ -959,9 +1019,19 @@ loglik_mixed_kernel(MixedArgs P) {
       float d2 = 0.0f;
       const float* qa = Qg + (size_t)ar * xs;
       const float* qb = Qg + (size_t)b * xs;
+      // global (L2) reads: three quads of each row in flight
+      const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      float4 a0 = *(const float4*)qa, b0 = *(const float4*)qb;
+      float4 a1 = 4 < mb4 ? *(const float4*)(qa + 4) : z4, b1 = 4 < mb4 ? *(const float4*)(qb + 4) : z4;
+      float4 a2 = 8 < mb4 ? *(const float4*)(qa + 8) : z4, b2 = 8 < mb4 ? *(const float4*)(qb + 8) : z4;
       for (int k = 0; k < mb4; k += 4) {
-        const float4 a4 = *(const float4*)(qa + k);
-        const float4 b4 = *(const float4*)(qb + k);
+        const float4 a4 = a0, b4 = b0;
+        a0 = a1;
+        b0 = b1;
+        a1 = a2;
+        b1 = b2;
+        a2 = k + 12 < mb4 ? *(const float4*)(qa + k + 12) : z4;
+        b2 = k + 12 < mb4 ? *(const float4*)(qb + k + 12) : z4;
         d2 = fmaf(a4.x, b4.x, d2);
         d2 = fmaf(a4.y, b4.y, d2);
         d2 = fmaf(a4.z, b4.z, d2);
@@ -1003,8 +1073,9 @@ loglik_mixed_kernel(MixedArgs P) {
         const int Tn = bs - 1 - k;               // trailing matrix rows k+1 .. bs-1
         const int ntri = Tn * (Tn + 1) / 2;
         const int ntr = ntri + Tn;               // plus the bordered row's Tn entries
-        for (int l = tid; l < ntr; l += THREADS) {
-          int i, j;
+        // two entries per thread and pass, both loaded before either is
+        // stored (the step reads column k, which it does not write)
+        auto entry = [&](int l, int& i, int& j) {
           if (l < ntri) {
             int ii = (int)((sqrtf(8.0f * (float)l + 1.0f) - 1.0f) * 0.5f);
             while (ii * (ii + 1) / 2 > l) --ii;
@@ -1015,10 +1086,26 @@ loglik_mixed_kernel(MixedArgs P) {
             i = bs;
             j = k + 1 + (l - ntri);
           }
-          const float2 sik = Sf[tri0(i, k)], sjk = Sf[tri0(j, k)], sij = Sf[tri0(i, j)];
-          const df lik = df_mul(df{sik.x, sik.y}, inv);
-          const df r = df_sub_acc(df{sij.x, sij.y}, df_mul(lik, df{sjk.x, sjk.y}));
-          Sf[tri0(i, j)] = make_float2(r.h, r.l);
+        };
+        for (int l = tid; l < ntr; l += 2 * THREADS) {
+          const int l2 = l + THREADS;
+          const bool two = l2 < ntr;
+          int i0, j0, i1 = 0, j1 = 0;
+          entry(l, i0, j0);
+          if (two) entry(l2, i1, j1);
+          const float2 a0 = Sf[tri0(i0, k)], b0 = Sf[tri0(j0, k)], c0 = Sf[tri0(i0, j0)];
+          float2 a1 = a0, b1 = b0, c1 = c0;
+          if (two) {
+            a1 = Sf[tri0(i1, k)];
+            b1 = Sf[tri0(j1, k)];
+            c1 = Sf[tri0(i1, j1)];
+          }
+          const df r0 = df_sub_acc(df{c0.x, c0.y},
+                                   df_mul(df_mul(df{a0.x, a0.y}, inv), df{b0.x, b0.y}));
+          const df r1 = df_sub_acc(df{c1.x, c1.y},
+                                   df_mul(df_mul(df{a1.x, a1.y}, inv), df{b1.x, b1.y}));
+          Sf[tri0(i0, j0)] = make_float2(r0.h, r0.l);
+          if (two) Sf[tri0(i1, j1)] = make_float2(r1.h, r1.l);
         }
         __syncthreads();
       }
@@ -1054,7 +1141,7 @@ loglik_mixed_kernel(MixedArgs P) {
     if (s_timeout) umma::mbar_wait(&mma_bar, mma_phase, 1u << 24);
     umma::fence_before_sync();
     __syncthreads();
-    if (warp == 0) umma::tmem_dealloc(tmem_base, 128);
+    if (warp == 0) umma::tmem_dealloc(tmem_base, MX_TMEM_COLS);
   }
 }
 
@@ -1147,28 +1234,32 @@ int mixed_plan(sbv_ctx* ctx, int nmax, int mcap, int bcap, int d, int precision,
   const bool tc = precision == SBV_PREC_MIXED_BF16 && !pred;
   o->pred = pred;
   o->tc = tc;
-  o->lay = mixed_layout(ncap, mcap, bcap, d, tc);
+  int threads = 256, per_sm = 2, tile = 0;
+  if (ctx->force.threads) {
+    threads = ctx->force.threads;
+    per_sm = ctx->force.per_sm;
+    tile = ctx->force.tile;
+  } else {
+    for (const auto& t : ctx->tuned)
+      if (t.precision == precision && t.pred == (int)pred && t.ncap == ncap && t.d == d) {
+        threads = t.threads;
+        per_sm = t.per_sm;
+        tile = t.tile;
+      }
+  }
+  o->wcap = tile;
+  const int tc_np = threads >= 512 ? 96 : 48;   // MX_NP of the kernel variant
+  o->lay = mixed_layout(ncap, mcap, bcap, d, tc, false, tc_np);
   size_t static_smem = 0;
   if (int st0 = mixed_static_smem(ctx, &static_smem)) return st0;
   if (o->lay.bytes + static_smem > ctx->smem_optin)
-    o->lay = mixed_layout(ncap, mcap, bcap, d, tc, true);
+    o->lay = mixed_layout(ncap, mcap, bcap, d, tc, true, tc_np);
   if (o->lay.bytes + static_smem > ctx->smem_optin)
     return fail(ctx, SBV_EUNSUPPORTED,
                 "mixed path: a block with N=%d (d=%d) needs %zu bytes of shared memory", nmax, d,
                 o->lay.bytes);
   int st = mixed_prepare(ctx);   // occupancy queries need the shared-memory opt-in
   if (st) return st;
-  int threads = 256, per_sm = 2;
-  if (ctx->force.threads) {
-    threads = ctx->force.threads;
-    per_sm = ctx->force.per_sm;
-  } else {
-    for (const auto& t : ctx->tuned)
-      if (t.precision == precision && t.pred == (int)pred && t.ncap == ncap && t.d == d) {
-        threads = t.threads;
-        per_sm = t.per_sm;
-      }
-  }
   int fit = 0;
   if ((st = mixed_occupancy(ctx, threads, tc, pred, o->lay.ga, o->lay.bytes, &fit))) return st;
   if (fit < 1)
@@ -1272,6 +1363,7 @@ int mixed_enqueue(sbv_ctx* ctx, MixedArgs& P, const MixedPlan& o, cudaStream_t s
   int st = 0;
   if ((st = mixed_prepare(ctx))) return st;
   P.lay = o.lay;
+  P.wcap = o.wcap;
   if (o.pred)
     return o.threads == 512 ? launch_variant<512, false, true>(ctx, P, o.grid, s)
                             : launch_variant<256, false, true>(ctx, P, o.grid, s);

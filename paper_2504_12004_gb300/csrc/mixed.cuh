@@ -49,9 +49,9 @@ __host__ __device__ __forceinline__ int tri0(int i, int j) { return (i * (i + 1)
 //           the Schur-complement passes the region holds the bs x bs
 //           conditional system (bordered by y_B - mu) in double-float
 // With ga, A and X live in a per-CTA slice of global memory instead.
-//   union   residual phase: a block of 16 residual columns (then L^{-1} of
-//           them), two constants per right-hand side and (tensor-core
-//           residual) the BF16 digit tiles of one K-step
+//   union   residual phase: two constants per right-hand side, and a block
+//           of 16 residual columns (then L^{-1} of them) or, before it, the
+//           BF16 digit tiles of one K-step of the tensor-core residual
 // Per-CTA global memory: the double-float joint covariance (N x N, both
 // triangles), L^{-1} R for every right-hand side and the partial
 // Schur-complement system.
@@ -69,8 +69,9 @@ struct MixedLayout {
 };
 
 // bcap: the largest bs of the structure when known (0: any bs up to ncap).
+// tc_np: right-hand sides per tensor-core pass (48 for 256 threads, 96 for 512).
 __host__ __device__ inline MixedLayout mixed_layout(int ncap, int mcap, int bcap, int d,
-                                                    bool tc, bool ga = false) {
+                                                    bool tc, bool ga = false, int tc_np = 96) {
   MixedLayout L;
   L.ncap = ncap;
   L.mcap = mcap < ncap ? mcap : ncap;
@@ -102,18 +103,23 @@ __host__ __device__ inline MixedLayout mixed_layout(int ncap, int mcap, int bcap
   // grid constant per right-hand side
   const size_t rblk = align_up((size_t)16 * rhs_stride(L.mcap) * sizeof(float), 16);
   const size_t cc = align_up((size_t)2 * (ncap + 2) * sizeof(float), 128);
-  // tensor-core residual: five 128 x 16 BF16 digit tiles of Sigma_JJ and
-  // three 16 x 16 digit tiles of X (K-major core-matrix layout)
-  const size_t sch = tc ? 5 * 4096 + 3 * 512 : 0;
+  // tensor-core residual (before the residual block is used): five 128 x 16
+  // BF16 digit tiles of Sigma_JJ and three tc_np x 16 digit tiles of X^
+  // (K-major core-matrix layout)
+  const size_t sch = tc ? 5 * 4096 + 3 * (size_t)tc_np * 32 : 0;
+  const size_t rpart = align_up(rblk > sch ? rblk : sch, 128);
   size_t uni = 2 * coord + tab;
   if (panel + stile > uni) uni = panel + stile;
-  if (align_up(rblk, 128) + cc + sch > uni) uni = align_up(rblk, 128) + cc + sch;
+  if (rpart + cc > uni) uni = rpart + cc;
+  uni = align_up(uni, 128);
   L.off_u = o;
   L.off_vl = o + coord;
   L.off_tab = o + 2 * coord;
   L.off_stile = o + panel;
-  L.off_cc = o + align_up(rblk, 128);
-  L.off_sch = L.off_cc + cc;   // 128-byte aligned (the digit tiles need 16)
+  L.off_sch = o;               // 128-byte aligned (the digit tiles need 16)
+  // the constants at the end of the union, so the residual block can take
+  // everything before them (more than 16 right-hand sides when room allows)
+  L.off_cc = o + uni - cc;
   o += align_up(uni, 128);
   L.off_A = o;
   if (!ga) o += L.a_floats * sizeof(float);
@@ -140,6 +146,9 @@ struct MixedArgs {
   // X region; fb_count and the list are read by the FP64 kernel in list mode
   unsigned int* fb_list;
   unsigned int* fb_count;
+  // right-hand sides per column block of the residual and the conditional
+  // system (0: as many as the residual block's room holds, at most 64)
+  int wcap;
   // prediction mode: one item per test point, J = its m nearest training points
   const void* Xt;        // test points (dtype of a.X)
   int64_t nt;
@@ -151,7 +160,7 @@ struct MixedArgs {
 struct MixedPlan {
   MixedLayout lay;
   bool pred, tc;
-  int threads, grid;
+  int threads, grid, wcap;
   size_t scratch_bytes() const { return lay.g_stride * sizeof(float) * (size_t)grid; }
 };
 

@@ -31,12 +31,13 @@ struct DevBuf {
 struct LaunchShape {
   int threads = 0;  // 0: no forced shape
   int per_sm = 0;
+  int tile = 0;     // mixed kernels: right-hand sides per column block (0: as many as fit)
 };
 
 // Autotuning record: the fastest shape measured for one kind of launch.
 struct TunedShape {
   int precision, pred, ncap, d;
-  int threads, per_sm;
+  int threads, per_sm, tile;
 };
 
 // Named device workspace slots of a context (grow-only buffers).
