@@ -419,6 +419,40 @@ int sbv_matern(sbv_ctx* ctx, int32_t precision, int32_t nu2, const double* d2, i
                double* out, void* stream);
 
 /*
+ * sbv_predict_blocked -- block prediction (Sec. 5.5: prediction follows the
+ * estimation pipeline): the test points are blocked like the training points
+ * (RAC anchors + up to kmeans_iters Lloyd iterations in the beta_scale space,
+ * bc_test blocks, seed as in sbv_blocking), each test block takes the m_pred
+ * training points nearest to its centre (all training points are candidates)
+ * as its conditioning set J, and every test point q of the block gets the
+ * exact Gaussian conditional given y_J: mean_q = Sigma_qJ Sigma_JJ^{-1} y_J,
+ * var_q = sigma^2 + tau^2 - Sigma_qJ Sigma_JJ^{-1} Sigma_Jq.  One factorisation
+ * of Sigma_JJ serves the whole block.
+ *
+ *   X ... theta, nu2, precision   as sbv_predict
+ *   bc_test            test blocks, 1 <= bc_test <= ntest (empty ones dropped)
+ *   ptr, pts, rank, centres, bc   training blocks from sbv_blocking on the same
+ *                      X and beta_scale (only prune the neighbour search), or
+ *                      ptr = NULL for the full scan
+ *   mean, var, var_latent  device, ntest doubles out (in test point order)
+ *   test_block         device, ntest int32 out (or NULL): block of each test point
+ *   nbr                device, bc_test x m_pred int32 out (or NULL): neighbours of
+ *                      each test block (rows < *bc_test_eff), ascending by
+ *                      (scaled distance to the centre, index)
+ *   bc_test_eff        host (or NULL): non-empty test blocks
+ *
+ * Requires m_pred + the largest test block <= SBV_MAX_BLOCK_N.  Synchronises
+ * `stream`.  Errors: as sbv_predict.
+ */
+int sbv_predict_blocked(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n,
+                        int32_t d, const void* Xtest, int64_t ntest, const double* beta_scale,
+                        int32_t m_pred, int64_t bc_test, int32_t kmeans_iters, uint64_t seed,
+                        const double* theta, int32_t nu2, int32_t precision, const int64_t* ptr,
+                        const int32_t* pts, const int32_t* rank, const double* centres,
+                        int64_t bc, double* mean, double* var, double* var_latent,
+                        int32_t* test_block, int32_t* nbr, int64_t* bc_test_eff, void* stream);
+
+/*
  * Captured evaluation (Sec. 5.4: all blocks of an evaluation in one batched
  * launch).  sbv_loglik_graph_create records one evaluation of sbv_loglik --
  * work-counter reset, the persistent block kernel over every (theta, block)

@@ -354,7 +354,7 @@ def predict(X, y, Xtest, beta_scale, m_pred: int, theta, nu2: int, rows=None):
     following Alg. 5 Step 1 with the test point as the block.  Reading of the
     garbled Sec. 5.5 sentence: var is the observation-scale variance
     (sigma^2 + tau^2 - ...) and var_latent = var - tau^2; the 1000-draw
-    conditional simulation is replaced by its exact limit (mean, variance).
+    conditional simulation from these is oracle/simulate.py.
     Returns (mean, var, var_latent, nbr) for the requested test rows.
     """
     Z = scale(X, beta_scale)
@@ -372,6 +372,34 @@ def predict(X, y, Xtest, beta_scale, m_pred: int, theta, nu2: int, rows=None):
         nbr[i, :J.size] = J
         mean[i], var[i] = predict_given(Xd, y, Xtest[j:j + 1], J, theta, nu2)
     return mean, var, var - t2, nbr
+
+
+def predict_blocked(X, y, Xtest, beta_scale, m_pred: int, bc_test: int, kmeans_iters: int,
+                    seed: int, theta, nu2: int, blocks=None):
+    """Block prediction (Sec. 5.5: prediction follows the estimation
+    pipeline): the test points are blocked like the training points
+    (`blocking`, one partition), each test block's conditioning set J is the
+    m_pred training points nearest to its centre (all training points are
+    candidates, ranked by (D, index)), and each test point of the block gets
+    the exact Gaussian conditional given y_J (`predict_given`).
+    Returns (mean, var, var_latent, test_block, nbr (blocks x m_pred)) for the
+    requested test blocks (default all; mean/var NaN for the others)."""
+    tb = blocking(Xtest, beta_scale, bc_test, kmeans_iters, seed)
+    Z = scale(X, beta_scale)
+    theta = np.asarray(theta, dtype=np.float64)
+    Xd = np.asarray(X, dtype=np.float64)
+    nt = np.asarray(Xtest).shape[0]
+    mean = np.full(nt, np.nan)
+    var = np.full(nt, np.nan)
+    K = tb["bc_eff"]
+    nbr = np.full((K, m_pred), -1, dtype=np.int64)
+    allidx = np.arange(Z.shape[0])
+    for b in (range(K) if blocks is None else blocks):
+        J = knn_block(Z, tb["centres"][b], allidx, m_pred)
+        nbr[b, :J.size] = J
+        for q in tb["pts"][tb["ptr"][b]:tb["ptr"][b + 1]]:
+            mean[q], var[q] = predict_given(Xd, y, Xtest[q:q + 1], J, theta, nu2)
+    return mean, var, var - theta[1], tb["blk"], nbr
 
 
 def predict_given(Xd, y, xt, J, theta, nu2: int):

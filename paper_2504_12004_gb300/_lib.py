@@ -100,6 +100,9 @@ SIGNATURES = {
     "sbv_simulate": (C.c_int, [_P, _P, _P, _I64, _I32, _U64, _U64, _P, _P, _P, _P, _P, _P]),
     "sbv_matern": (C.c_int, [_P, _I32, _I32, _P, _I64, _P, _P]),
     "sbv_slabs": (C.c_int, [_P, _P, C.c_int, _I64, _I32, _P, _I32, _P, _P]),
+    "sbv_predict_blocked": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _I64, _P, _I32, _I64,
+                                      _I32, _U64, _P, _I32, _I32, _P, _P, _P, _P, _I64, _P, _P,
+                                      _P, _P, _P, C.POINTER(_I64), _P]),
     "sbv_rac_plan": (C.c_int, [_U64, _I32, _P, _I64, _P, _P, _I64, _P]),
     "sbv_blocking_anchored": (C.c_int, [_P, _P, C.c_int, _I64, _I32, _P, _P, _I64, _I32,
                                         _P, _P, _P, _P, C.POINTER(_I64), _P]),
@@ -511,6 +514,34 @@ class Context:
         self._check(self.lib.sbv_matern(self.h, prec, nu2, _ptr(d2), d2.numel(), _ptr(out),
                                         _stream(stream)))
         return out
+
+    def sbv_predict_blocked(self, X, y, Xtest, beta_scale, m_pred: int, bc_test: int, theta,
+                            nu2: int = 5, precision="fp64", kmeans_iters: int = 10, seed: int = 0,
+                            blocks=None, stream=None):
+        """Block prediction: (mean, var, var_latent, test_block, nbr of the
+        non-empty test blocks)."""
+        X = _dev(X, None, "X")
+        Xtest = _dev(Xtest, X.dtype, "Xtest")
+        n, d = X.shape
+        nt = Xtest.shape[0]
+        dev = X.device
+        mean = torch.empty(nt, dtype=torch.float64, device=dev)
+        var = torch.empty(nt, dtype=torch.float64, device=dev)
+        var_lat = torch.empty(nt, dtype=torch.float64, device=dev)
+        tblk = torch.empty(nt, dtype=torch.int32, device=dev)
+        nbr = torch.empty(bc_test, m_pred, dtype=torch.int32, device=dev)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        b = blocks or {}
+        keff = C.c_int64(0)
+        rc = self.lib.sbv_predict_blocked(
+            self.h, _ptr(X), _xdtype(X), _ptr(_dev(y, torch.float64, "y")), n, d, _ptr(Xtest), nt,
+            _ptr(_host_f64(beta_scale, "beta_scale")), m_pred, bc_test, kmeans_iters,
+            int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(_host_f64(theta, "theta").reshape(-1)), nu2, prec,
+            _ptr(b.get("ptr")), _ptr(b.get("pts")), _ptr(b.get("rank")), _ptr(b.get("centres")),
+            b["rank"].numel() if b else 0, _ptr(mean), _ptr(var), _ptr(var_lat), _ptr(tblk),
+            _ptr(nbr), C.byref(keff), _stream(stream))
+        self._check(rc)
+        return mean, var, var_lat, tblk, nbr[:keff.value]
 
 
 class LoglikGraph:

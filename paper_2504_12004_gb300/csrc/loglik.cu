@@ -316,7 +316,8 @@ int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a, int nmax, int bsmax, 
                         unsigned int* fb_list, unsigned int* fb_count, cudaStream_t s);
 int launch_predict_mixed(sbv_ctx* ctx, const LoglikArgs& a0, const void* Xt, int64_t nt,
                          double* mean, double* var, double* var_latent, int precision,
-                         unsigned int* fb_list, unsigned int* fb_count, cudaStream_t s);
+                         unsigned int* fb_list, unsigned int* fb_count, cudaStream_t s,
+                         const int64_t* tptr, const int32_t* tpts, int bsmax);
 
 int run_max_n(sbv_ctx* ctx, const int64_t* ptr, const int32_t* cnt, int64_t bc, int* out,
               cudaStream_t s) {
@@ -836,8 +837,14 @@ struct PredictArgs {
   unsigned int* counter;
   double* gmat;
   size_t gmat_stride;
-  const unsigned int* list;     // list mode: the test points handed over, or NULL
+  const unsigned int* list;     // list mode: the items handed over, or NULL
   const unsigned int* list_n;
+  // blocks of test points (Sec. 5.5): item b predicts test points
+  // tpts[tptr[b] .. tptr[b+1]) from the m training neighbours nbr[b]; NULL:
+  // one item per test point
+  const int64_t* tptr;
+  const int32_t* tpts;
+  int nmax;                     // m + the largest test block
 };
 
 __global__ void __launch_bounds__(LL_THREADS)
@@ -846,14 +853,14 @@ predict_fp64_kernel(PredictArgs a) {
   __shared__ double s_scalar;
   __shared__ int s_flag;
   __shared__ unsigned int s_item;
-  __shared__ double red[LL_THREADS / 32];
-  const int d = a.d, m = a.m, N = m + 1;
-  const int ustride = N + 1;
+  const int d = a.d, m = a.m;
+  const int ustride = a.nmax + 1;
   double* u = sm;
   double* yv = u + (size_t)d * ustride;
   double* A = a.gmat ? a.gmat + (size_t)blockIdx.x * a.gmat_stride : yv + ustride;
   const ThetaDev& th = a.theta[0];
   const unsigned int total = a.list ? *a.list_n : (unsigned int)a.nt;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (;;) {
     if (threadIdx.x == 0) {
       const unsigned int k = atomicAdd(a.counter, 1u);
@@ -862,6 +869,11 @@ predict_fp64_kernel(PredictArgs a) {
     __syncthreads();
     const unsigned int item = s_item;
     if (item == 0xffffffffu) break;
+    const int64_t t0 = a.tptr ? a.tptr[item] : (int64_t)item;
+    const int bs = a.tptr ? (int)(a.tptr[item + 1] - t0) : 1;
+    const int N = m + bs;
+    // the test point of member q
+    auto tp = [&](int q) -> int64_t { return a.tptr ? (int64_t)a.tpts[t0 + q] : (int64_t)item; };
     for (int e = threadIdx.x; e < N * d; e += blockDim.x) {
       int p = e / d, t = e - p * d;
       double x;
@@ -869,8 +881,8 @@ predict_fp64_kernel(PredictArgs a) {
         int64_t id = a.nbr[(int64_t)item * m + p];
         x = a.dtype == SBV_F64 ? ld_x<double>(a.X, id * d + t) : ld_x<float>(a.X, id * d + t);
       } else {
-        x = a.dtype == SBV_F64 ? ld_x<double>(a.Xt, (int64_t)item * d + t)
-                               : ld_x<float>(a.Xt, (int64_t)item * d + t);
+        const int64_t q = tp(p - m);
+        x = a.dtype == SBV_F64 ? ld_x<double>(a.Xt, q * d + t) : ld_x<float>(a.Xt, q * d + t);
       }
       u[t * ustride + p] = x * th.inv_beta[t];
     }
@@ -880,25 +892,31 @@ predict_fp64_kernel(PredictArgs a) {
     build_cov(u, ustride, d, N, th, a.nu2, yv, A);
     if (threadIdx.x == 0) s_flag = 0;
     __syncthreads();
-    bool ok = chol_columns(A, N, m, &s_scalar, &s_flag);
-    double v = 0.0;
-    if (ok)
-      for (int t = threadIdx.x; t < m; t += blockDim.x) v += A[tri(m, t)] * A[tri(N, t)];
-    double s = cta_sum(v, red);
-    if (threadIdx.x == 0) {
-      if (ok) {
-        double var = A[tri(m, m)];
-        a.mean[item] = s;
-        a.var[item] = var;
-        a.var_latent[item] = var - th.tau2;
-      } else {
-        double nan = __longlong_as_double(0x7ff8000000000000ll);
-        a.mean[item] = nan;
-        a.var[item] = nan;
-        a.var_latent[item] = nan;
-        record_failure(a.dstat, SBV_ENOTSPD, (int)item, 0);
+    // factor the m columns of Sigma_JJ: row m + q then holds
+    // w_q = L^{-1} Sigma_{J,q}, the bordered row z = L^{-1} y_J, and the
+    // diagonal entry Sigma_qq - |w_q|^2 (the marginal conditional variance)
+    const bool ok = chol_columns(A, N, m, &s_scalar, &s_flag);
+    for (int q = warp; q < bs; q += nw) {
+      double v = 0.0;
+      if (ok)
+        for (int t = lane; t < m; t += 32) v += A[tri(m + q, t)] * A[tri(N, t)];
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) {
+        const int64_t pt = tp(q);
+        if (ok) {
+          const double var = A[tri(m + q, m + q)];
+          a.mean[pt] = v;
+          a.var[pt] = var;
+          a.var_latent[pt] = var - th.tau2;
+        } else {
+          const double nan = __longlong_as_double(0x7ff8000000000000ll);
+          a.mean[pt] = nan;
+          a.var[pt] = nan;
+          a.var_latent[pt] = nan;
+        }
       }
     }
+    if (!ok && threadIdx.x == 0) record_failure(a.dstat, SBV_ENOTSPD, (int)item, 0);
     __syncthreads();
   }
 }
@@ -906,7 +924,8 @@ predict_fp64_kernel(PredictArgs a) {
 int run_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n, int d,
                 const void* Xt, int64_t nt, const int32_t* nbr, int m, const double* h_theta,
                 int nu2, int precision, double* mean, double* var, double* var_latent,
-                cudaStream_t s) {
+                cudaStream_t s, const int64_t* tptr, const int32_t* tpts, int bsmax) {
+  if (!tptr) bsmax = 1;
   int st = 0;
   ThetaDev* dth = nullptr;
   if ((st = upload_theta(ctx, h_theta, 1, d, &dth, s))) return st;
@@ -935,7 +954,7 @@ int run_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t
     la.dstat = ctx->d_status;
     la.counter = counter;
     if ((st = launch_predict_mixed(ctx, la, Xt, nt, mean, var, var_latent, precision, list,
-                                   counter + 1, s)))
+                                   counter + 1, s, tptr, tpts, bsmax)))
       return st;
   }
   PredictArgs a;
@@ -957,12 +976,15 @@ int run_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t
   a.counter = counter;
   a.gmat = nullptr;
   a.gmat_stride = 0;
-  if (list) {  // FP64 pass over the test points the mixed kernel handed over
+  a.tptr = tptr;
+  a.tpts = tpts;
+  a.nmax = m + bsmax;
+  if (list) {  // FP64 pass over the items the mixed kernel handed over
     a.list = list;
     a.list_n = counter + 1;
     a.counter = counter + 2;
   }
-  const int N = m + 1;
+  const int N = m + bsmax;
   const size_t ub = (size_t)(d + 1) * (N + 1) * sizeof(double);
   const size_t mat = (size_t)(N + 1) * (N + 2) / 2 * sizeof(double);
   size_t smem = ub + mat;

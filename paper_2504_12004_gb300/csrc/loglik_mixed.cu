@@ -147,7 +147,13 @@ loglik_mixed_kernel(MixedArgs P) {
     const int th_i = PRED ? 0 : (int)(item / a.bc);
     const int64_t blk = PRED ? (int64_t)item : (int64_t)(item % a.bc);
     const ThetaDev& th = a.theta[th_i];
-    const int bs = PRED ? 1 : (int)(a.ptr[blk + 1] - a.ptr[blk]);
+    // prediction: the test points of the item are tpts[tb .. tb + bs)
+    const int64_t tb = PRED ? (P.tptr ? P.tptr[blk] : (int64_t)item) : 0;
+    const int bs = PRED ? (P.tptr ? (int)(P.tptr[blk + 1] - tb) : 1)
+                        : (int)(a.ptr[blk + 1] - a.ptr[blk]);
+    auto test_point = [&](int q) -> int64_t {
+      return P.tptr ? (int64_t)P.tpts[tb + q] : (int64_t)item;
+    };
     const int mb = PRED ? a.m : a.cnt[blk];
     const int N = mb + bs;
     const int nr = bs + 1;               // rows of the right-hand-side block: B, then y
@@ -156,9 +162,12 @@ loglik_mixed_kernel(MixedArgs P) {
     if (N > cap || mb > lay.mcap) {
       if (tid == 0) {
         if (PRED) {
-          P.mean[item] = nan;
-          P.var[item] = nan;
-          P.var_latent[item] = nan;
+          for (int q = 0; q < bs; ++q) {
+            const int64_t pt = test_point(q);
+            P.mean[pt] = nan;
+            P.var[pt] = nan;
+            P.var_latent[pt] = nan;
+          }
         } else {
           a.terms[item] = nan;
           if (a.status) a.status[item] = SBV_EUNSUPPORTED;
@@ -194,8 +203,8 @@ loglik_mixed_kernel(MixedArgs P) {
       tab_l[i] = C.tab_l[i];
     }
     for (int p = tid; p < N; p += THREADS) {
-      if (PRED && p == mb) {
-        yv[p] = make_float2(0.0f, 0.0f);  // the test point's observation is unknown
+      if (PRED && p >= mb) {
+        yv[p] = make_float2(0.0f, 0.0f);  // the test points' observations are unknown
         continue;
       }
       const int64_t id = p < mb ? (int64_t)a.nbr[blk * a.m + p] : (int64_t)a.pts[base + (p - mb)];
@@ -206,11 +215,12 @@ loglik_mixed_kernel(MixedArgs P) {
     for (int e = tid; e < N * d; e += THREADS) {
       const int p = e / d, t = e - p * d;
       df x;
-      if (PRED && p == mb) {
+      if (PRED && p >= mb) {
+        const int64_t q = test_point(p - mb);
         if (a.dtype == SBV_F64) {
-          x = df_from_double(((const double*)P.Xt)[(int64_t)item * d + t]);
+          x = df_from_double(((const double*)P.Xt)[q * d + t]);
         } else {
-          x = {((const float*)P.Xt)[(int64_t)item * d + t], 0.0f};
+          x = {((const float*)P.Xt)[q * d + t], 0.0f};
         }
       } else {
         const int64_t id = p < mb ? (int64_t)a.nbr[blk * a.m + p] : (int64_t)a.pts[base + (p - mb)];
@@ -921,6 +931,8 @@ loglik_mixed_kernel(MixedArgs P) {
         for (int t = tid; t < max(ncb, 0) * na; t += THREADS) {
           const int c = t % ncb, ar = cb + t / ncb, r = cb + c;
           if (ar < r) continue;
+          // prediction needs the diagonal and the bordered row only
+          if (PRED && ar != r && ar != bs) continue;
           const float2 v0 = ar < bs ? S[(size_t)(mb + r) * N + (mb + ar)] : yv[mb + r];
           df e = {v0.x, v0.y};
           float d1 = 0.0f;
@@ -1016,6 +1028,7 @@ loglik_mixed_kernel(MixedArgs P) {
     for (int t = tid; t < nr * bs; t += THREADS) {
       const int ar = t / bs, b = t - ar * bs;
       if (b > ar) continue;
+      if (PRED && ar != b && ar != bs) continue;
       float d2 = 0.0f;
       const float* qa = Qg + (size_t)ar * xs;
       const float* qb = Qg + (size_t)b * xs;
@@ -1043,14 +1056,16 @@ loglik_mixed_kernel(MixedArgs P) {
     }
     __syncthreads();
     if (PRED) {
-      // mean = mu^new, var = Sigma^new (1 x 1); the bordered row holds 0 - mu
-      if (tid == 0) {
-        const float2 v = Sf[tri0(0, 0)], mu = Sf[tri0(1, 0)];
+      // per test point q: mean = mu^new_q, var = Sigma^new_qq; the bordered
+      // row holds 0 - mu
+      for (int q = tid; q < bs; q += THREADS) {
+        const float2 v = Sf[tri0(q, q)], mu = Sf[tri0(bs, q)];
         const double var = (double)v.x + (double)v.y;
         const double mean = -((double)mu.x + (double)mu.y);
-        P.mean[item] = mean;
-        P.var[item] = var;
-        P.var_latent[item] = var - th.tau2;
+        const int64_t pt = test_point(q);
+        P.mean[pt] = mean;
+        P.var[pt] = var;
+        P.var_latent[pt] = var - th.tau2;
         if (!isfinite(mean) || !isfinite(var)) record_failure(a.dstat, SBV_ENOTSPD, (int)blk, 0);
       }
       __syncthreads();
@@ -1407,7 +1422,8 @@ int launch_loglik_mixed(sbv_ctx* ctx, const LoglikArgs& a0, int nmax, int bsmax,
 // Prediction: a0 carries X, y, d, nbr (ntest x m), m, theta, nu2, dstat, counter.
 int launch_predict_mixed(sbv_ctx* ctx, const LoglikArgs& a0, const void* Xt, int64_t nt,
                          double* mean, double* var, double* var_latent, int precision,
-                         unsigned int* fb_list, unsigned int* fb_count, cudaStream_t s) {
+                         unsigned int* fb_list, unsigned int* fb_count, cudaStream_t s,
+                         const int64_t* tptr, const int32_t* tpts, int bsmax) {
   MixedArgs P;
   memset(&P, 0, sizeof(P));
   P.a = a0;
@@ -1418,7 +1434,10 @@ int launch_predict_mixed(sbv_ctx* ctx, const LoglikArgs& a0, const void* Xt, int
   P.var_latent = var_latent;
   P.fb_list = fb_list;
   P.fb_count = fb_count;
-  return launch_mixed(ctx, P, a0.m + 1, a0.m, 1, precision, true, nt, s);
+  P.tptr = tptr;
+  P.tpts = tpts;
+  if (!tptr) bsmax = 1;
+  return launch_mixed(ctx, P, a0.m + bsmax, a0.m, bsmax, precision, true, nt, s);
 }
 
 }  // namespace sbv

@@ -149,9 +149,13 @@ struct MixedArgs {
   // right-hand sides per column block of the residual and the conditional
   // system (0: as many as the residual block's room holds, at most 64)
   int wcap;
-  // prediction mode: one item per test point, J = its m nearest training points
+  // prediction mode: one item per test point, J = its m nearest training
+  // points, or (tptr set) one item per block of test points b, the points
+  // tpts[tptr[b] .. tptr[b+1]) sharing the block's J
   const void* Xt;        // test points (dtype of a.X)
-  int64_t nt;
+  int64_t nt;            // items
+  const int64_t* tptr;
+  const int32_t* tpts;
   double* mean;
   double* var;
   double* var_latent;

@@ -397,6 +397,86 @@ extern "C" int sbv_predict(sbv_ctx* ctx, const void* X, int dtype, const double*
                         nbr, stream);
 }
 
+extern "C" int sbv_predict_blocked(sbv_ctx* ctx, const void* X, int dtype, const double* y,
+                                   int64_t n, int32_t d, const void* Xtest, int64_t ntest,
+                                   const double* beta_scale, int32_t m_pred, int64_t bc_test,
+                                   int32_t kmeans_iters, uint64_t seed, const double* theta,
+                                   int32_t nu2, int32_t precision, const int64_t* ptr,
+                                   const int32_t* pts, const int32_t* rank,
+                                   const double* centres, int64_t bc, double* mean, double* var,
+                                   double* var_latent, int32_t* test_block, int32_t* nbr,
+                                   int64_t* bc_test_eff, void* stream) {
+  int st = check_common(ctx, X, dtype, n, d);
+  if (st) return st;
+  if (!y || !Xtest || !mean || !var || !var_latent)
+    return fail(ctx, SBV_EINVAL, "null pointer argument");
+  if (ntest < 1 || ntest > (int64_t)INT32_MAX - 1) return fail(ctx, SBV_EINVAL, "ntest out of range");
+  if ((st = check_beta(ctx, beta_scale, d, "beta_scale"))) return st;
+  if (m_pred < 1 || m_pred > n) return fail(ctx, SBV_EINVAL, "m_pred=%d outside [1, n]", m_pred);
+  if (bc_test < 1 || bc_test > ntest)
+    return fail(ctx, SBV_EINVAL, "bc_test=%lld outside [1, ntest]", (long long)bc_test);
+  if (kmeans_iters < 0) return fail(ctx, SBV_EINVAL, "kmeans_iters must be >= 0");
+  if ((st = check_theta(ctx, theta, 1, d))) return st;
+  if (precision != SBV_PREC_FP64 && precision != SBV_PREC_MIXED &&
+      precision != SBV_PREC_MIXED_BF16)
+    return fail(ctx, SBV_EINVAL, "precision=%d unknown", precision);
+  if (!nu_ok_prec(nu2, precision))
+    return fail(ctx, SBV_EINVAL, "nu2=%d: FP64 takes 1..%d, the mixed precisions {1,3,5,7}", nu2,
+                SBV_MAX_NU2);
+  if (ptr && (!pts || !rank || !centres || bc < 1 || bc > n))
+    return fail(ctx, SBV_EINVAL, "incomplete block structure");
+  cudaStream_t s = (cudaStream_t)stream;
+  SBV_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  size_t zbytes = (size_t)(n + ntest) * d * sizeof(double);
+  double* Z = (double*)ws_get(ctx, WS_Z, zbytes, &st);
+  if (!Z) return st;
+  double* Zt = Z + (size_t)n * d;
+  if ((st = scale_points(ctx, X, dtype, n, d, nullptr, beta_scale, Z, s))) return st;
+  if ((st = scale_points(ctx, Xtest, dtype, ntest, d, nullptr, beta_scale, Zt, s))) return st;
+  // blocks of test points (RAC + Lloyd in the same scaled space)
+  const size_t tb_bytes = (size_t)ntest * 2 * sizeof(int32_t) + (size_t)(bc_test + 1) * 8 +
+                          (size_t)bc_test * d * sizeof(double) + 256;
+  char* tw = (char*)ws_get(ctx, WS_TBLK, tb_bytes, &st);
+  if (!tw) return st;
+  double* tcent = (double*)tw;
+  int64_t* tptr = (int64_t*)(tcent + (size_t)bc_test * d);
+  int32_t* tpts = (int32_t*)(tptr + bc_test + 1);
+  int32_t* tblk = tpts + ntest;
+  int64_t kt = 0;
+  if ((st = run_blocking(ctx, Zt, Xtest, dtype, beta_scale, ntest, d, bc_test, kmeans_iters, seed,
+                         1, tblk, tptr, tpts, nullptr, tcent, &kt, s)))
+    return st;
+  // m_pred nearest training points of every test block's centre
+  int32_t* knbr = nbr;
+  if (!knbr) {
+    knbr = (int32_t*)ws_get(ctx, WS_PRED, (size_t)kt * m_pred * sizeof(int32_t), &st);
+    if (!knbr) return st;
+  }
+  if (ptr)
+    st = run_knn_blocks_all(ctx, Z, n, d, ptr, pts, rank, centres, bc, tcent, kt, m_pred, knbr, s);
+  else
+    st = run_knn_all(ctx, Z, n, d, tcent, kt, m_pred, knbr, s);
+  if (st) return st;
+  std::vector<int64_t> hptr((size_t)kt + 1);
+  SBV_CUDA_TRY(ctx, cudaMemcpyAsync(hptr.data(), tptr, (kt + 1) * sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, s));
+  SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  int bsmax = 1;
+  for (int64_t b = 0; b < kt; ++b) bsmax = std::max<int>(bsmax, (int)(hptr[b + 1] - hptr[b]));
+  if (m_pred + bsmax > SBV_MAX_BLOCK_N)
+    return fail(ctx, SBV_EUNSUPPORTED, "m_pred + largest test block = %d above %d",
+                m_pred + bsmax, SBV_MAX_BLOCK_N);
+  if ((st = run_predict(ctx, X, dtype, y, n, d, Xtest, kt, knbr, m_pred, theta, nu2, precision,
+                        mean, var, var_latent, s, tptr, tpts, bsmax)))
+    return st;
+  if (test_block)
+    SBV_CUDA_TRY(ctx, cudaMemcpyAsync(test_block, tblk, (size_t)ntest * sizeof(int32_t),
+                                      cudaMemcpyDeviceToDevice, s));
+  if (bc_test_eff) *bc_test_eff = kt;
+  SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  return sbv_sync_status(ctx, stream);
+}
+
 extern "C" int sbv_matern(sbv_ctx* ctx, int32_t precision, int32_t nu2, const double* d2,
                           int64_t n, double* out, void* stream) {
   if (!ctx) return SBV_EINVAL;

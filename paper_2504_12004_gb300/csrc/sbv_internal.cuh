@@ -62,6 +62,7 @@ enum WsSlot {
   WS_GRADZ,       // per-CTA right-hand sides of the gradient kernel
   WS_RERUN,       // items the mixed kernels hand to the FP64 kernels
   WS_GMAT64,      // global matrices of the FP64 kernel after a mixed launch
+  WS_TBLK,        // blocking of the test points (block prediction)
   WS_COUNT
 };
 
@@ -159,6 +160,7 @@ int run_simulate(sbv_ctx* ctx, const double* mean, const double* var, int64_t nt
 int run_predict(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n,
                 int d, const void* Xt, int64_t nt, const int32_t* nbr, int m,
                 const double* h_theta, int nu2, int precision, double* mean,
-                double* var, double* var_latent, cudaStream_t s);
+                double* var, double* var_latent, cudaStream_t s,
+                const int64_t* tptr = nullptr, const int32_t* tpts = nullptr, int bsmax = 1);
 
 }  // namespace sbv

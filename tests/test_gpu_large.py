@@ -1,6 +1,9 @@
 """The large single-GPU workload at full size: 50,000,000 points on [0,1]^10
-in FP32 storage (sine-sum response), 1,000,000 blocks, m = 300, predictions
-with m_pred = 300.
+in FP32 storage (sine-sum response), 1,000,000 blocks, m = 300; predictive
+means and variances at all 1,000,000 test points with m_pred = 300 (block
+prediction: 40,000 test blocks of ~25 points, each conditioned on its
+centre's 300 nearest training points), and per-point prediction at a
+leading sample of the test points.
 
 The structure follows the paper's large-scale pipeline: slabs along the most
 relevant dimension (Alg. 2, P = 100) and RAC inside every slab (Alg. 3, no
@@ -28,7 +31,9 @@ from synth.inputs import workload
 pytestmark = pytest.mark.gpu
 
 P_SLABS = 100
-NTEST = 20_000     # a leading sample of the 1,000,000 test points
+NTEST = 1_000_000
+BC_TEST = 40_000     # test blocks of ~25 points (the paper's bs_pred = 25, Sec. 6.3)
+NPOINT = 2_000       # leading test points also predicted one by one
 
 
 @pytest.fixture(scope="module")
@@ -80,10 +85,17 @@ def test_large_workload(ctx):
     times["loglik_mixed"] = time.time() - t0
     ctx.sbv_sync_status()
     t0 = time.time()
-    mean, var, var_lat, pnbr = ctx.sbv_predict(X, y, Xt, w["beta_scale"], w["m_pred"], th, 5,
+    Xp = Xt[:NPOINT].contiguous()
+    mean, var, var_lat, pnbr = ctx.sbv_predict(X, y, Xp, w["beta_scale"], w["m_pred"], th, 5,
                                                precision="mixed", want_nbr=True, blocks=b)
     torch.cuda.synchronize()
-    times["predict_mixed"] = time.time() - t0
+    times["predict_mixed_per_point_2000"] = time.time() - t0
+    t0 = time.time()
+    bmean, bvar, bvar_lat, tblk, tnbr = ctx.sbv_predict_blocked(
+        X, y, Xt, w["beta_scale"], w["m_pred"], BC_TEST, th, 5, "mixed", 10, 5, blocks=b)
+    torch.cuda.synchronize()
+    times["predict_mixed_blocked_1M"] = time.time() - t0
+    assert torch.isfinite(bmean).all() and torch.isfinite(bvar).all()
     bt64 = torch.empty(1, bc, dtype=torch.float64, device="cuda")
     t0 = time.time()
     ll64 = ctx.sbv_loglik(X, y, b["ptr"], b["pts"], nbr, cnt, th, nu2=5, precision="fp64",
@@ -126,7 +138,21 @@ def test_large_workload(ctx):
     allidx = np.arange(n)
     pn = pnbr.cpu().numpy()
     mh, vh = mean.cpu().numpy(), var.cpu().numpy()
-    for j in rng.choice(NTEST, 2, replace=False):
+    for j in rng.choice(NPOINT, 2, replace=False):
         assert knn_is_exact(Z, allidx, Zt[j], pn[j])
         om, ov = sbv.predict_given(Xh, w["y"], w["Xtest"][j:j + 1], pn[j], th, 5)
         assert abs(mh[j] - om) <= 1e-6 and abs(vh[j] - ov) <= 1e-6, (j, mh[j], om, vh[j], ov)
+    # block prediction: sampled test blocks -- centre (recomputed from the
+    # members in index order), neighbour set key for key, and every member's
+    # mean and variance against the exact conditional given that set
+    tb = tblk.cpu().numpy()
+    tn = tnbr.cpu().numpy()
+    bm, bv = bmean.cpu().numpy(), bvar.cpu().numpy()
+    assert tb.min() == 0 and tb.max() == tn.shape[0] - 1
+    for bi in rng.choice(tn.shape[0], 2, replace=False):
+        mem = np.flatnonzero(tb == bi)
+        c = np.cumsum(Zt[mem], axis=0)[-1] / len(mem)
+        assert knn_is_exact(Z, allidx, c, tn[bi])
+        for j in mem[:3]:
+            om, ov = sbv.predict_given(Xh, w["y"], w["Xtest"][j:j + 1], tn[bi], th, 5)
+            assert abs(bm[j] - om) <= 1e-6 and abs(bv[j] - ov) <= 1e-6, (j, bm[j], om, bv[j], ov)
