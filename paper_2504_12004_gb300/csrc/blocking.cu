@@ -83,14 +83,32 @@ __global__ void gather_rows_kernel(const double* __restrict__ Z, const int32_t* 
 constexpr int ASSIGN_THREADS = 256;
 constexpr int ASSIGN_TILE = 128;
 
+// Bounds for skipping points in later Lloyd iterations (Hamerly, "Making
+// k-means even faster", SDM 2010): ub >= the distance to the assigned centre,
+// lb <= the distance to every other centre, both for true distances with a
+// relative slack that covers the rounding of the FP64 squared distances the
+// argmin compares.  When ub < lb after the centres moved (ub grown by the
+// assigned centre's move, lb shrunk by the largest move), the assigned centre
+// is still the unique nearest one and the point keeps its block.
+constexpr double kBoundSlack = 1e-12;
+
+// list: when not NULL, the thread's point is list[g] for g < *list_n (the
+// points whose bounds did not decide); ub/lb: when not NULL, the bounds of
+// each assigned point are written.
 template <int DM>
 __global__ void __launch_bounds__(ASSIGN_THREADS)
 assign_kernel(const double* __restrict__ Z, int64_t n, int d, const double* __restrict__ C,
               int64_t k, ScreenBound sb, const int32_t* __restrict__ old_blk,
-              int32_t* __restrict__ blk, unsigned long long* __restrict__ changed) {
+              int32_t* __restrict__ blk, unsigned long long* __restrict__ changed,
+              const int32_t* __restrict__ list, const unsigned int* __restrict__ list_n,
+              double* __restrict__ ub, double* __restrict__ lb) {
   __shared__ float cf[ASSIGN_TILE * DM];
-  int64_t i = blockIdx.x * (int64_t)ASSIGN_THREADS + threadIdx.x;
-  bool live = i < n;
+  const int64_t g = blockIdx.x * (int64_t)ASSIGN_THREADS + threadIdx.x;
+  const int64_t nl = list ? (int64_t)*list_n : n;
+  if (list && (int64_t)blockIdx.x * ASSIGN_THREADS >= nl) return;   // the whole CTA is idle
+  int64_t i = g;
+  bool live = g < nl;
+  if (list) i = live ? (int64_t)list[g] : 0;
   float zf[DM];
 #pragma unroll
   for (int t = 0; t < DM; ++t) zf[t] = (live && t < d) ? (float)Z[i * d + t] : 0.0f;
@@ -120,8 +138,10 @@ assign_kernel(const double* __restrict__ Z, int64_t n, int d, const double* __re
       }
     }
   }
-  // pass 2: exact FP64 distance for every centre whose lower bound can reach best_ub
-  double best = INFINITY;
+  // pass 2: exact FP64 distance for every centre whose lower bound can reach
+  // best_ub; `second` bounds every other centre from below (exact values
+  // where computed, the screen's lower bound elsewhere)
+  double best = INFINITY, second = INFINITY;
   int64_t arg = 0;
   double zi[DM];
 #pragma unroll
@@ -144,13 +164,21 @@ assign_kernel(const double* __restrict__ Z, int64_t n, int d, const double* __re
             acc = fmaf(df, df, acc);
           }
         }
-        float lb = acc - screen_margin(acc, sb);
-        if (lb <= best_ub) {
+        float lb32 = acc - screen_margin(acc, sb);
+        if (lb32 <= best_ub) {
           double D = dist2_exact<DM>(zi, C + (j0 + jj) * d, d);
           if (D < best) {  // strict: ties keep the smaller index
+            // the old best joins the others (a pruned centre's bound may
+            // already be below it)
+            second = fmin(second, best);
             best = D;
             arg = j0 + jj;
+          } else {
+            second = fmin(second, D);
           }
+        } else {
+          // the screen's lower bound, widened against its own float rounding
+          second = fmin(second, (double)fmaxf(lb32, 0.0f) * (1.0 - 1e-6));
         }
       }
     }
@@ -159,6 +187,47 @@ assign_kernel(const double* __restrict__ Z, int64_t n, int d, const double* __re
     int32_t a = (int32_t)arg;
     if (old_blk && old_blk[i] != a) atomicAdd(changed, 1ull);
     blk[i] = a;
+    if (ub) {
+      ub[i] = sqrt(best) * (1.0 + kBoundSlack);
+      lb[i] = sqrt(second) * (1.0 - kBoundSlack);
+    }
+  }
+}
+
+// How far each centre moved (rounded up), and the largest move.
+__global__ void centre_move_kernel(const double* __restrict__ Cold, const double* __restrict__ Cnew,
+                                   int64_t k, int d, double* __restrict__ delta,
+                                   unsigned long long* __restrict__ dmax) {
+  double m = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < k;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int t = 0; t < d; ++t) {
+      const double q = Cnew[j * d + t] - Cold[j * d + t];
+      s = fma(q, q, s);
+    }
+    const double v = sqrt(s) * (1.0 + kBoundSlack) + 1e-300;
+    delta[j] = v;
+    m = fmax(m, v);
+  }
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(dmax, (unsigned long long)__double_as_longlong(m));
+}
+
+// Move the bounds with the centres; list the points they no longer decide.
+__global__ void bound_filter_kernel(int64_t n, const int32_t* __restrict__ blk,
+                                    const double* __restrict__ delta,
+                                    const unsigned long long* __restrict__ dmax,
+                                    double* __restrict__ ub, double* __restrict__ lb,
+                                    int32_t* __restrict__ list, unsigned int* __restrict__ list_n) {
+  const double dm = __longlong_as_double((long long)*dmax);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double u = ub[i] + delta[blk[i]];
+    const double l = lb[i] - dm;
+    ub[i] = u;
+    lb[i] = l;
+    if (!(u < l)) list[atomicAdd(list_n, 1u)] = (int32_t)i;
   }
 }
 
@@ -385,10 +454,13 @@ int absmax(sbv_ctx* ctx, const double* Z, int64_t total, double* out, cudaStream
 
 static int launch_assign(sbv_ctx* ctx, const double* Z, int64_t n, int d, const double* C,
                          int64_t k, ScreenBound sb, const int32_t* old_blk, int32_t* blk,
-                         unsigned long long* changed, cudaStream_t s) {
+                         unsigned long long* changed, cudaStream_t s,
+                         const int32_t* list = nullptr, const unsigned int* list_n = nullptr,
+                         double* ub = nullptr, double* lb = nullptr) {
   int g = (int)((n + ASSIGN_THREADS - 1) / ASSIGN_THREADS);
-#define SBV_ASSIGN(DM) \
-  assign_kernel<DM><<<g, ASSIGN_THREADS, 0, s>>>(Z, n, d, C, k, sb, old_blk, blk, changed)
+#define SBV_ASSIGN(DM)                                                                     \
+  assign_kernel<DM><<<g, ASSIGN_THREADS, 0, s>>>(Z, n, d, C, k, sb, old_blk, blk, changed, \
+                                                 list, list_n, ub, lb)
   if (d <= 4) SBV_ASSIGN(4);
   else if (d <= 8) SBV_ASSIGN(8);
   else if (d <= 12) SBV_ASSIGN(12);
@@ -589,11 +661,34 @@ int run_blocking(sbv_ctx* ctx, const double* Z, const void* X, int dtype, const 
   SBV_LAUNCH_CHECK(ctx, "gather_rows_kernel");
   SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));  // anchors buffer reused below
 
-  auto assign = [&](const double* Cc, const int32_t* old, int32_t* out) {
+  // flat blocking with Lloyd iterations: bounds let later assignments skip
+  // the points whose block cannot change (Hamerly); the slab-partitioned
+  // assignment scans every centre of the point's slab
+  double* bnd_u = nullptr;
+  double* bnd_l = nullptr;
+  double* delta = nullptr;
+  int32_t* blist = nullptr;
+  unsigned int* blist_n = nullptr;
+  unsigned long long* dmax = nullptr;
+  if (!pslab && kmeans_iters > 0) {
+    char* wb = (char*)ws_get(ctx, WS_BOUNDS,
+                             (size_t)n * (2 * sizeof(double) + sizeof(int32_t)) +
+                                 (size_t)bc * sizeof(double) + 256, &st);
+    if (!wb) return st;
+    bnd_u = (double*)wb;
+    bnd_l = bnd_u + n;
+    delta = bnd_l + n;
+    blist = (int32_t*)(delta + bc);
+    blist_n = (unsigned int*)(changed + 1);
+    dmax = changed + 2;
+  }
+  auto assign = [&](const double* Cc, const int32_t* old, int32_t* out, bool listed) {
     return pslab ? launch_assign_slab(ctx, Z, n, d, Cc, sorder, pslab, cstart, sb, old, out, changed, s)
-                 : launch_assign(ctx, Z, n, d, Cc, bc, sb, old, out, changed, s);
+                 : launch_assign(ctx, Z, n, d, Cc, bc, sb, old, out, changed, s,
+                                 listed ? blist : nullptr, listed ? blist_n : nullptr, bnd_u,
+                                 bnd_l);
   };
-  if ((st = assign(Ca, nullptr, blk))) return st;
+  if ((st = assign(Ca, nullptr, blk, false))) return st;
   double* C = Ca;
   double* Cn = Cb;
   for (int it = 0; it < kmeans_iters; ++it) {
@@ -602,11 +697,20 @@ int run_blocking(sbv_ctx* ctx, const double* Z, const void* X, int dtype, const 
     centroid_kernel<<<grid_for(bc * d, 128, ctx->num_sms), 128, 0, s>>>(Z, d, ptr_tmp, pts, bc,
                                                                          C, Cn);
     SBV_LAUNCH_CHECK(ctx, "centroid_kernel");
+    if (bnd_u) {
+      SBV_CUDA_TRY(ctx, cudaMemsetAsync(blist_n, 0, 16, s));   // list count and largest move
+      centre_move_kernel<<<grid_for(bc, 256, ctx->num_sms), 256, 0, s>>>(C, Cn, bc, d, delta,
+                                                                         dmax);
+      SBV_LAUNCH_CHECK(ctx, "centre_move_kernel");
+      bound_filter_kernel<<<grid_for(n, 256, ctx->num_sms), 256, 0, s>>>(
+          n, blk, delta, dmax, bnd_u, bnd_l, blist, blist_n);
+      SBV_LAUNCH_CHECK(ctx, "bound_filter_kernel");
+    }
     std::swap(C, Cn);
     SBV_CUDA_TRY(ctx, cudaMemcpyAsync(old_blk, blk, n * sizeof(int32_t),
                                       cudaMemcpyDeviceToDevice, s));
     SBV_CUDA_TRY(ctx, cudaMemsetAsync(changed, 0, 8, s));
-    if ((st = assign(C, old_blk, blk))) return st;
+    if ((st = assign(C, old_blk, blk, bnd_u != nullptr))) return st;
     unsigned long long h_changed = 0;
     SBV_CUDA_TRY(ctx, cudaMemcpyAsync(&h_changed, changed, 8, cudaMemcpyDeviceToHost, s));
     SBV_CUDA_TRY(ctx, cudaStreamSynchronize(s));

@@ -63,6 +63,7 @@ enum WsSlot {
   WS_RERUN,       // items the mixed kernels hand to the FP64 kernels
   WS_GMAT64,      // global matrices of the FP64 kernel after a mixed launch
   WS_TBLK,        // blocking of the test points (block prediction)
+  WS_BOUNDS,      // distance bounds and point list of the bounded K-means assignment
   WS_COUNT
 };
 
