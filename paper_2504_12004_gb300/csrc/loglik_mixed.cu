@@ -999,20 +999,25 @@ loglik_mixed_kernel(MixedArgs P) {
           if (c < nc && rr < nbk) Rb[(size_t)c * xs + k0 + rr] = xo[j];
         }
         __syncthreads();
-        const int ni4 = (mb - k1 + 3) >> 2;
-        for (int t = tid; t < nc * ni4; t += THREADS) {
-          const int cc = t / ni4, i = k1 + (t - cc * ni4) * 4;
-          float* pr = Rb + (size_t)cc * xs;
-          const float4 acc = *(const float4*)(pr + i);
-          float av[4] = {acc.x, acc.y, acc.z, acc.w};
-#pragma unroll 4
-          for (int q = 0; q < nbk; ++q) {
-            const float qc = pr[k0 + q];
+        // trailing rows: thread (i, c), the columns fastest so that a warp
+        // shares the row of L (a broadcast) and reads its columns' solved
+        // tile entries; a full tile (nbk = 16) whenever rows remain below it
+        const int ni = mb - k1;
+        for (int t = tid; t < nc * ni; t += THREADS) {
+          const int ir = t / nc, c = t - ir * nc, i = k1 + ir;
+          float* pr = Rb + (size_t)c * xs;
+          const float* Lr = A + trp(i, k0);
+          float acc = pr[i];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (i + u < mb) av[u] = fmaf(-A[trp(i + u, k0 + q)], qc, av[u]);
+          for (int q4 = 0; q4 < NB; q4 += 4) {
+            const float4 l = *(const float4*)(Lr + q4);
+            const float4 x = *(const float4*)(pr + k0 + q4);
+            acc = fmaf(-l.x, x.x, acc);
+            acc = fmaf(-l.y, x.y, acc);
+            acc = fmaf(-l.z, x.z, acc);
+            acc = fmaf(-l.w, x.w, acc);
           }
-          *(float4*)(pr + i) = make_float4(av[0], av[1], av[2], av[3]);
+          pr[i] = acc;
         }
       }
       __syncthreads();
