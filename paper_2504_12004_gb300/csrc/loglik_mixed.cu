@@ -1077,55 +1077,86 @@ loglik_mixed_kernel(MixedArgs P) {
       continue;
     }
     // ---- 10. LDL^T of Sigma^new (bs x bs) bordered by z = y_B - mu^new, in
-    // double-float, one column per step (the step's entries spread over the
-    // CTA): S_ij -= (S_ik / d_k) S_jk for k < j <= i (i <= bs, j < bs);
-    // then log det = sum log d_k and the quadratic form = sum z_k^2 / d_k
-    // (z in the bordered row)
+    // double-float, right-looking in panels of eight columns: inside a panel
+    // one column per step, the CTA updating the panel's later columns
+    // (S_ij -= (S_ik / d_k) S_jk, rows down to the bordered row bs); then the
+    // trailing matrix takes the panel's eight columns in one pass,
+    // S_ij -= sum_k S_ik W_jk with W_jk = S_jk / d_k.  Afterwards log det =
+    // sum log d_k and the quadratic form = sum z_k^2 / d_k (z in the
+    // bordered row).
     {
+      constexpr int PW = 8;
+      float2* Wp = (float2*)(smem + lay.off_u);   // W_jk of the panel, PW per row j
+      __shared__ float2 s_inv[PW];
       bool bad = false;
-      for (int k = 0; k < bs; ++k) {
-        const float2 dk2 = Sf[tri0(k, k)];
-        if (!(dk2.x > 0.0f)) {   // the same value in every thread
-          bad = true;
-          break;
+      for (int k0 = 0; k0 < bs && !bad; k0 += PW) {
+        const int k1 = min(k0 + PW, bs);
+        for (int k = k0; k < k1; ++k) {
+          const float2 dk2 = Sf[tri0(k, k)];
+          if (!(dk2.x > 0.0f)) {   // the same value in every thread
+            bad = true;
+            break;
+          }
+          const df inv = df_recip(df{dk2.x, dk2.y});
+          if (tid == 0) s_inv[k - k0] = make_float2(inv.h, inv.l);
+          // panel columns j = k+1 .. k1-1, rows i = j .. bs
+          const int pc = k1 - 1 - k, prow = bs - k;
+          for (int e = tid; e < pc * prow; e += THREADS) {
+            const int jj = e / prow, i = k + 1 + (e - jj * prow), jc = k + 1 + jj;
+            if (jc > i) continue;
+            const float2 a = Sf[tri0(i, k)], b = Sf[tri0(jc, k)], c = Sf[tri0(i, jc)];
+            const df r = df_sub_acc(df{c.x, c.y},
+                                    df_mul(df_mul(df{a.x, a.y}, inv), df{b.x, b.y}));
+            Sf[tri0(i, jc)] = make_float2(r.h, r.l);
+          }
+          __syncthreads();
         }
-        const df inv = df_recip(df{dk2.x, dk2.y});
-        const int Tn = bs - 1 - k;               // trailing matrix rows k+1 .. bs-1
+        if (bad || k1 >= bs) break;
+        const int np = k1 - k0;
+        // W_jk = S_jk / d_k for the trailing columns j = k1 .. bs-1
+        for (int e = tid; e < (bs - k1) * PW; e += THREADS) {
+          const int jr = e / PW, q = e - jr * PW;
+          float2 w = make_float2(0.0f, 0.0f);
+          if (q < np) {
+            const float2 sjk = Sf[tri0(k1 + jr, k0 + q)], iv = s_inv[q];
+            const df t = df_mul(df{sjk.x, sjk.y}, df{iv.x, iv.y});
+            w = make_float2(t.h, t.l);
+          }
+          Wp[e] = w;
+        }
+        __syncthreads();
+        const int Tn = bs - k1;                  // trailing rows/columns k1 .. bs-1
         const int ntri = Tn * (Tn + 1) / 2;
         const int ntr = ntri + Tn;               // plus the bordered row's Tn entries
-        // two entries per thread and pass, both loaded before either is
-        // stored (the step reads column k, which it does not write)
-        auto entry = [&](int l, int& i, int& j) {
+        for (int l = tid; l < ntr; l += THREADS) {
+          int i, jr;
           if (l < ntri) {
             int ii = (int)((sqrtf(8.0f * (float)l + 1.0f) - 1.0f) * 0.5f);
             while (ii * (ii + 1) / 2 > l) --ii;
             while ((ii + 1) * (ii + 2) / 2 <= l) ++ii;
-            i = k + 1 + ii;
-            j = k + 1 + (l - ii * (ii + 1) / 2);
+            i = k1 + ii;
+            jr = l - ii * (ii + 1) / 2;
           } else {
             i = bs;
-            j = k + 1 + (l - ntri);
+            jr = l - ntri;
           }
-        };
-        for (int l = tid; l < ntr; l += 2 * THREADS) {
-          const int l2 = l + THREADS;
-          const bool two = l2 < ntr;
-          int i0, j0, i1 = 0, j1 = 0;
-          entry(l, i0, j0);
-          if (two) entry(l2, i1, j1);
-          const float2 a0 = Sf[tri0(i0, k)], b0 = Sf[tri0(j0, k)], c0 = Sf[tri0(i0, j0)];
-          float2 a1 = a0, b1 = b0, c1 = c0;
-          if (two) {
-            a1 = Sf[tri0(i1, k)];
-            b1 = Sf[tri0(j1, k)];
-            c1 = Sf[tri0(i1, j1)];
+          const float2* si = Sf + tri0(i, k0);
+          const float4* wj = (const float4*)(Wp + jr * PW);
+          const float2 sij = Sf[tri0(i, k1 + jr)];
+          df r = {sij.x, sij.y};
+#pragma unroll
+          for (int q2 = 0; q2 < PW / 2; ++q2) {
+            const float4 w2 = wj[q2];
+            if (2 * q2 < np) {
+              const float2 a0 = si[2 * q2];
+              r = df_sub_acc(r, df_mul(df{a0.x, a0.y}, df{w2.x, w2.y}));
+            }
+            if (2 * q2 + 1 < np) {
+              const float2 a1 = si[2 * q2 + 1];
+              r = df_sub_acc(r, df_mul(df{a1.x, a1.y}, df{w2.z, w2.w}));
+            }
           }
-          const df r0 = df_sub_acc(df{c0.x, c0.y},
-                                   df_mul(df_mul(df{a0.x, a0.y}, inv), df{b0.x, b0.y}));
-          const df r1 = df_sub_acc(df{c1.x, c1.y},
-                                   df_mul(df_mul(df{a1.x, a1.y}, inv), df{b1.x, b1.y}));
-          Sf[tri0(i0, j0)] = make_float2(r0.h, r0.l);
-          if (two) Sf[tri0(i1, j1)] = make_float2(r1.h, r1.l);
+          Sf[tri0(i, k1 + jr)] = make_float2(r.h, r.l);
         }
         __syncthreads();
       }
