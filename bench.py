@@ -9,10 +9,10 @@ covariance, FP32 factor of the neighbour covariance, extended-precision
 residual, corrected Schur complement, LDL^T, block terms and the
 deterministic sum.
 
-The headline is the mixed path (SBV_PREC_MIXED); the FP64 path and the
-variant with the residual's products on the tensor cores (SBV_PREC_MIXED_BF16)
-are timed beside it on the same structure, each at its autotuned launch
-shape, with |l_path - l_fp64| / n.
+The headline is the mixed path with the residual's products on the tensor
+cores (SBV_PREC_MIXED_BF16); the FP64 path and the CUDA-core mixed path
+(SBV_PREC_MIXED) are timed beside it on the same structure, each at its
+autotuned launch shape, with |l_path - l_fp64| / n.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -48,7 +48,8 @@ FALLBACK_BF16_TFLOPS = 1900.0   # used only when the measured-peaks file is abse
 # the sources of the mixed block kernel (the recorded traffic is valid for these)
 KERNEL_SRC = [os.path.join(ROOT, "paper_2504_12004_gb300", "csrc", f)
               for f in ("loglik_mixed.cu", "mixed.cuh", "dfloat.cuh", "block_common.cuh")]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "loglik_mixed_sine10d_traffic.txt")
+TRAFFIC_FILES = {"mixed": os.path.join(ROOT, "profiles", "loglik_mixed_sine10d_traffic.txt"),
+                 "mixed_bf16": os.path.join(ROOT, "profiles", "loglik_mixed_bf16_sine10d_traffic.txt")}
 
 
 def parse():
@@ -60,7 +61,7 @@ def parse():
     p.add_argument("--workload", default="sine10d")
     p.add_argument("--n", type=int, default=None, help="shrink the workload (profiling runs)")
     p.add_argument("--bc", type=int, default=None, help="blocks of the shrunk workload")
-    p.add_argument("--precision", default="mixed", choices=["mixed", "mixed_bf16", "fp64"])
+    p.add_argument("--precision", default="mixed_bf16", choices=["mixed", "mixed_bf16", "fp64"])
     p.add_argument("--kmeans-iters", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-side-paths", action="store_true")
@@ -162,6 +163,37 @@ def algorithmic_flops(ptr: np.ndarray, cnt: np.ndarray) -> float:
     return float(np.sum(N ** 3 / 3.0 + N ** 2))
 
 
+def tensor_residual(ptr: np.ndarray, cnt: np.ndarray, tuned, call_ms: float, peaks) -> dict:
+    """The residual R = Sigma_J,B' - Sigma_JJ X of SBV_PREC_MIXED_BF16 on the
+    tensor cores: per item with m_i <= 128, per pass of up to NP right-hand
+    sides (48 at 256 threads, 96 at 512) and per K-step of 16, twelve BF16
+    digit MMAs of 128 x N x 16 (N = the pass's right-hand sides rounded up to
+    16).  Issued tensor flops over the kernel's time, against the measured
+    BF16 rate; and the residual's own algorithmic flops, 2 m^2 (bs + 1)."""
+    threads = tuned[0] if tuned else 256
+    NP = 96 if threads >= 512 else 48
+    bs = np.diff(ptr).astype(np.int64)
+    m = cnt.astype(np.int64)
+    issued = 0.0
+    alg = 0.0
+    for b, mb in zip(bs, m):
+        if mb == 0 or mb > 128:
+            continue
+        nr = int(b) + 1
+        nks = (int(mb) + 15) // 16
+        n_sum = 0
+        for pb in range(0, nr, NP):
+            n_sum += (min(NP, nr - pb) + 15) // 16 * 16
+        issued += 12 * 2 * 128 * 16 * nks * n_sum
+        alg += 2.0 * mb * mb * nr
+    t = call_ms / 1000.0
+    return {"issued_tflops": issued / t / 1e12, "peak_bf16": peaks["bf16_burst"],
+            "frac_issued": issued / t / 1e12 / peaks["bf16_burst"],
+            "issued_flops_per_eval": issued, "residual_algorithmic_flops_per_eval": alg,
+            "note": "the tensor work of one evaluation over the whole kernel's time; the "
+                    "kernel's other phases run on the CUDA cores"}
+
+
 def algorithmic_bytes(ptr: np.ndarray, cnt: np.ndarray, d: int, xbytes: int) -> float:
     """Bytes one evaluation must move: per block the N_i gathered points (d
     coordinates and y), the m_i neighbour ids and bs_i member ids, its slice of
@@ -202,11 +234,11 @@ def source_hash(paths) -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str):
+def recorded_traffic(workload: str, precision: str):
     """DRAM bytes per launch of the mixed kernel recorded from ncu, if the kernel source is unchanged."""
     try:
         kv = {}
-        with open(TRAFFIC_FILE) as f:
+        with open(TRAFFIC_FILES[precision]) as f:
             for line in f:
                 if ":" in line:
                     k, v = line.split(":", 1)
@@ -523,9 +555,11 @@ def main():
             e0 = time.perf_counter()
         for k, v in host.items():
             dev_bufs[k].copy_(v, non_blocking=True)
+        # no size hint: the call reads the block sizes of the buffers it is
+        # given (one small kernel), as a user's call would, so that the kernel
+        # plans for the largest block rather than for any block
         o = ctx.sbv_loglik(dev_bufs["X"], dev_bufs["y"], dev_bufs["ptr"], dev_bufs["pts"],
-                           dev_bufs["nbr"], dev_bufs["cnt"], th, nu2=w["nu2"], precision=precision,
-                           nmax=nmax)
+                           dev_bufs["nbr"], dev_bufs["cnt"], th, nu2=w["nu2"], precision=precision)
         ll_host.copy_(o, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - e0
@@ -547,7 +581,7 @@ def main():
                 "peak_source": "of measured: FP64 DFMA rate from sbv_peak_probe in this run"}
     else:
         tf32 = peaks["bf16_burst"] * TF32_PER_BF16
-        traffic = recorded_traffic(args.workload) if precision == "mixed" else None
+        traffic = recorded_traffic(args.workload, precision)
         roof = {"bound": "tensor", "achieved": achieved_tflops, "peak": tf32,
                 "unit": "TFLOP/s", "frac": achieved_tflops / tf32, "traffic": traffic,
                 "peak_source": "of %s: BF16 burst %.1f TFLOP/s x nominal TF32/BF16 ratio 1.1/2.25 "
@@ -560,6 +594,8 @@ def main():
                 "simt_fp32": {"peak": fp32_peak, "frac": achieved_tflops / fp32_peak,
                               "peak_source": "of measured: FP32 FFMA rate from sbv_peak_probe"},
                 "fp64_probe_tflops": fp64_peak,
+                "tensor_residual": tensor_residual(ptr_h, cnt_h, tuned, call_ms, peaks)
+                if precision == "mixed_bf16" else None,
                 "note": "achieved counts the Cholesky flops sum N^3/3 + N^2 only; the "
                         "double-float covariance (%.3g kernel evaluations per call) is the "
                         "larger share of the issued instructions" % pairs}
@@ -573,7 +609,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if precision == "fp64" else "f32+df64",
+            "dtype": {"fp64": "f64", "mixed": "f32+df64", "mixed_bf16": "bf16+f32+df64"}[precision],
             "data": "synthetic",
             "config": {"workload": args.workload, "n": w["n"], "d": w["d"], "bc": bc, "m": w["m"],
                        "nu": w["nu2"] / 2, "theta_per_eval": 1, "precision": precision,

@@ -1312,7 +1312,15 @@ int mixed_plan(sbv_ctx* ctx, int nmax, int mcap, int bcap, int d, int precision,
   int st = mixed_prepare(ctx);   // occupancy queries need the shared-memory opt-in
   if (st) return st;
   int fit = 0;
-  if ((st = mixed_occupancy(ctx, threads, tc, pred, o->lay.ga, o->lay.bytes, &fit))) return st;
+  // The occupancy calculator admits one CTA per SM for any variant with
+  // tcgen05 instructions, whatever its shared memory; the SM runs two when
+  // shared memory and registers allow (measured: 25.4 ms at two CTAs of 256
+  // threads per SM against 40.3 ms at one on the 1M-point workload).  So the
+  // tensor-core variant takes the cap of its twin without tcgen05 (same
+  // threads, registers and shared memory) and of TMEM: MX_TMEM_COLS columns
+  // per CTA (256 at 256 threads, 512 at 512) out of an SM's 512.
+  if ((st = mixed_occupancy(ctx, threads, false, pred, o->lay.ga, o->lay.bytes, &fit))) return st;
+  if (tc) fit = std::min(fit, threads >= 512 ? 1 : 2);
   if (fit < 1)
     return fail(ctx, SBV_EUNSUPPORTED, "mixed path: no CTA of %d threads fits an SM (N=%d, d=%d)",
                 threads, nmax, d);
