@@ -622,6 +622,9 @@ loglik_mixed_kernel(MixedArgs P) {
     float* colX = colC + lay.ncap + 2;           // grid unit of X^ per right-hand side
     float* Qg = Rg;                              // L^{-1} R for every column, global
     const bool tc = TC && mb <= 128;
+    // with tc, the products Sigma_BJ X^ of the conditional system also run on
+    // the tensor cores (a second pass with the B rows of Sigma as A)
+    const bool tcg = tc && bs <= 128 && mb > 0;   // (mb = 0: no products to take)
     // X <- X^ on a 24-bit fixed-point grid per column (unit 2^(ex - 24),
     // |X| < 2^ex): every later use (residual, conditional system) sees the
     // same X^, whose digits the tensor cores take exactly
@@ -668,12 +671,17 @@ loglik_mixed_kernel(MixedArgs P) {
       const int am = tid >> 1, ak = (tid & 1) * 8;   // A digits: row am, k ak..ak+7
       const float sc8 = ldexpf(1.0f, 8 - eA);
       float2 sv[8];
+      // target 0: A = Sigma_JJ (rows 0 .. mb-1 of Sigma), result R into Rg;
+      // target 1: A = Sigma_BJ (rows mb .. mb+bs-1), result G = Sigma_BJ X^,
+      // written as the partial conditional system Sigma_BB - G (lower triangle)
+      for (int tgt = 0; tgt < (tcg ? 2 : 1); ++tgt) {
+      const int ro = tgt ? mb : 0, arows = tgt ? bs : mb;
       auto load_sv = [&](int ks) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int kk = ks * 16 + ak + j;
-          sv[j] = (tid < 256 && am < mb && kk < mb) ? S[(size_t)kk * N + am]
-                                                    : make_float2(0.0f, 0.0f);
+          sv[j] = (tid < 256 && am < arows && kk < mb) ? S[(size_t)kk * N + ro + am]
+                                                       : make_float2(0.0f, 0.0f);
         }
       };
       for (int pb = 0; pb < nr; pb += MX_NP) {
@@ -802,7 +810,7 @@ loglik_mixed_kernel(MixedArgs P) {
 #pragma unroll
               for (int c = 0; c < 16; ++c) acc[c] = df_add_f(acc[c], gv[c] * wg);
             }
-            if (k < mb) {
+            if (tgt == 0 && k < mb) {
 #pragma unroll
               for (int c = 0; c < 16; ++c) {
                 const int n = 16 * ch + c, r = pb + n;
@@ -814,12 +822,26 @@ loglik_mixed_kernel(MixedArgs P) {
                   Rg[(size_t)r * xs + k] = __fadd_rn(rv.h, rv.l);
                 }
               }
+            } else if (tgt == 1 && k < bs) {
+              // row a = k of B: Sp[a][r] = Sigma_BB[a][r] - G[a][r] for r <= a
+#pragma unroll
+              for (int c = 0; c < 16; ++c) {
+                const int n = 16 * ch + c, r = pb + n;
+                if (n < npc && r <= k) {
+                  const float scl = ldexpf(colX[r], eA + 8);
+                  const df dd = {acc[c].h * scl, acc[c].l * scl};
+                  const float2 v = S[(size_t)(mb + r) * N + (mb + k)];
+                  const df sv2 = df_sub_acc(df{v.x, v.y}, dd);
+                  Spg[tri0(k, r)] = make_float2(sv2.h, sv2.l);
+                }
+              }
             }
           }
         }
         umma::fence_before_sync();
         __syncthreads();   // TMEM and the digit tiles are free for the next pass
       }
+      }   // targets
     }
     // right-hand sides per column block: as many as the residual block's
     // room holds (at most 64), split evenly
@@ -933,6 +955,24 @@ loglik_mixed_kernel(MixedArgs P) {
           if (ar < r) continue;
           // prediction needs the diagonal and the bordered row only
           if (PRED && ar != r && ar != bs) continue;
+          if (tcg && ar < bs) {
+            // Sigma_BB - Sigma_BJ X^ came from the tensor cores: subtract X^[a] . R[r]
+            const float* xa = Xr + (size_t)ar * xs;
+            const float* rr = Rb + (size_t)c * xs;
+            float d1 = 0.0f;
+            for (int k = 0; k < mb4; k += 4) {
+              const float4 a4 = *(const float4*)(xa + k);
+              const float4 r4 = *(const float4*)(rr + k);
+              d1 = fmaf(a4.x, r4.x, d1);
+              d1 = fmaf(a4.y, r4.y, d1);
+              d1 = fmaf(a4.z, r4.z, d1);
+              d1 = fmaf(a4.w, r4.w, d1);
+            }
+            const float2 sp = Spg[tri0(ar, r)];
+            const df sres = df_add_f(df{sp.x, sp.y}, -d1);
+            Spg[tri0(ar, r)] = make_float2(sres.h, sres.l);
+            continue;
+          }
           const float2 v0 = ar < bs ? S[(size_t)(mb + r) * N + (mb + ar)] : yv[mb + r];
           df e = {v0.x, v0.y};
           float d1 = 0.0f;
