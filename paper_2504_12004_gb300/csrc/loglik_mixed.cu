@@ -625,6 +625,11 @@ loglik_mixed_kernel(MixedArgs P) {
     // with tc, the products Sigma_BJ X^ of the conditional system also run on
     // the tensor cores (a second pass with the B rows of Sigma as A)
     const bool tcg = tc && bs <= 128 && mb > 0;   // (mb = 0: no products to take)
+    // right-hand sides the tensor-core passes take: all, except a last pass
+    // of at most 16 columns, which the CUDA cores take instead of a whole
+    // round of digit splits
+    int ntc = nr;
+    if (nr > MX_NP && nr % MX_NP != 0 && nr % MX_NP <= 16) ntc = nr - nr % MX_NP;
     // X <- X^ on a 24-bit fixed-point grid per column (unit 2^(ex - 24),
     // |X| < 2^ex): every later use (residual, conditional system) sees the
     // same X^, whose digits the tensor cores take exactly
@@ -684,8 +689,8 @@ loglik_mixed_kernel(MixedArgs P) {
                                                        : make_float2(0.0f, 0.0f);
         }
       };
-      for (int pb = 0; pb < nr; pb += MX_NP) {
-        const int npc = min(MX_NP, nr - pb);
+      for (int pb = 0; pb < ntc; pb += MX_NP) {
+        const int npc = min(MX_NP, ntc - pb);
         const int nn = (npc + 15) & ~15;   // MMA N
         load_sv(0);
         for (int ks = 0; ks < nks; ++ks) {
@@ -852,33 +857,35 @@ loglik_mixed_kernel(MixedArgs P) {
     for (int cb = 0; cb < nr; cb += W) {
       const int nc = min(W, nr - cb);
       // 6a. Rb[c][k] = Sigma_{J,B'}[k][cb+c] - sum_k' Sigma_JJ[k][k'] X[cb+c][k']
-      if (tc) {
-        // the tensor-core residual of these columns, computed above
-        for (int e = tid; e < nc * (mb4 >> 2); e += THREADS) {
-          const int c = e / (mb4 >> 2), k = (e - c * (mb4 >> 2)) * 4;
-          *(float4*)(Rb + (size_t)c * xs + k) = *(const float4*)(Rg + (size_t)(cb + c) * xs + k);
-        }
-      } else {
+      // columns [0, ctc) of the block come from the tensor-core pass, the
+      // rest from the CUDA cores
+      const int ctc = tc ? max(0, min(nc, ntc - cb)) : 0;
+      for (int e = tid; e < ctc * (mb4 >> 2); e += THREADS) {
+        const int c = e / (mb4 >> 2), k = (e - c * (mb4 >> 2)) * 4;
+        *(float4*)(Rb + (size_t)c * xs + k) = *(const float4*)(Rg + (size_t)(cb + c) * xs + k);
+      }
+      if (ctc < nc) {
       // CUDA cores: thread (k, c0) streams row k of Sigma_JJ itself
       // (S[kp N + k], coalesced over the warp's rows k) with the next four
       // loads in flight, and keeps eight columns' accumulators in registers;
-      // no CTA barrier inside
+      // no CTA barrier inside.  Columns cofs + c of the block, c < ncx.
       {
-        const int ngrp = (nc + 7) >> 3;   // groups of eight columns
+        const int cofs = ctc, ncx = nc - ctc;
+        const int ngrp = (ncx + 7) >> 3;   // groups of eight columns
         for (int t0 = 0; t0 < ngrp * mb; t0 += THREADS) {
           const int tk = t0 + tid;
           // tasks whose eight columns all lie past the block do nothing
-          if (tk < ngrp * mb && (tk / mb) * 8 < nc) {
+          if (tk < ngrp * mb && (tk / mb) * 8 < ncx) {
             const int k = tk % mb, c0 = (tk / mb) * 8;
             float Cq[8], ahi[8];
             df atot[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-              Cq[q] = c0 + q < nc ? colC[cb + c0 + q] : 1.0f;
+              Cq[q] = c0 + q < ncx ? colC[cb + cofs + c0 + q] : 1.0f;
               ahi[q] = 0.0f;
               atot[q] = {0.0f, 0.0f};
             }
-            const float* xc = Xr + (size_t)(cb + c0) * xs;
+            const float* xc = Xr + (size_t)(cb + cofs + c0) * xs;
             const float2* sk = S + k;
             float2 nx[4];
 #pragma unroll
@@ -900,7 +907,7 @@ loglik_mixed_kernel(MixedArgs P) {
               for (int q = 0; q < 8; ++q) {
                 // columns past the block read column cb + c0 (c0 < nc: in
                 // bounds) and are discarded
-                const float4 x4 = *(const float4*)(xc + (size_t)(c0 + q < nc ? q : 0) * xs + kp);
+                const float4 x4 = *(const float4*)(xc + (size_t)(c0 + q < ncx ? q : 0) * xs + kp);
                 const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -923,12 +930,12 @@ loglik_mixed_kernel(MixedArgs P) {
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-              const int r = cb + c0 + q;
-              if (c0 + q < nc) {
+              const int r = cb + cofs + c0 + q;
+              if (c0 + q < ncx) {
                 const float2 v = r < bs ? S[(size_t)(mb + r) * N + k] : yv[k];
                 df rv = df_sub_acc(df{v.x, v.y}, df{ahi[q], 0.0f});
                 rv = df_sub_acc(rv, atot[q]);
-                Rb[(size_t)(c0 + q) * xs + k] = __fadd_rn(rv.h, rv.l);
+                Rb[(size_t)(cofs + c0 + q) * xs + k] = __fadd_rn(rv.h, rv.l);
               }
             }
           }
@@ -955,7 +962,7 @@ loglik_mixed_kernel(MixedArgs P) {
           if (ar < r) continue;
           // prediction needs the diagonal and the bordered row only
           if (PRED && ar != r && ar != bs) continue;
-          if (tcg && ar < bs) {
+          if (tcg && ar < bs && r < ntc) {
             // Sigma_BB - Sigma_BJ X^ came from the tensor cores: subtract X^[a] . R[r]
             const float* xa = Xr + (size_t)ar * xs;
             const float* rr = Rb + (size_t)c * xs;
