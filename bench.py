@@ -17,7 +17,11 @@ autotuned launch shape, with |l_path - l_fp64| / n.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on host
-cores on a bounded sample of the same workload.
+cores on a bounded sample of the same workload.  `--mle-surrogate` runs the
+surrogate-assisted maximum-likelihood comparison on the workload instead
+(exact BFGS runs produce `--pairs` training pairs; from `--later-starts`
+further starts, exact-only BFGS against BFGS with the network's proposals)
+and prints its own JSON line.
 """
 from __future__ import annotations
 
@@ -69,6 +73,12 @@ def parse():
     p.add_argument("--launch", default="graph", choices=["graph", "direct"],
                    help="time graph replays (default) or direct sbv_loglik calls")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--mle-surrogate", action="store_true",
+                   help="surrogate-assisted MLE on the workload instead of the evaluation bench")
+    p.add_argument("--pairs", type=int, default=20000,
+                   help="(theta, l) pairs of exact MLE runs that train the surrogate")
+    p.add_argument("--later-starts", type=int, default=2,
+                   help="starts run both exact-only and with the surrogate")
     return p.parse_args()
 
 
@@ -389,6 +399,75 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- our arm
+def lhs(rs, n: int, lo: np.ndarray, hi: np.ndarray) -> np.ndarray:
+    """n points of a Latin hypercube in the box [lo, hi]."""
+    P = np.stack([rs.permutation(n) for _ in range(len(lo))], 1)
+    return lo + (P + rs.uniform(size=(n, len(lo)))) / n * (hi - lo)
+
+
+def run_mle_surrogate(args, ctx, X, y, ptr, pts, nbr, cnt, nmax, w):
+    """Surrogate-assisted MLE (the network proposes theta inside the BFGS loop
+    and at restarts; the exact likelihood judges every row).  Exact BFGS runs
+    from a Latin hypercube of starts around (var y, 0.01 var y, 0.5, ...)
+    produce `--pairs` (log theta, l) pairs; from each of `--later-starts`
+    further starts, BFGS runs once exact-only and once with the network
+    trained on those pairs.  Prints one JSON line with the exact rows, the
+    optima and the wall times of both arms."""
+    from paper_2504_12004_gb300 import Mlp
+    from paper_2504_12004_gb300._lib import mle_opts, surrogate_opts
+    d = X.shape[1]
+    p = d + 2
+    lower = np.r_[1e-2, 1e-6, np.full(d, 1e-2)]
+    upper = np.r_[1e2, 1e1, np.full(d, 1e1)]
+    vy = float(np.var(w["y"]))
+    centre = np.log(np.r_[vy, 0.01 * vy, np.full(d, 0.5)])
+    lo = np.maximum(centre - 1.5, np.log(lower))
+    hi = np.minimum(centre + 1.5, np.log(upper))
+    S0 = 64
+    starts = np.exp(lhs(np.random.default_rng(123), S0 + args.later_starts, lo, hi))
+    prec = args.precision
+    hu, hl, runs = [], [], []
+    t0 = time.perf_counter()
+    i = 0
+    while sum(len(h) for h in hl) < args.pairs and i < S0:
+        left = args.pairs - sum(len(h) for h in hl)
+        th, res, (u_, l_) = ctx.sbv_mle(X, y, ptr, pts, nbr, cnt, starts[i], lower, upper,
+                                        mle_opts(precision=prec, max_evals=min(4000, max(left, 40))),
+                                        nmax=nmax, history=4000)
+        hu.append(u_)
+        hl.append(l_)
+        runs.append(dict(ll=res.ll, evals=res.evals, converged=res.converged))
+        i += 1
+    t_pairs = time.perf_counter() - t0
+    prior = (np.concatenate(hu), np.concatenate(hl))
+    later = starts[S0:]
+    arms = {}
+    for name in ("exact", "surrogate"):
+        t0 = time.perf_counter()
+        if name == "exact":
+            res = [ctx.sbv_mle(X, y, ptr, pts, nbr, cnt, st_, lower, upper,
+                               mle_opts(precision=prec, max_evals=4000), nmax=nmax)[1]
+                   for st_ in later]
+        else:
+            net = Mlp(ctx, p, seed=1)
+            _, res = ctx.sbv_mle_multistart(X, y, ptr, pts, nbr, cnt, later, lower, upper,
+                                            mle_opts(precision=prec, max_evals=4000), mlp=net,
+                                            sopts=surrogate_opts(exact_starts=0), nmax=nmax,
+                                            prior=prior)
+        arms[name] = dict(seconds=round(time.perf_counter() - t0, 2),
+                          rows=[int(r.evals) for r in res], ll=[float(r.ll) for r in res],
+                          iterations=[int(r.iterations) for r in res],
+                          converged=[int(r.converged) for r in res],
+                          proposals_won=[int(r.proposals_won) for r in res])
+    e, s_ = arms["exact"], arms["surrogate"]
+    print(json.dumps({
+        "mode": "mle_surrogate", "workload": args.workload, "n": int(X.shape[0]), "d": d,
+        "precision": prec, "pairs": int(len(prior[1])), "pair_runs": runs,
+        "pairs_seconds": round(t_pairs, 1), "exact": e, "surrogate": s_,
+        "rows_ratio": round(sum(s_["rows"]) / max(1, sum(e["rows"])), 3),
+        "delta_ll": [round(a - b, 4) for a, b in zip(s_["ll"], e["ll"])]}), flush=True)
+
+
 def main():
     args = parse()
     if args.oracle_worker:
@@ -441,6 +520,9 @@ def main():
         ctx.sbv_autotune(X, y, ptr, pts, nbr, cnt, th, nu2=w["nu2"],
                          precision=args.precision, nmax=nmax)
         tuned = ctx.sbv_tuned_shape(args.precision, nmax, X.shape[1])
+    if args.mle_surrogate:
+        run_mle_surrogate(args, ctx, X, y, ptr, pts, nbr, cnt, nmax, w)
+        return
     graph = None
     if args.launch == "graph":
         graph = ctx.sbv_loglik_graph_create(X, y, ptr, pts, nbr, cnt, B=1, nu2=w["nu2"],

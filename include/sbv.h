@@ -655,6 +655,7 @@ typedef struct {
   int32_t converged;     /* 1 gain < ftol, 2 stationary, 0 budget exhausted */
   int32_t grad_evals;    /* analytic gradients evaluated (each also one row of evals;
                             about 2.4 FP64 likelihood rows of work) */
+  int32_t proposals_won; /* line-search calls that a network proposal won */
 } sbv_mle_result;
 
 /* theta0, theta_out: host, 2 + d.  opts may be NULL (defaults above).  If
@@ -676,9 +677,15 @@ typedef struct {
   float lr;              /* Adam step size (1e-3) */
   int32_t ascent_starts; /* points of the gradient ascent on the network (256) */
   int32_t ascent_iters;  /* sign-gradient steps of 1/200 of the data's box (300) */
-  int32_t candidates;    /* distinct maximisers judged by the exact likelihood (8) */
+  int32_t candidates;    /* distinct maximisers judged by the exact likelihood at a restart
+                            (8; 0: restarts run from their given point) */
   double ascent_radius;  /* ascent points drawn uniformly within this max-norm radius (1.0) */
   uint64_t seed;         /* SplitMix64 seed of those draws and of the mini-batches (1) */
+  int32_t step_candidates; /* network maximisers added to every line-search call (2; 0: none) */
+  double step_radius;    /* initial trust radius of those, max-norm in log theta (0.5); it
+                            doubles up to ascent_radius when a proposal wins the call and
+                            halves down to step_radius / 64 when none does */
+  int32_t refit_every;   /* accepted iterations between refits inside the loop (10) */
 } sbv_surrogate_opts;
 
 /*
@@ -689,16 +696,27 @@ typedef struct {
  * (inputs: log theta per coordinate, target: l), climbs it from
  * `ascent_starts` points around start i, and evaluates the best distinct
  * `candidates` maximisers together with start i in one exact call; BFGS then
- * runs from the best of them.  theta_out (S x (2 + d)) and results (S) report
- * each start; results[i].evals includes the proposal call.  The network keeps
- * its last fit.  sopts may be NULL (defaults above).
+ * runs from the best of them.  Inside BFGS (starts i >= exact_starts) every
+ * line-search call also evaluates `step_candidates` maximisers of the
+ * network within the trust radius of the iterate (the network refitted to
+ * the grown history every `refit_every` accepted iterations); the best exact
+ * value of the call is the next iterate, whichever row it is.  theta_out
+ * (S x (2 + d)) and results (S) report each start; results[i].evals includes
+ * the proposal rows.  The network keeps its last fit.  sopts may be NULL
+ * (defaults above).  prior_u (host, prior_n x (2 + d), log theta) and
+ * prior_l (prior_n) are (log theta, l) pairs of earlier runs on the same
+ * problem (sbv_mle's history): they join the history before the first start
+ * and train the network like this call's own pairs; they are not counted in
+ * results[i].evals.  prior_n = 0 with NULL pointers for none; SBV_EINVAL for
+ * prior_n < 0 or missing pointers.
  */
 int sbv_mle_multistart(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t n,
                        int32_t d, const int64_t* ptr, const int32_t* pts, const int32_t* nbr,
                        const int32_t* cnt, int64_t bc, int32_t m, int32_t nmax,
                        const double* starts, int32_t S, const double* lower,
                        const double* upper, const sbv_mle_opts* opts, sbv_mlp* mlp,
-                       const sbv_surrogate_opts* sopts, double* theta_out,
+                       const sbv_surrogate_opts* sopts, const double* prior_u,
+                       const double* prior_l, int64_t prior_n, double* theta_out,
                        sbv_mle_result* results, void* stream);
 
 #ifdef __cplusplus

@@ -35,7 +35,8 @@ class MleOpts(C.Structure):
 class MleResult(C.Structure):
     """sbv_mle_result"""
     _fields_ = [("ll", C.c_double), ("evals", C.c_int32), ("calls", C.c_int32),
-                ("iterations", C.c_int32), ("converged", C.c_int32), ("grad_evals", C.c_int32)]
+                ("iterations", C.c_int32), ("converged", C.c_int32), ("grad_evals", C.c_int32),
+                ("proposals_won", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -45,7 +46,9 @@ class SurrogateOpts(C.Structure):
     """sbv_surrogate_opts"""
     _fields_ = [("exact_starts", C.c_int32), ("train_steps", C.c_int32), ("batch", C.c_int32),
                 ("lr", C.c_float), ("ascent_starts", C.c_int32), ("ascent_iters", C.c_int32),
-                ("candidates", C.c_int32), ("ascent_radius", C.c_double), ("seed", C.c_uint64)]
+                ("candidates", C.c_int32), ("ascent_radius", C.c_double), ("seed", C.c_uint64),
+                ("step_candidates", C.c_int32), ("step_radius", C.c_double),
+                ("refit_every", C.c_int32)]
 
 
 def mle_opts(max_evals=4000, fd_step=1e-3, ftol=1e-10, max_step=1.0, line_points=8,
@@ -57,9 +60,12 @@ def mle_opts(max_evals=4000, fd_step=1e-3, ftol=1e-10, max_step=1.0, line_points
 
 
 def surrogate_opts(exact_starts=4, train_steps=4000, batch=512, lr=1e-3, ascent_starts=256,
-                   ascent_iters=300, candidates=8, ascent_radius=1.0, seed=1) -> SurrogateOpts:
+                   ascent_iters=300, candidates=8, ascent_radius=1.0, seed=1, step_candidates=2,
+                   step_radius=0.5, refit_every=10) -> SurrogateOpts:
+    """candidates: restart proposals (0: none); step_candidates: proposals in every line search."""
     return SurrogateOpts(exact_starts, train_steps, batch, lr, ascent_starts, ascent_iters,
-                         candidates, ascent_radius, seed)
+                         candidates, ascent_radius, seed, step_candidates, step_radius,
+                         refit_every)
 
 # (name, restype, argtypes) of every exported symbol
 _P, _I32, _I64, _U64, _D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
@@ -119,7 +125,8 @@ SIGNATURES = {
     "sbv_mle": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64, _I32, _I32, _P, _P,
                           _P, _P, _P, _P, _P, _P, _I64, C.POINTER(_I64), _P]),
     "sbv_mle_multistart": (C.c_int, [_P, _P, C.c_int, _P, _I64, _I32, _P, _P, _P, _P, _I64, _I32,
-                                     _I32, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _P]),
+                                     _I32, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P,
+                                     _P]),
 }
 
 
@@ -425,20 +432,30 @@ class Context:
         return out, res
 
     def sbv_mle_multistart(self, X, y, ptr, pts, nbr, cnt, starts, lower=None, upper=None,
-                           opts=None, mlp=None, sopts=None, nmax: int = 0, stream=None):
-        """MLE from every row of starts; returns (thetas, [MleResult])."""
+                           opts=None, mlp=None, sopts=None, nmax: int = 0, stream=None,
+                           prior=None):
+        """MLE from every row of starts; returns (thetas, [MleResult]).  prior:
+        (hist_u, hist_l) pairs of earlier runs (sbv_mle's history) that join
+        the history before the first start."""
         st = self._structure(X, y, ptr, pts, nbr, cnt)
         d = st[4]
         S0 = _host_f64(starts, "starts").reshape(-1, 2 + d)
         lo = None if lower is None else _host_f64(lower, "lower").reshape(2 + d)
         hi = None if upper is None else _host_f64(upper, "upper").reshape(2 + d)
+        pu = pl = None
+        if prior is not None:
+            pu = _host_f64(prior[0], "prior_u").reshape(-1, 2 + d)
+            pl = _host_f64(prior[1], "prior_l").reshape(-1)
+            if len(pl) != len(pu):
+                raise ValueError("prior_u and prior_l differ in length")
         out = np.empty_like(S0)
         res = (MleResult * len(S0))()
         rc = self.lib.sbv_mle_multistart(self.h, *st, int(nmax), _ptr(S0), len(S0), _ptr(lo), _ptr(hi),
                                          C.byref(opts) if opts is not None else None,
                                          mlp.h if mlp is not None else None,
-                                         C.byref(sopts) if sopts is not None else None, _ptr(out),
-                                         C.cast(res, C.c_void_p), _stream(stream))
+                                         C.byref(sopts) if sopts is not None else None,
+                                         _ptr(pu), _ptr(pl), 0 if pl is None else len(pl),
+                                         _ptr(out), C.cast(res, C.c_void_p), _stream(stream))
         self._check(rc)
         return out, [r for r in res]
 

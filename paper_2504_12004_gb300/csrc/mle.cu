@@ -14,7 +14,10 @@
 // likelihood produced so far -- predicts high likelihood: gradient ascent on
 // the network from points around the given start proposes candidates, one
 // exact call judges them together with the start itself, and the exact BFGS
-// loop continues from the best.  The exact likelihood decides every step.
+// loop continues from the best.  Inside that loop the network proposes too:
+// every line-search call also carries its maximisers within a trust radius
+// of the iterate, refitted to the growing history every few accepted
+// iterations.  The exact likelihood decides every step.
 #include <math.h>
 #include <string.h>
 
@@ -234,8 +237,198 @@ int fd_gradient(Evaluator& E, const Vec& u, double h, Vec& g) {
   return SBV_OK;
 }
 
+// ---- surrogate ------------------------------------------------------------
+struct Surrogate {
+  sbv_mlp* net;
+  std::vector<float> init;     // parameters at creation: every fit starts there
+  float* d_x = nullptr;        // training rows (K x p) and targets (K)
+  float* d_t = nullptr;
+  float* d_q = nullptr;        // ascent points (Q x p), values (Q), gradients (Q x p)
+  float* d_s = nullptr;
+  float* d_g = nullptr;
+  size_t cap_rows = 0, cap_q = 0;
+  // standardisation of the last fit and the box its rows span
+  bool fitted = false;
+  Vec mu, sd, bmin, bmax;
+  double fm = 0.0, fs = 1.0;
+  ~Surrogate() {
+    for (float* q : {d_x, d_t, d_q, d_s, d_g})
+      if (q) cudaFree(q);
+  }
+};
+
+// Fit the network, from its initial parameters, to every finite (log theta,
+// l) pair of the history, standardised per coordinate.  With fewer than 4p
+// pairs nothing is fitted and S.fitted is false.
+int fit(Evaluator& E, Surrogate& S, const sbv_surrogate_opts& so) {
+  sbv_ctx* ctx = E.pb.ctx;
+  const int p = E.p;
+  std::vector<const Vec*> rows;
+  Vec ls;
+  for (size_t i = 0; i < E.hist_l.size(); ++i)
+    if (isfinite(E.hist_l[i])) {
+      rows.push_back(&E.hist_u[i]);
+      ls.push_back(E.hist_l[i]);
+    }
+  const int64_t K = (int64_t)rows.size();
+  S.fitted = false;
+  if (K < 4 * p) return SBV_OK;
+  Vec mu(p, 0.0), sd(p, 0.0), bmin(p, INFINITY), bmax(p, -INFINITY);
+  double fm = 0.0, fs = 0.0;
+  for (int64_t i = 0; i < K; ++i) {
+    for (int j = 0; j < p; ++j) {
+      mu[j] += (*rows[i])[j];
+      bmin[j] = std::min(bmin[j], (*rows[i])[j]);
+      bmax[j] = std::max(bmax[j], (*rows[i])[j]);
+    }
+    fm += ls[i];
+  }
+  for (int j = 0; j < p; ++j) mu[j] /= K;
+  fm /= K;
+  for (int64_t i = 0; i < K; ++i) {
+    for (int j = 0; j < p; ++j) sd[j] += ((*rows[i])[j] - mu[j]) * ((*rows[i])[j] - mu[j]);
+    fs += (ls[i] - fm) * (ls[i] - fm);
+  }
+  for (int j = 0; j < p; ++j) sd[j] = sqrt(sd[j] / K) + 1e-6;
+  fs = sqrt(fs / K) + 1e-12;
+  std::vector<float> hx((size_t)K * p), ht((size_t)K);
+  for (int64_t i = 0; i < K; ++i) {
+    for (int j = 0; j < p; ++j) hx[(size_t)i * p + j] = (float)(((*rows[i])[j] - mu[j]) / sd[j]);
+    ht[i] = (float)((ls[i] - fm) / fs);
+  }
+  if ((size_t)K > S.cap_rows) {
+    if (S.d_x) cudaFree(S.d_x);
+    if (S.d_t) cudaFree(S.d_t);
+    S.d_x = S.d_t = nullptr;
+    S.cap_rows = 0;
+    if (cudaMalloc(&S.d_x, (size_t)K * p * 4) != cudaSuccess || cudaMalloc(&S.d_t, (size_t)K * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, SBV_ENOMEM, "surrogate training rows");
+    }
+    S.cap_rows = (size_t)K;
+  }
+  SBV_CUDA_TRY(ctx, cudaMemcpy(S.d_x, hx.data(), hx.size() * 4, cudaMemcpyHostToDevice));
+  SBV_CUDA_TRY(ctx, cudaMemcpy(S.d_t, ht.data(), ht.size() * 4, cudaMemcpyHostToDevice));
+  int st = sbv_mlp_set_params(S.net, S.init.data(), (int64_t)S.init.size());
+  if (!st) st = sbv_mlp_train(S.net, S.d_x, S.d_t, K, so.train_steps, so.batch, so.lr, so.seed,
+                              nullptr, E.pb.s);
+  if (st) return st;
+  S.mu = mu;
+  S.sd = sd;
+  S.bmin = bmin;
+  S.bmax = bmax;
+  S.fm = fm;
+  S.fs = fs;
+  S.fitted = true;
+  return SBV_OK;
+}
+
+// Gradient ascent on the fitted network from `ascent_starts` points: the
+// centre and points drawn uniformly within max-norm `radius` of it, kept in
+// the box that the training rows span (and the bounds), narrowed to the
+// radius around the centre when `local` is set; sign steps of 1/200 of the
+// box per iteration.  The `k` best maximisers that lie at least `sep` apart
+// (max-norm) are returned, best first.
+int ascend(Evaluator& E, Surrogate& S, const sbv_surrogate_opts& so, const Vec& centre,
+           double radius, bool local, int k, double sep, Mix64& rng, std::vector<Vec>& cand) {
+  sbv_ctx* ctx = E.pb.ctx;
+  const int p = E.p;
+  cudaStream_t s = E.pb.s;
+  cand.clear();
+  if (!S.fitted) return SBV_OK;
+  const int Q = so.ascent_starts;
+  if ((size_t)Q > S.cap_q) {
+    for (float** q : {&S.d_q, &S.d_s, &S.d_g}) {
+      if (*q) cudaFree(*q);
+      *q = nullptr;
+    }
+    S.cap_q = 0;
+    if (cudaMalloc(&S.d_q, (size_t)Q * p * 4) != cudaSuccess || cudaMalloc(&S.d_s, (size_t)Q * 4) != cudaSuccess ||
+        cudaMalloc(&S.d_g, (size_t)Q * p * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, SBV_ENOMEM, "surrogate ascent rows");
+    }
+    S.cap_q = (size_t)Q;
+  }
+  Vec lo(p), hi(p);
+  for (int j = 0; j < p; ++j) {
+    lo[j] = std::max(S.bmin[j], E.lo[j]);
+    hi[j] = std::min(S.bmax[j], E.hi[j]);
+    if (local) {
+      lo[j] = std::max(lo[j], centre[j] - radius);
+      hi[j] = std::min(hi[j], centre[j] + radius);
+    }
+    if (hi[j] < lo[j]) hi[j] = lo[j];
+  }
+  std::vector<Vec> P(Q, Vec(p));
+  for (int q = 0; q < Q; ++q)
+    for (int j = 0; j < p; ++j) {
+      const double v = q == 0 ? centre[j] : centre[j] + radius * (2.0 * rng.uniform() - 1.0);
+      P[q][j] = std::min(std::max(v, lo[j]), hi[j]);
+    }
+  std::vector<float> hq((size_t)Q * p), hs(Q), hg((size_t)Q * p);
+  auto upload = [&]() -> int {
+    for (int q = 0; q < Q; ++q)
+      for (int j = 0; j < p; ++j) hq[(size_t)q * p + j] = (float)((P[q][j] - S.mu[j]) / S.sd[j]);
+    SBV_CUDA_TRY(ctx, cudaMemcpy(S.d_q, hq.data(), hq.size() * 4, cudaMemcpyHostToDevice));
+    return SBV_OK;
+  };
+  int st = 0;
+  for (int it = 0; it < so.ascent_iters; ++it) {
+    if ((st = upload())) return st;
+    if ((st = sbv_mlp_predict(S.net, S.d_q, Q, S.d_s, S.d_g, s))) return st;
+    SBV_CUDA_TRY(ctx, cudaMemcpy(hg.data(), S.d_g, hg.size() * 4, cudaMemcpyDeviceToHost));
+    for (int q = 0; q < Q; ++q)
+      for (int j = 0; j < p; ++j) {
+        const float gj = hg[(size_t)q * p + j];
+        const double step = 0.005 * (hi[j] - lo[j]) * (gj > 0.f ? 1.0 : (gj < 0.f ? -1.0 : 0.0));
+        P[q][j] = std::min(std::max(P[q][j] + step, lo[j]), hi[j]);
+      }
+  }
+  if ((st = upload())) return st;
+  if ((st = sbv_mlp_predict(S.net, S.d_q, Q, S.d_s, nullptr, s))) return st;
+  SBV_CUDA_TRY(ctx, cudaMemcpy(hs.data(), S.d_s, hs.size() * 4, cudaMemcpyDeviceToHost));
+  std::vector<int> order(Q);
+  for (int q = 0; q < Q; ++q) order[q] = q;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a] > hs[b]; });
+  for (int q : order) {
+    if ((int)cand.size() >= k) break;
+    bool far = true;
+    for (const Vec& c : cand) {
+      double dist = 0.0;
+      for (int j = 0; j < p; ++j) dist = std::max(dist, fabs(c[j] - P[q][j]));
+      far = far && dist > sep;
+    }
+    if (far) cand.push_back(P[q]);
+  }
+  return SBV_OK;
+}
+
+// Restart proposal: fit to the whole history, climb from points around the
+// start over the box the history spans.
+int propose(Evaluator& E, Surrogate& S, const sbv_surrogate_opts& so, const Vec& u_start,
+            Mix64& rng, std::vector<Vec>& cand) {
+  int st = fit(E, S, so);
+  if (st) return st;
+  return ascend(E, S, so, u_start, so.ascent_radius, false, so.candidates, 0.05, rng, cand);
+}
+
+// Proposals inside the BFGS loop: every iteration the network's maximisers
+// within the trust radius of the iterate join the line search's call, and
+// the exact values decide.  The radius doubles (up to ascent_radius) when a
+// proposal wins the call and halves (down to step_radius / 64) when it does
+// not; the network is refitted to the grown history every refit_every
+// accepted iterations.
+struct InLoop {
+  Surrogate* S = nullptr;
+  const sbv_surrogate_opts* so = nullptr;
+  Mix64* rng = nullptr;
+  int since_fit = 0;   // accepted iterations since the last fit
+};
+
 // BFGS on -l with the inverse-Hessian update; H0 = 0.1 I
-int bfgs(Evaluator& E, const Vec& u0, const sbv_mle_opts& o, Vec& u_out, sbv_mle_result& r) {
+int bfgs(Evaluator& E, const Vec& u0, const sbv_mle_opts& o, Vec& u_out, sbv_mle_result& r,
+         InLoop* IL = nullptr) {
   const int p = E.p;
   const int64_t ev0 = E.evals;
   const size_t h0 = E.hist_l.size();
@@ -264,7 +457,11 @@ int bfgs(Evaluator& E, const Vec& u0, const sbv_mle_opts& o, Vec& u_out, sbv_mle
   bool fresh = true;
   int iters = 0, conv = 0;
   const int L = o.line_points;
-  const int per_iter = L + (analytic ? 1 : 2 * p);
+  const int kp = IL ? IL->so->step_candidates : 0;
+  const int per_iter = L + (analytic ? 1 : 2 * p) + kp;
+  double radius = IL ? IL->so->step_radius : 0.0;
+  const double rmin = radius / 64.0;
+  int won = 0;
   while (E.evals - ev0 + per_iter <= o.max_evals) {
     Vec dir(p, 0.0);
     double mx = 0.0;
@@ -285,10 +482,28 @@ int bfgs(Evaluator& E, const Vec& u0, const sbv_mle_opts& o, Vec& u_out, sbv_mle
       for (int j = 0; j < p; ++j) v[j] += a * dir[j];
       C.push_back(v);
     }
+    if (kp > 0) {
+      if (IL->since_fit >= IL->so->refit_every) {
+        if ((st = fit(E, *IL->S, *IL->so))) return st;
+        IL->since_fit = 0;
+      }
+      std::vector<Vec> props;
+      if ((st = ascend(E, *IL->S, *IL->so, u, radius, true, kp, 0.05 * radius, *IL->rng, props)))
+        return st;
+      for (Vec& v : props) C.push_back(v);
+    }
     if ((st = E.eval(C, F))) return st;
     int kb = 0;
-    for (int k = 1; k < L; ++k)
+    for (int k = 1; k < (int)C.size(); ++k)
       if (F[k] > F[kb]) kb = k;
+    if ((int)C.size() > L) {
+      if (kb >= L) {
+        ++won;
+        radius = std::min(2.0 * radius, IL->so->ascent_radius);
+      } else {
+        radius = std::max(0.5 * radius, rmin);
+      }
+    }
     if (!(F[kb] > f + 1e-12 * fabs(f))) {
       if (fresh) {
         conv = 2;   // no ascent along the gradient direction: stationary
@@ -299,6 +514,7 @@ int bfgs(Evaluator& E, const Vec& u0, const sbv_mle_opts& o, Vec& u_out, sbv_mle
       continue;
     }
     ++iters;
+    if (IL) ++IL->since_fit;
     Vec un = C[kb];   // clamped by the evaluator
     double fn = F[kb];
     if (analytic) {
@@ -351,6 +567,7 @@ int bfgs(Evaluator& E, const Vec& u0, const sbv_mle_opts& o, Vec& u_out, sbv_mle
   r.iterations = iters;
   r.converged = conv;
   r.grad_evals = (int32_t)(E.grad_evals - gv0);
+  r.proposals_won = won;
   return SBV_OK;
 }
 
@@ -408,143 +625,6 @@ void write_history(const Evaluator& E, int64_t from, double* hist_u, double* his
   *len = k;
 }
 
-// ---- surrogate proposal ----------------------------------------------------
-struct Surrogate {
-  sbv_mlp* net;
-  std::vector<float> init;     // parameters at creation: every fit starts there
-  float* d_x = nullptr;        // training rows (K x p) and targets (K)
-  float* d_t = nullptr;
-  float* d_q = nullptr;        // ascent points (Q x p), values (Q), gradients (Q x p)
-  float* d_s = nullptr;
-  float* d_g = nullptr;
-  size_t cap_rows = 0, cap_q = 0;
-  ~Surrogate() {
-    for (float* q : {d_x, d_t, d_q, d_s, d_g})
-      if (q) cudaFree(q);
-  }
-};
-
-int propose(Evaluator& E, Surrogate& S, const sbv_surrogate_opts& so, const Vec& u_start,
-            Mix64& rng, std::vector<Vec>& cand) {
-  sbv_ctx* ctx = E.pb.ctx;
-  const int p = E.p;
-  cudaStream_t s = E.pb.s;
-  // training rows: every finite pair so far, standardised per coordinate
-  std::vector<const Vec*> rows;
-  Vec ls;
-  for (size_t i = 0; i < E.hist_l.size(); ++i)
-    if (isfinite(E.hist_l[i])) {
-      rows.push_back(&E.hist_u[i]);
-      ls.push_back(E.hist_l[i]);
-    }
-  const int64_t K = (int64_t)rows.size();
-  cand.clear();
-  if (K < 4 * p) return SBV_OK;   // too little data: keep the given start
-  Vec mu(p, 0.0), sd(p, 0.0), bmin(p, INFINITY), bmax(p, -INFINITY);
-  double fm = 0.0, fs = 0.0;
-  for (int64_t i = 0; i < K; ++i) {
-    for (int j = 0; j < p; ++j) {
-      mu[j] += (*rows[i])[j];
-      bmin[j] = std::min(bmin[j], (*rows[i])[j]);
-      bmax[j] = std::max(bmax[j], (*rows[i])[j]);
-    }
-    fm += ls[i];
-  }
-  for (int j = 0; j < p; ++j) mu[j] /= K;
-  fm /= K;
-  for (int64_t i = 0; i < K; ++i) {
-    for (int j = 0; j < p; ++j) sd[j] += ((*rows[i])[j] - mu[j]) * ((*rows[i])[j] - mu[j]);
-    fs += (ls[i] - fm) * (ls[i] - fm);
-  }
-  for (int j = 0; j < p; ++j) sd[j] = sqrt(sd[j] / K) + 1e-6;
-  fs = sqrt(fs / K) + 1e-12;
-  std::vector<float> hx((size_t)K * p), ht((size_t)K);
-  for (int64_t i = 0; i < K; ++i) {
-    for (int j = 0; j < p; ++j) hx[(size_t)i * p + j] = (float)(((*rows[i])[j] - mu[j]) / sd[j]);
-    ht[i] = (float)((ls[i] - fm) / fs);
-  }
-  const int Q = so.ascent_starts;
-  if ((size_t)K > S.cap_rows) {
-    if (S.d_x) cudaFree(S.d_x);
-    if (S.d_t) cudaFree(S.d_t);
-    S.d_x = S.d_t = nullptr;
-    S.cap_rows = 0;
-    if (cudaMalloc(&S.d_x, (size_t)K * p * 4) != cudaSuccess || cudaMalloc(&S.d_t, (size_t)K * 4) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(ctx, SBV_ENOMEM, "surrogate training rows");
-    }
-    S.cap_rows = (size_t)K;
-  }
-  if ((size_t)Q > S.cap_q) {
-    for (float** q : {&S.d_q, &S.d_s, &S.d_g}) {
-      if (*q) cudaFree(*q);
-      *q = nullptr;
-    }
-    S.cap_q = 0;
-    if (cudaMalloc(&S.d_q, (size_t)Q * p * 4) != cudaSuccess || cudaMalloc(&S.d_s, (size_t)Q * 4) != cudaSuccess ||
-        cudaMalloc(&S.d_g, (size_t)Q * p * 4) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(ctx, SBV_ENOMEM, "surrogate ascent rows");
-    }
-    S.cap_q = (size_t)Q;
-  }
-  SBV_CUDA_TRY(ctx, cudaMemcpy(S.d_x, hx.data(), hx.size() * 4, cudaMemcpyHostToDevice));
-  SBV_CUDA_TRY(ctx, cudaMemcpy(S.d_t, ht.data(), ht.size() * 4, cudaMemcpyHostToDevice));
-  int st = sbv_mlp_set_params(S.net, S.init.data(), (int64_t)S.init.size());
-  if (!st) st = sbv_mlp_train(S.net, S.d_x, S.d_t, K, so.train_steps, so.batch, so.lr, so.seed,
-                              nullptr, s);
-  if (st) return st;
-  // gradient ascent on s from Q points around the start, inside the box
-  // spanned by the training rows (sign steps of 1/200 of the box per iteration)
-  Vec lo(p), hi(p);
-  for (int j = 0; j < p; ++j) {
-    lo[j] = std::max(bmin[j], E.lo[j]);
-    hi[j] = std::min(bmax[j], E.hi[j]);
-    if (hi[j] < lo[j]) hi[j] = lo[j];
-  }
-  std::vector<Vec> P(Q, Vec(p));
-  for (int q = 0; q < Q; ++q)
-    for (int j = 0; j < p; ++j) {
-      const double v = q == 0 ? u_start[j] : u_start[j] + so.ascent_radius * (2.0 * rng.uniform() - 1.0);
-      P[q][j] = std::min(std::max(v, lo[j]), hi[j]);
-    }
-  std::vector<float> hq((size_t)Q * p), hs(Q), hg((size_t)Q * p);
-  auto upload = [&]() -> int {
-    for (int q = 0; q < Q; ++q)
-      for (int j = 0; j < p; ++j) hq[(size_t)q * p + j] = (float)((P[q][j] - mu[j]) / sd[j]);
-    SBV_CUDA_TRY(ctx, cudaMemcpy(S.d_q, hq.data(), hq.size() * 4, cudaMemcpyHostToDevice));
-    return SBV_OK;
-  };
-  for (int it = 0; it < so.ascent_iters; ++it) {
-    if ((st = upload())) return st;
-    if ((st = sbv_mlp_predict(S.net, S.d_q, Q, S.d_s, S.d_g, s))) return st;
-    SBV_CUDA_TRY(ctx, cudaMemcpy(hg.data(), S.d_g, hg.size() * 4, cudaMemcpyDeviceToHost));
-    for (int q = 0; q < Q; ++q)
-      for (int j = 0; j < p; ++j) {
-        const float gj = hg[(size_t)q * p + j];
-        const double step = 0.005 * (hi[j] - lo[j]) * (gj > 0.f ? 1.0 : (gj < 0.f ? -1.0 : 0.0));
-        P[q][j] = std::min(std::max(P[q][j] + step, lo[j]), hi[j]);
-      }
-  }
-  if ((st = upload())) return st;
-  if ((st = sbv_mlp_predict(S.net, S.d_q, Q, S.d_s, nullptr, s))) return st;
-  SBV_CUDA_TRY(ctx, cudaMemcpy(hs.data(), S.d_s, hs.size() * 4, cudaMemcpyDeviceToHost));
-  std::vector<int> order(Q);
-  for (int q = 0; q < Q; ++q) order[q] = q;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a] > hs[b]; });
-  for (int q : order) {
-    if ((int)cand.size() >= so.candidates) break;
-    bool far = true;
-    for (const Vec& c : cand) {
-      double dist = 0.0;
-      for (int j = 0; j < p; ++j) dist = std::max(dist, fabs(c[j] - P[q][j]));
-      far = far && dist > 0.05;
-    }
-    if (far) cand.push_back(P[q]);
-  }
-  return SBV_OK;
-}
-
 sbv_surrogate_opts default_surrogate_opts() {
   sbv_surrogate_opts o;
   memset(&o, 0, sizeof(o));
@@ -557,6 +637,9 @@ sbv_surrogate_opts default_surrogate_opts() {
   o.candidates = 8;
   o.ascent_radius = 1.0;
   o.seed = 1;
+  o.step_candidates = 2;
+  o.step_radius = 0.5;
+  o.refit_every = 10;
   return o;
 }
 
@@ -594,7 +677,8 @@ extern "C" int sbv_mle_multistart(sbv_ctx* ctx, const void* X, int dtype, const 
                                   int32_t nmax, const double* starts, int32_t S,
                                   const double* lower, const double* upper,
                                   const sbv_mle_opts* opts, sbv_mlp* mlp,
-                                  const sbv_surrogate_opts* sopts, double* theta_out,
+                                  const sbv_surrogate_opts* sopts, const double* prior_u,
+                                  const double* prior_l, int64_t prior_n, double* theta_out,
                                   sbv_mle_result* results, void* stream) {
   const sbv_mle_opts o = opts ? *opts : default_opts();
   const sbv_surrogate_opts so = sopts ? *sopts : default_surrogate_opts();
@@ -604,13 +688,22 @@ extern "C" int sbv_mle_multistart(sbv_ctx* ctx, const void* X, int dtype, const 
   if (!starts || S < 1 || !theta_out || !results)
     return fail(ctx, SBV_EINVAL, "starts, S >= 1, theta_out and results are required");
   if (mlp && (so.exact_starts < 0 || so.train_steps < 1 || so.batch < 1 || !(so.lr > 0.f) ||
-              so.ascent_starts < 1 || so.ascent_iters < 0 || so.candidates < 1 ||
-              !(so.ascent_radius >= 0.0)))
+              so.ascent_starts < 1 || so.ascent_iters < 0 || so.candidates < 0 ||
+              !(so.ascent_radius >= 0.0) || so.step_candidates < 0 || so.step_candidates > 64 ||
+              !(so.step_radius > 0.0) || !(so.step_radius <= so.ascent_radius) ||
+              so.refit_every < 1))
     return fail(ctx, SBV_EINVAL, "bad surrogate options");
+  if (prior_n < 0 || (prior_n > 0 && (!prior_u || !prior_l)))
+    return fail(ctx, SBV_EINVAL, "prior_n >= 0 rows of prior_u and prior_l required");
   Evaluator E;
   E.pb = pb;
   E.p = d + 2;
   if ((st = set_bounds(E, lower, upper))) return st;
+  // pairs of earlier runs join the history (they count as no evaluation here)
+  for (int64_t i = 0; i < prior_n; ++i) {
+    E.hist_u.emplace_back(prior_u + i * E.p, prior_u + (i + 1) * E.p);
+    E.hist_l.push_back(isfinite(prior_l[i]) ? prior_l[i] : -INFINITY);
+  }
   Surrogate Sg;
   Sg.net = mlp;
   if (mlp) {
@@ -626,9 +719,15 @@ extern "C" int sbv_mle_multistart(sbv_ctx* ctx, const void* X, int dtype, const 
     memset(&r, 0, sizeof(r));
     const int64_t ev0 = E.evals;
     const int c0 = E.calls;
-    if (mlp && i >= so.exact_starts) {
+    InLoop il;
+    il.S = &Sg;
+    il.so = &so;
+    il.rng = &rng;
+    il.since_fit = so.refit_every;   // fit before the first in-loop proposal ...
+    if (mlp && i >= so.exact_starts && so.candidates > 0) {
       std::vector<Vec> cand;
       if ((st = propose(E, Sg, so, u0, rng, cand))) return st;
+      il.since_fit = 0;              // ... unless the restart proposal just did
       if (!cand.empty()) {
         cand.push_back(u0);   // the start itself competes: the exact values decide
         Vec F;
@@ -640,7 +739,8 @@ extern "C" int sbv_mle_multistart(sbv_ctx* ctx, const void* X, int dtype, const 
       }
     }
     Vec u;
-    if ((st = bfgs(E, u0, o, u, r))) return st;
+    const bool inloop = mlp && i >= so.exact_starts && so.step_candidates > 0;
+    if ((st = bfgs(E, u0, o, u, r, inloop ? &il : nullptr))) return st;
     r.evals = (int32_t)(E.evals - ev0);   // proposal calls included
     r.calls = E.calls - c0;
     for (int j = 0; j < E.p; ++j) theta_out[(size_t)i * E.p + j] = exp(u[j]);

@@ -66,6 +66,36 @@ def test_mle_structs_match_the_c_layout():
     assert o.gradient == 1 and o.precision == 0
 
 
+def test_option_structs_match_a_c_compilers_layout(tmp_path):
+    """sizeof and offsetof of the option and result structs, printed by a C
+    program compiled against include/sbv.h, equal the ctypes mirrors'."""
+    import ctypes
+    import subprocess
+    from paper_2504_12004_gb300 import _lib
+    mirrors = {"sbv_mle_opts": _lib.MleOpts, "sbv_mle_result": _lib.MleResult,
+               "sbv_surrogate_opts": _lib.SurrogateOpts}
+    lines = []
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"sbv.h\"\n"
+                   "int main(void) {\n" + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", str(ROOT / "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n"):
+        if line:
+            c, f, v = line.split()
+            got[(c, f)] = int(v)
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
 def test_product_path_does_not_import_oracle():
     pkg = ROOT / "paper_2504_12004_gb300"
     for f in list(pkg.rglob("*.py")) + list(pkg.rglob("*.cu")) + list(pkg.rglob("*.cuh")):
