@@ -1231,6 +1231,16 @@ loglik_mixed_kernel(MixedArgs P) {
       if (!ok) record_failure(a.dstat, code, (int)blk, th_i);
     }
     __syncthreads();
+    // the item's global slice is dead: drop its L2 lines without writing
+    // them back to HBM (a discarded line reads as indeterminate until it is
+    // written again, and every item writes each slice entry it reads).  The
+    // slice starts on a 256-byte boundary and spans whole 256-byte units.
+    {
+      const char* g0 = (const char*)G;
+      const int lines = (int)(lay.g_stride * sizeof(float) / 128);
+      for (int q = tid; q < lines; q += THREADS)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(g0 + (size_t)q * 128) : "memory");
+    }
     if (s_timeout) break;   // leave the item loop; TMEM is released below
   }
   // after a timed-out wait, give the outstanding MMAs one more bounded wait
