@@ -213,3 +213,25 @@ def test_surrogate_proposals_inside_the_loop(ctx):
         assert same_or_better >= 6
         if name == "in-loop":
             assert won >= 8
+
+
+def test_surrogate_option_and_prior_errors(ctx):
+    from paper_2504_12004_gb300 import Mlp, SBVError
+    from paper_2504_12004_gb300._lib import mle_opts, surrogate_opts
+    dev, f = small_problem(ctx, 300, 2, 30, 10, np.array([1.0, 0.01, 0.2, 0.3]), 5, 9)
+    S = (dev["X"], dev["y"], dev["ptr"], dev["pts"], dev["nbr"], dev["cnt"])
+    start = np.array([[1.0, 0.01, 0.3, 0.3]])
+    opts = mle_opts(precision="fp64", max_evals=200)
+    net = Mlp(ctx, 4, seed=1)
+    for bad in (surrogate_opts(step_candidates=-1), surrogate_opts(step_candidates=65),
+                surrogate_opts(step_radius=0.0), surrogate_opts(step_radius=2.0, ascent_radius=1.0),
+                surrogate_opts(refit_every=0), surrogate_opts(candidates=-1)):
+        with pytest.raises(SBVError):
+            ctx.sbv_mle_multistart(*S, start, opts=opts, mlp=net, sopts=bad)
+    with pytest.raises(ValueError):
+        ctx.sbv_mle_multistart(*S, start, opts=opts, prior=(np.zeros((3, 4)), np.zeros(2)))
+    # prior pairs join the history but are not counted as evaluations
+    _, r0 = ctx.sbv_mle_multistart(*S, start, opts=opts)
+    prior = (np.log(np.tile(start, (50, 1))) + 0.01 * np.arange(50)[:, None], -np.arange(50.0))
+    _, r1 = ctx.sbv_mle_multistart(*S, start, opts=opts, prior=prior)
+    assert r1[0].evals == r0[0].evals and r1[0].ll == r0[0].ll
