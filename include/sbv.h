@@ -278,7 +278,7 @@ int sbv_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y,
 /*
  * sbv_loglik_grad -- the FP64 log-likelihood of sbv_loglik together with its
  * gradient with respect to theta = (sigma^2, tau^2, beta_1..beta_d), for B
- * parameter rows (the "gradient quantities" handed to the optimiser, Sec. 6).
+ * parameter rows (the gradient information handed to the optimiser, Sec. 6).
  *
  * Arguments as sbv_loglik (FP64 arithmetic; no precision argument), plus
  *   grad               device, B x (2+d) doubles out: d l(theta_b) / d theta_k

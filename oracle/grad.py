@@ -1,8 +1,8 @@
 """Gradient of the Block Vecchia log-likelihood with respect to theta, FP64
 (test infrastructure only).
 
-The paper evaluates the likelihood and hands "gradient quantities" to the
-optimiser (Sec. 6) without printing them; this module writes out the
+The paper evaluates the likelihood and hands gradient information to the
+optimiser (Sec. 6) without printing it; this module writes out the
 textbook derivative of a Gaussian log-density for the block conditional of
 Alg. 5.  Block i's term is the difference of two Gaussian log-densities,
 

@@ -205,10 +205,11 @@ def knn_block(Z, centre, cand: np.ndarray, m: int) -> np.ndarray:
 def knn(Z, blk, rank, centres, m: int, blocks=None):
     """NN set of each block: points of strictly earlier-ranked blocks nearest to its centre.
 
-    Readings: the query is the block centre (Alg. 4 line "Searching m nearest
-    neighbors for the i-th block"); "order not exceeds" is taken as strictly
-    earlier so that a block never conditions on itself; with fewer than m
-    earlier points all of them are taken.  The lambda filter of Alg. 4 changes
+    Readings: the query is the block centre (Alg. 4 searches each block's
+    neighbours from one query point per block); a neighbour's block may not
+    come later in the order, taken here as strictly earlier so that a block
+    never conditions on itself; with fewer than m earlier points all of them
+    are taken.  The lambda filter of Alg. 4 changes
     only which points are examined, not the answer, so it is not applied here.
 
     Returns (nbr (k x m, -1 padded), cnt (k)) for the requested blocks (default all).

@@ -514,7 +514,7 @@ int run_loglik(sbv_ctx* ctx, const void* X, int dtype, const double* y, int64_t 
 
 // ---------------------------------------------------------------------------
 // Gradient of the block terms with respect to theta = (sigma^2, tau^2,
-// beta_1..beta_d), FP64 (the "gradient quantities" of Sec. 6).  For either
+// beta_1..beta_d), FP64 (the gradient information of Sec. 6).  For either
 // Gaussian system (joint S = J u B, and J), with x = Sigma^{-1} y,
 //   d log N(y; 0, Sigma) / d theta_k = 1/2 x^T dSigma_k x - 1/2 tr(Sigma^{-1} dSigma_k),
 // and l_i is the joint log-density minus the J one.  From the item's factor L:
